@@ -1,0 +1,395 @@
+"""Pins for the FP64 oracle against facts fixed outside the oracle itself:
+published test vectors, closed forms, finite differences, brute force,
+spectral (Bochner) representations and statistical bands.
+
+CPU only; the whole file runs in well under a minute.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- probes --
+
+def test_splitmix64_published_vectors():
+    with open(os.path.join(GOLDEN, "splitmix64.txt")) as fh:
+        rows = [l.split() for l in fh if l.strip() and not l.startswith("#")]
+    assert len(rows) == 2
+    for row in rows:
+        state = int(row[0])
+        for expect in row[1:]:
+            state, out = O.splitmix64_next(state)
+            assert out == int(expect)
+
+
+def test_rademacher_matches_scalar_definition():
+    n, p, seed = 37, 5, 0xC0FFEE
+    Z = O.rademacher_probes(n, p, seed)
+    for c in range(p):
+        for i in range(n):
+            h = O.probe_hash(seed, c, i)
+            assert Z[i, c] == (1.0 if (h >> 63) == 0 else -1.0)
+
+
+def test_rademacher_balance():
+    Z = O.rademacher_probes(20000, 4, 3)
+    assert set(np.unique(Z)) == {-1.0, 1.0}
+    # Each column is a fair coin: mean within 4 sigma of 0.
+    assert np.all(np.abs(Z.mean(axis=0)) < 4.0 / math.sqrt(20000))
+    # Columns differ from one another (the column index enters the hash).
+    assert np.abs(Z[:, 0] @ Z[:, 1]) < 4.0 * math.sqrt(20000)
+
+
+# ---------------------------------------------------------------- kernels --
+
+def _bochner_gaussian(delta, l, nsamp, rng):
+    # k(r) = E[cos(w . delta)], w ~ N(0, I / l^2)  (spectral density of the RBF kernel)
+    w = rng.standard_normal((nsamp, delta.size)) / l
+    return float(np.mean(np.cos(w @ delta)))
+
+
+def _bochner_matern32(delta, l, nsamp, rng):
+    # Matern-nu spectral density ~ (2 nu / l^2 + |w|^2)^-(nu + d/2): a multivariate
+    # Student-t with 2 nu = 3 degrees of freedom and scale 1 / l.
+    g = rng.standard_normal((nsamp, delta.size))
+    u = rng.chisquare(3.0, size=(nsamp, 1))
+    w = g / (l * np.sqrt(u / 3.0))
+    return float(np.mean(np.cos(w @ delta)))
+
+
+@pytest.mark.parametrize("kind,sampler", [(O.GAUSSIAN, _bochner_gaussian),
+                                          (O.MATERN32, _bochner_matern32)])
+def test_kernel_matches_spectral_representation(kind, sampler):
+    rng = np.random.default_rng(11)
+    l = 0.7
+    for d in (1, 3):
+        for r in (0.0, 0.3, 0.7, 1.5):
+            delta = np.zeros(d)
+            delta[0] = r
+            mc = sampler(delta, l, 400_000, rng)
+            k = O.kernel_value(np.array(r * r), kind, l)
+            assert abs(mc - k) < 6e-3, (kind, d, r, mc, k)
+
+
+def test_gaussian_is_separable_over_dimensions():
+    rng = np.random.default_rng(1)
+    A = rng.random((7, 4))
+    B = rng.random((5, 4))
+    l = 0.4
+    full = O.kernel_value(O.sqdist(A, B), O.GAUSSIAN, l)
+    prod = np.ones_like(full)
+    for t in range(4):
+        prod *= O.kernel_value(O.sqdist(A[:, t:t + 1], B[:, t:t + 1]), O.GAUSSIAN, l)
+    np.testing.assert_allclose(full, prod, rtol=1e-13)
+
+
+def test_sqdist_brute_force():
+    rng = np.random.default_rng(2)
+    A = rng.standard_normal((6, 3))
+    B = rng.standard_normal((4, 3))
+    R2 = O.sqdist(A, B)
+    for i in range(6):
+        for j in range(4):
+            assert R2[i, j] == pytest.approx(sum((A[i, t] - B[j, t]) ** 2 for t in range(3)), rel=1e-14)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_kernel_dl_central_difference(kind):
+    r2 = np.array([1e-4, 0.01, 0.09, 0.3, 1.0, 2.5])
+    for l in (0.2, 0.7, 1.3):
+        h = 1e-5 * l
+        fd = (O.kernel_value(r2, kind, l + h) - O.kernel_value(r2, kind, l - h)) / (2 * h)
+        np.testing.assert_allclose(O.kernel_dl(r2, kind, l), fd, rtol=1e-7, atol=1e-13)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_kernel_special_cases(kind):
+    assert O.kernel_value(np.array(0.0), kind, 0.3) == 1.0
+    assert O.kernel_dl(np.array(0.0), kind, 0.3) == 0.0
+    far = np.array((40 * 0.3) ** 2)
+    assert O.kernel_value(far, kind, 0.3) < 1e-25
+    assert O.kernel_dl(far, kind, 0.3) < 1e-20
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_khat_symmetric_positive_definite(kind):
+    X = inputs.points(300, 3, seed=5)
+    theta = (0.05, 1.3, 0.25)
+    Kh = O.khat_dense(X, kind, theta)
+    assert np.array_equal(Kh, Kh.T)
+    assert np.linalg.eigvalsh(Kh).min() >= theta[0] * (1 - 1e-10)
+
+
+# -------------------------------------------------------------- the matvec --
+
+def _identical_points(n, d, value=0.37):
+    return np.full((n, d), value, dtype=np.float32)
+
+
+def _far_points(n, d, spacing):
+    X = np.zeros((n, d), dtype=np.float32)
+    X[:, 0] = spacing * np.arange(n)
+    return X
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_kmv_identical_points_closed_form(kind):
+    n, s, f, l = 50, 0.2, 1.7, 0.3
+    V = inputs.gaussian_block(n, 3, seed=1).astype(np.float64)
+    Y, dYf, dYl = O.kmv_rows(_identical_points(n, 2), V, kind, (s, f, l), block=16)
+    colsum = V.sum(axis=0)
+    np.testing.assert_allclose(Y, f * f * colsum[None, :] + s * V, rtol=1e-13)
+    np.testing.assert_allclose(dYf, 2 * f * np.repeat(colsum[None, :], n, 0), rtol=1e-13)
+    np.testing.assert_allclose(dYl, 0.0, atol=1e-15)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_kmv_far_points_closed_form(kind):
+    n, s, f, l = 40, 0.2, 1.7, 0.1
+    V = inputs.gaussian_block(n, 2, seed=2).astype(np.float64)
+    Y, dYf, dYl = O.kmv_rows(_far_points(n, 3, 40 * l), V, kind, (s, f, l))
+    np.testing.assert_allclose(Y, (f * f + s) * V, rtol=1e-12)
+    np.testing.assert_allclose(dYf, 2 * f * V, rtol=1e-12)
+    np.testing.assert_allclose(dYl, 0.0, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_kmv_rows_brute_force(kind):
+    n, theta = 60, (0.1, 1.2, 0.35)
+    X = inputs.points(n, 3, seed=9)
+    V = inputs.gaussian_block(n, 4, seed=3).astype(np.float64)
+    rows = np.array([0, 7, 59, 13])
+    Y, dYf, dYl = O.kmv_rows(X, V, kind, theta, rows=rows, block=3)
+    s, f, l = theta
+    Xd = X.astype(np.float64)
+    for a, i in enumerate(rows):
+        for c in range(4):
+            acc_k = acc_d = 0.0
+            for j in range(n):
+                r2 = float(np.sum((Xd[i] - Xd[j]) ** 2))
+                acc_k += float(O.kernel_value(np.array(r2), kind, l)) * V[j, c]
+                acc_d += float(O.kernel_dl(np.array(r2), kind, l)) * V[j, c]
+            assert Y[a, c] == pytest.approx(f * f * acc_k + s * V[i, c], rel=1e-12, abs=1e-13)
+            assert dYf[a, c] == pytest.approx(2 * f * acc_k, rel=1e-12, abs=1e-13)
+            assert dYl[a, c] == pytest.approx(f * f * acc_d, rel=1e-12, abs=1e-13)
+
+
+def test_predict_mean_identical_points_closed_form():
+    n, s, f, l = 30, 0.3, 1.1, 0.5
+    X = _identical_points(n, 3)
+    y = inputs.gaussian_block(n, 1, seed=4)[:, 0].astype(np.float64)
+    alpha = O.exact_nll(X, y, O.GAUSSIAN, (s, f, l))["alpha"]
+    mu = O.predict_mean(X, X[:2], alpha, O.GAUSSIAN, (s, f, l))
+    np.testing.assert_allclose(mu, f * f * y.sum() / (s + n * f * f), rtol=1e-12)
+
+
+def test_predict_mean_interpolates_at_small_noise():
+    X = inputs.points(40, 2, seed=12)
+    y = np.sin(3 * X[:, 0].astype(np.float64))
+    theta = (1e-8, 1.0, 0.3)
+    alpha = O.exact_nll(X, y, O.GAUSSIAN, theta)["alpha"]
+    mu = O.predict_mean(X, X, alpha, O.GAUSSIAN, theta)
+    np.testing.assert_allclose(mu, y, atol=1e-5)
+
+
+# --------------------------------------------------------- exact NLL / grad --
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_exact_nll_identical_points_closed_form(kind):
+    n, s, f, l = 25, 0.15, 0.9, 0.4
+    X = _identical_points(n, 3)
+    y = inputs.gaussian_block(n, 1, seed=6)[:, 0].astype(np.float64)
+    out = O.exact_nll(X, y, kind, (s, f, l))
+    lam = s + n * f * f
+    alpha = (y - f * f * y.sum() / lam) / s           # Sherman-Morrison
+    logdet = math.log(lam) + (n - 1) * math.log(s)
+    loss = 0.5 * (y @ alpha + logdet + n * math.log(2 * math.pi))
+    g_s = 0.5 * (-(alpha @ alpha) + 1.0 / lam + (n - 1) / s)
+    g_f = 0.5 * (-2 * f * alpha.sum() ** 2 + 2 * f * n / lam)
+    np.testing.assert_allclose(out["alpha"], alpha, rtol=1e-10)
+    assert out["logdet"] == pytest.approx(logdet, rel=1e-12)
+    assert out["loss"] == pytest.approx(loss, rel=1e-12)
+    np.testing.assert_allclose(out["grad"], [g_s, g_f, 0.0], rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_exact_nll_far_points_closed_form(kind):
+    n, s, f, l = 30, 0.2, 1.4, 0.1
+    X = _far_points(n, 2, 40 * l)
+    y = inputs.gaussian_block(n, 1, seed=7)[:, 0].astype(np.float64)
+    out = O.exact_nll(X, y, kind, (s, f, l))
+    c = f * f + s
+    yy = y @ y
+    assert out["logdet"] == pytest.approx(n * math.log(c), rel=1e-12)
+    assert out["loss"] == pytest.approx(0.5 * (yy / c + n * math.log(c) + n * math.log(2 * math.pi)), rel=1e-12)
+    np.testing.assert_allclose(out["grad"], [0.5 * (-yy / c ** 2 + n / c),
+                                             0.5 * (-2 * f * yy / c ** 2 + 2 * f * n / c), 0.0],
+                               rtol=1e-10, atol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_exact_grad_central_difference(kind):
+    prob = inputs.uniform_problem(120, 3, kind, (0.1, 1.2, 0.3), seed=4)
+    theta = np.array(prob.theta)
+    g = O.exact_nll(prob.X, prob.y, kind, theta)["grad"]
+    for t in range(3):
+        h = 1e-4 * theta[t]
+        tp, tm = theta.copy(), theta.copy()
+        tp[t] += h
+        tm[t] -= h
+        fd = (O.exact_nll(prob.X, prob.y, kind, tp)["loss"]
+              - O.exact_nll(prob.X, prob.y, kind, tm)["loss"]) / (2 * h)
+        assert g[t] == pytest.approx(fd, rel=1e-6, abs=1e-8 * np.abs(g).max()), (t, g[t], fd)
+
+
+def test_exact_logdet_against_eigenvalues():
+    X = inputs.points(80, 2, seed=8)
+    theta = (0.05, 1.0, 0.2)
+    out = O.exact_nll(X, np.ones(80), O.MATERN32, theta)
+    ev = np.linalg.eigvalsh(O.khat_dense(X, O.MATERN32, theta))
+    assert out["logdet"] == pytest.approx(np.sum(np.log(ev)), rel=1e-11)
+
+
+# ------------------------------------------------------------------- SLQ --
+
+def test_lanczos_two_distinct_eigenvalues_exact():
+    # Identical points: Kh = f^2 11^T + s I has eigenvalues s + n f^2 and s, so a
+    # 2-step Gauss rule integrates log exactly: z^T log(Kh) z in closed form.
+    n, s, f = 40, 0.3, 0.8
+    A = f * f * np.ones((n, n)) + s * np.eye(n)
+    z = O.rademacher_probes(n, 1, 17)[:, 0]
+    a, b = O.lanczos(A, z, 2)
+    est = O.gauss_quadrature_log(a, b, z @ z)
+    m = z.sum() ** 2 / n
+    exact = math.log(s + n * f * f) * m + math.log(s) * (z @ z - m)
+    assert est == pytest.approx(exact, rel=1e-12)
+
+
+def test_lanczos_full_length_equals_matrix_log():
+    X = inputs.points(30, 2, seed=10)
+    A = O.khat_dense(X, O.GAUSSIAN, (0.1, 1.0, 0.4))
+    z = O.rademacher_probes(30, 1, 2)[:, 0]
+    a, b = O.lanczos(A, z, 30)
+    ev, U = np.linalg.eigh(A)
+    exact = float(z @ (U @ (np.log(ev) * (U.T @ z))))
+    assert O.gauss_quadrature_log(a, b, z @ z) == pytest.approx(exact, rel=1e-9)
+
+
+def test_lanczos_from_cg_matches_explicit_lanczos():
+    # The CG step coefficients carry the Lanczos tridiagonal of K from q1 = b/||b||.
+    X = inputs.points(200, 3, seed=11)
+    A = O.khat_dense(X, O.GAUSSIAN, (0.1, 1.0, 0.3))
+    z = O.rademacher_probes(200, 1, 5)[:, 0]
+    _, _, _, al, be = O.cg(A, z, 1e-12, 12)
+    a1, b1 = O.lanczos_from_cg(al[0], be[0], 10)
+    a2, b2 = O.lanczos(A, z, 10)
+    np.testing.assert_allclose(a1, a2, rtol=1e-8)
+    np.testing.assert_allclose(b1, np.abs(b2), rtol=1e-7)
+
+
+def test_slq_converges_to_logdet_within_3_sigma():
+    X = inputs.points(300, 3, seed=13)
+    A = O.khat_dense(X, O.GAUSSIAN, (0.1, 1.0, 0.3))
+    exact = np.linalg.slogdet(A)[1]
+    Z = O.rademacher_probes(300, 200, 99)
+    est, vals = O.slq_logdet(A, Z, 30)
+    sigma = vals.std(ddof=1) / math.sqrt(vals.size)
+    assert abs(est - exact) < 3 * sigma + 1e-9 * abs(exact)
+    # More probes shrink the band at ~1/sqrt(p).
+    est_few, vals_few = O.slq_logdet(A, Z[:, :20], 30)
+    assert vals_few.std(ddof=1) / math.sqrt(20) > sigma
+
+
+# ------------------------------------------------------------- Hutchinson --
+
+def test_hutchinson_exact_for_diagonal():
+    n, s, f, l = 50, 0.25, 1.3, 0.1
+    X = _far_points(n, 2, 40 * l)
+    Kh = O.khat_dense(X, O.GAUSSIAN, (s, f, l))
+    dKs = O.dkhat_dense(X, O.GAUSSIAN, (s, f, l))
+    Z = O.rademacher_probes(n, 3, 4)
+    tr, vals = O.hutchinson_traces(Kh, dKs, Z)
+    c = f * f + s
+    np.testing.assert_allclose(vals[0], n / c, rtol=1e-12)
+    np.testing.assert_allclose(vals[1], 2 * f * n / c, rtol=1e-12)
+    np.testing.assert_allclose(vals[2], 0.0, atol=1e-12)
+
+
+def test_hutchinson_unbiased_within_3_sigma():
+    prob = inputs.uniform_problem(250, 3, O.MATERN32, (0.1, 1.0, 0.3), seed=14)
+    ex = O.exact_nll(prob.X, prob.y, prob.kind, prob.theta)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    dKs = O.dkhat_dense(prob.X, prob.kind, prob.theta)
+    Z = O.rademacher_probes(250, 400, 7)
+    tr, vals = O.hutchinson_traces(Kh, dKs, Z)
+    sig = vals.std(axis=1, ddof=1) / math.sqrt(400)
+    assert np.all(np.abs(tr - ex["trace"]) < 3 * sig + 1e-10)
+
+
+def test_est_nll_approaches_exact():
+    prob = inputs.small_problem(seed=0, n=300)
+    ex = O.exact_nll(prob.X, prob.y, prob.kind, prob.theta)
+    Z = O.rademacher_probes(300, 256, 1)
+    es = O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 30)
+    assert es["yalpha"] == pytest.approx(ex["yalpha"], rel=1e-12)
+    np.testing.assert_allclose(es["quad"], ex["quad"], rtol=1e-12)
+    sig_ld = es["logdet_probes"].std(ddof=1) / 16.0
+    assert abs(es["logdet"] - ex["logdet"]) < 3 * sig_ld
+    sig_tr = es["trace_probes"].std(axis=1, ddof=1) / 16.0
+    assert np.all(np.abs(es["trace"] - ex["trace"]) < 3 * sig_tr + 1e-10)
+
+
+# -------------------------------------------------------------------- CG --
+
+def test_cg_matches_cholesky_solve():
+    X = inputs.points(200, 3, seed=15)
+    A = O.khat_dense(X, O.GAUSSIAN, (0.1, 1.0, 0.3))
+    B = inputs.gaussian_block(200, 3, seed=5).astype(np.float64)
+    Xs, iters, relres, _, _ = O.cg(A, B, 1e-10, 1000)
+    ref = sla.cho_solve(sla.cho_factor(A), B)
+    kappa = np.linalg.cond(A)
+    assert np.all(relres <= 1e-10)
+    for c in range(3):
+        err = np.linalg.norm(Xs[:, c] - ref[:, c]) / np.linalg.norm(ref[:, c])
+        assert err <= kappa * 1e-10 * 10
+    assert np.all(iters < 200)
+
+
+def test_cg_maxit_reports_residual():
+    X = inputs.points(200, 2, seed=16)
+    A = O.khat_dense(X, O.GAUSSIAN, (1e-3, 1.0, 0.3))
+    b = np.ones(200)
+    _, iters, relres, _, _ = O.cg(A, b, 1e-14, 3)
+    assert iters[0] == 3 and relres[0] > 1e-14
+
+
+# ---------------------------------------------- pins catch planted mistakes --
+
+def test_planted_sign_error_in_dl_is_caught(monkeypatch):
+    good = O.kernel_dl
+    monkeypatch.setattr(O.gp_oracle, "kernel_dl", lambda r2, kind, l: -good(r2, kind, l))
+    with pytest.raises(AssertionError):
+        test_exact_grad_central_difference(O.GAUSSIAN)
+
+
+def test_planted_dropped_noise_term_is_caught(monkeypatch):
+    monkeypatch.setattr(O.gp_oracle, "khat_dense",
+                        lambda X, kind, th: th[1] ** 2 * O.kernel_value(O.sqdist(X, X), kind, th[2]))
+    with pytest.raises(Exception):
+        test_exact_nll_far_points_closed_form(O.GAUSSIAN)
+
+
+def test_planted_transposed_cross_product_is_caught(monkeypatch):
+    # A cross product taking points in the wrong order changes the shape/values.
+    orig = O.gp_oracle.sqdist
+    monkeypatch.setattr(O.gp_oracle, "sqdist", lambda A, B: orig(B, A).T * 1.0001)
+    with pytest.raises(AssertionError):
+        test_kmv_rows_brute_force(O.GAUSSIAN)
