@@ -1,0 +1,341 @@
+"""Benchmark of the GP hot path on GB300: fused on-the-fly kernel product throughput.
+
+Workload (one "step"): one fused pass Kh V, dKh/df V, dKh/dl V (dKh/ds V = V)
+over n = 100,000 points in d = 3 (uniform on [0,1]^3, seeded), Matern-3/2 with
+f = 1.5, l = 0.2, s = 0.05, V = [y | 31 Rademacher columns] (w = 32), FP32.
+Metric: kernel entries x columns per second, n^2 w / (pass time).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gp|reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload on
+its own GPU (the product does not shard without an exchange step); the value is
+the sum over ranks / the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle (test infrastructure, never the
+product path) on a bounded sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("kernel entries×cols/s and loss+grad ms per Θ on 1 GB300, "
+          "mixed vs FP32 at ≤1e-4 rel err")
+UNIT = "entries*cols/s"
+WORKLOAD = ("fused on-the-fly product Kh.V + dKh/df.V + dKh/dl.V: n=100000 d=3 uniform[0,1]^3, "
+            "Matern-3/2 f=1.5 l=0.2 s=0.05, V=[y | 31 Rademacher] w=32, FP32")
+N_PTS, D, W = 100_000, 3, 32
+L2_FLUSH_BYTES = 256 << 20
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+def _traffic():
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_oracle_rate(target_s: float = 12.0) -> dict:
+    """FP64 oracle on sampled rows of the same workload: entries*cols/s on the host."""
+    import oracle as O
+    from paper_2503_02259_gb300 import inputs
+    prob = inputs.matvec_problem(seed=0)
+    V = inputs.multivector(prob.y, W, seed=0)
+    rng = np.random.default_rng(1)
+    rows = rng.choice(prob.n, 4000, replace=False)
+    t0 = time.perf_counter()
+    O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows[:16], block=16)
+    per_row = (time.perf_counter() - t0) / 16
+    nrows = int(max(16, min(4000, target_s / max(per_row, 1e-9))))
+    t0 = time.perf_counter()
+    O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows[:nrows], block=64)
+    dt = time.perf_counter() - t0
+    value = nrows * prob.n * W / dt
+    return {"value": value, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": (f"FP64 NumPy oracle, fused Kh.V + dKh.V on {nrows} sampled rows of the "
+                       f"n=100000 w=32 workload ({dt:.1f} s); NumPy elementwise single-threaded, "
+                       "BLAS matmul on default threads")}
+
+
+def run_reference(args) -> int:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    vals = []
+    t_all = time.perf_counter()
+    budget = max(3.0, 60.0 / max(1, args.steps + args.warmup))
+    for i in range(args.warmup + args.steps):
+        r = cpu_oracle_rate(target_s=min(budget, 8.0))
+        if i >= args.warmup:
+            vals.append(r)
+    value = statistics.median(v["value"] for v in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": N_PTS * N_PTS * W / value * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": vals[-1]["sample"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle", "sample": vals[-1]["sample"]},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_all}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def loss_grad_small(api, torch, reps: int = 3) -> dict:
+    """Loss + gradient per Theta on the small configuration (n=2000, d=3, Gaussian)."""
+    from paper_2503_02259_gb300 import inputs
+    prob = inputs.small_problem(seed=0)
+    X = torch.from_numpy(prob.X).cuda()
+    y = torch.from_numpy(prob.y).cuda()
+    opts = api.solve_opts(nprobe=10, nlanczos=30, cg_rtol=1e-8, seed=1234)
+    api.gp_loss_and_grad(X, y, prob.kind, prob.theta, opts)
+    ts = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, grad, info = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, opts)
+        ts.append((time.perf_counter() - t0) * 1e3)
+    return {"workload": "n=2000 d=3 uniform, Gaussian f=1 l=0.3 s=0.1, block CG on [y|10 probes] "
+                        "to rtol 1e-8, SLQ 10x30, Hutchinson, FP32",
+            "ms": statistics.median(ts), "loss": loss, "grad": grad,
+            "cg_iters": info["cg_iters"]}
+
+
+def main() -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import _binding as B
+    from paper_2503_02259_gb300 import api, inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    prob = inputs.matvec_problem(seed=0)
+    Vh = inputs.multivector(prob.y, W, seed=0)
+    X = torch.from_numpy(prob.X).to(dev)
+    V = torch.from_numpy(Vh).to(dev)
+    Y = torch.empty_like(V)
+    dYf = torch.empty_like(V)
+    dYl = torch.empty_like(V)
+    pr, _ = api.problem(X, prob.kind, prob.theta)
+    ws = api.workspace(B.OP_GRAD_MATMUL, pr, W, None, dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    L = B.lib()
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        B.check(L.gp_kernel_grad_matmul(B.ctypes.byref(pr), api._ptr(V), W, api._ptr(Y),
+                                        api._ptr(dYf), api._ptr(dYl), B.PREC_FP32, api._ptr(ws),
+                                        ws.numel(), api._stream(dev)), "gp_kernel_grad_matmul")
+
+    for _ in range(max(3, args.warmup)):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    stops = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    B.check(L.gp_profile_begin(), "gp_profile_begin")
+    for i in range(args.steps):
+        flush.zero_()                     # L2 flushed between steps, outside the timed bracket
+        starts[i].record(stream)
+        step()
+        stops[i].record(stream)
+    torch.cuda.synchronize()
+    prod_ms = B.c_double()
+    prod_n = B.c_int64()
+    launches = B.c_int64()
+    B.check(L.gp_profile_end(B.ctypes.byref(prod_ms), B.ctypes.byref(prod_n),
+                             B.ctypes.byref(launches)), "gp_profile_end")
+    step_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    if dist:
+        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.barrier()
+        step_ms = float(t.item())
+    clocks = sampler.stop() if sampler else None
+
+    # End to end through the public call with host buffers: pinned H2D of X and V,
+    # the call, D2H of the three outputs, every step.
+    e2e_steps = min(args.steps, 10)
+    Xp = torch.from_numpy(prob.X).pin_memory()
+    Vp = torch.from_numpy(Vh).pin_memory()
+    outs = [torch.empty((N_PTS, W), dtype=torch.float32).pin_memory() for _ in range(3)]
+    Xd = torch.empty_like(X)
+    Vd = torch.empty_like(V)
+    pr2, _ = api.problem(Xd, prob.kind, prob.theta)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        Xd.copy_(Xp, non_blocking=True)
+        Vd.copy_(Vp, non_blocking=True)
+        B.check(L.gp_kernel_grad_matmul(B.ctypes.byref(pr2), api._ptr(Vd), W, api._ptr(Y),
+                                        api._ptr(dYf), api._ptr(dYl), B.PREC_FP32, api._ptr(ws),
+                                        ws.numel(), api._stream(dev)), "gp_kernel_grad_matmul")
+        for o, src in zip(outs, (Y, dYf, dYl)):
+            o.copy_(src, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    h2d = Xp.numel() * 4 + Vp.numel() * 4
+    d2h = 3 * N_PTS * W * 4
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        extras["loss_grad"] = loss_grad_small(api, torch)
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    per_step_ms = step_ms / args.steps
+    work = N_PTS * N_PTS * W
+    value = world * work / (per_step_ms * 1e-3)
+    peaks = _peaks()
+    sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
+    kern_ms = prod_ms.value / max(1, prod_n.value)
+    flops_per_launch = N_PTS * N_PTS * (4 * W + 3 * D + 6)
+    achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
+    peak = 2 * 128 * 152 * sm_mhz * 1e6 / 1e12
+    tr = _traffic().get("kmv_simt_matern_d3_w32_grad")
+    roofline = {"bound": "alu", "kernel": "kmv_simt_kernel<MATERN32,grad,D=3,TW=32>",
+                "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": tr.get("bytes_per_launch") if tr else None,
+                "peak_source": f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median "
+                               "sampled SM clock in the timed region)",
+                "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops_per_launch,
+                "kernel_share_of_step": kern_ms / per_step_ms}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = cpu_oracle_rate()
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write outside "
+                                                   "the timed bracket)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
+            "roofline": roofline, "cpu_baseline": cpu,
+            "e2e": {"value": world * work / (e2e_ms * 1e-3), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
+            "gpu_launches": int(launches.value), "clocks": clocks}
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,289 @@
+/*
+ * gp.h -- C ABI of libgp.so: on-the-fly Gaussian-process kernel products and the
+ * GP training loss on one GB300 (sm_103a).
+ *
+ * Problem statement (HiGP, arXiv 2503.02259, §Gaussian Processes): training points
+ * X in R^{n x d}, observations y in R^n, test points X* in R^{m x d}, and
+ * hyper-parameters Theta = (s, f, l): noise s, scale f, length-scale l.  The
+ * regularised kernel matrix is read as
+ *
+ *     Kh = f^2 K_l + s I,     K_l[i][j] = k(|x_i - x_j|; l),
+ *
+ * with k the Gaussian kernel exp(-r^2/(2 l^2)) or the Matern-3/2 kernel
+ * (1 + sqrt(3) r/l) exp(-sqrt(3) r/l).  Kh is never stored: every product
+ * evaluates kernel tiles on the fly and discards them (§Statement of Need).
+ *
+ * Conventions shared by every call
+ *  - Memory: arrays named X, V, Y, B, Xsol, y, alpha, Xstar, mu, Z and probes
+ *    are DEVICE pointers (cudaMalloc'ed or from a device tensor) of float32,
+ *    row-major, densely packed (leading dimension = number of columns).
+ *    Scalar outputs (loss, grad, iters, relres, logdet, info) are HOST pointers.
+ *  - Ownership: the caller owns every buffer.  No call allocates device memory;
+ *    calls that need scratch take a caller-provided workspace `ws` of at least
+ *    gp_workspace_bytes(op, ...) bytes, 256-byte aligned.  The workspace is
+ *    scratch only: its contents on entry are ignored.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  gp_kernel_matmul, gp_kernel_grad_matmul, gp_predict_mean and
+ *    gp_generate_probes are asynchronous on `stream`.  Calls with host scalar
+ *    outputs synchronise `stream` before returning.
+ *  - Errors: every call returns a gp_status; no exceptions cross the ABI.
+ *    Outputs are valid only on GP_OK, except that iters/relres are also written
+ *    on GP_ERR_NOT_CONVERGED.  gp_last_error() returns a thread-local message
+ *    describing the last non-OK status of the calling thread.
+ *  - Argument checks (GP_ERR_ARG): n >= 1, 1 <= d <= GP_MAX_DIM,
+ *    1 <= w <= GP_MAX_COLS, s > 0, f > 0, l > 0, non-NULL device pointers,
+ *    kernel in {GAUSSIAN, MATERN32}.
+ *  - Statelessness (§Design and Implementation: the interfaces are stateless):
+ *    no call keeps state between calls except the thread-local error string
+ *    and per-device launch-configuration caches.
+ */
+#ifndef GP_H
+#define GP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GP_MAX_DIM 16     /* largest supported point dimension d */
+#define GP_MAX_COLS 128   /* largest multivector width w per product */
+#define GP_MAX_LANCZOS 64 /* largest number of Lanczos steps k for SLQ */
+
+typedef enum {
+  GP_OK = 0,
+  GP_ERR_ARG = 1,            /* invalid argument (message in gp_last_error) */
+  GP_ERR_CUDA = 2,           /* a CUDA runtime call or kernel launch failed */
+  GP_ERR_OOM = 3,            /* workspace too small / server admission refused */
+  GP_ERR_NOT_CONVERGED = 4,  /* CG hit cg_maxit before cg_rtol */
+  GP_ERR_BREAKDOWN = 5,      /* CG breakdown: p^T Kh p <= 0 or non-finite */
+  GP_ERR_TIMEOUT = 6,        /* a bounded device-side wait gave up */
+  GP_ERR_UNIMPLEMENTED = 7,  /* combination not built (e.g. precision/kernel) */
+  GP_ERR_NUMERIC = 8         /* non-finite or non-positive Lanczos eigenvalue */
+} gp_status;
+
+typedef enum { GP_KERNEL_GAUSSIAN = 0, GP_KERNEL_MATERN32 = 1 } gp_kernel;
+
+/* Arithmetic of the K-tile x V-tile contraction.  FP32: CUDA-core FP32 FMA.
+ * TF32 / BF16: tcgen05 tensor cores with operands rounded to that type and FP32
+ * accumulation in tensor memory. */
+typedef enum { GP_PREC_FP32 = 0, GP_PREC_TF32 = 1, GP_PREC_BF16 = 2 } gp_precision;
+
+typedef enum {
+  GP_OP_MATMUL = 0,       /* gp_kernel_matmul */
+  GP_OP_GRAD_MATMUL = 1,  /* gp_kernel_grad_matmul */
+  GP_OP_PCG = 2,          /* gp_pcg_solve */
+  GP_OP_SLQ = 3,          /* gp_slq_logdet */
+  GP_OP_LOSS_GRAD = 4,    /* gp_loss_and_grad, gp_nll_forward, gp_nll_backward */
+  GP_OP_PREDICT = 5       /* gp_predict_mean */
+} gp_op;
+
+/* Theta = (s, f, l): noise s, scale f, length-scale l (§Gaussian Processes). */
+typedef struct {
+  double s, f, l;
+} gp_theta;
+
+/* X: device, n x d row-major float32 training points. kernel: a gp_kernel. */
+typedef struct {
+  const float* X;
+  int64_t n;
+  int32_t d;
+  int32_t kernel;
+  gp_theta theta;
+} gp_problem;
+
+/* Options of the iterative solvers.
+ *  nprobe:     Rademacher probes p for SLQ and Hutchinson (0 <= p < GP_MAX_COLS).
+ *  nlanczos:   Lanczos steps k per probe (1 <= k <= GP_MAX_LANCZOS).
+ *  cg_maxit:   CG iteration cap (<= 0: n).
+ *  cg_rtol:    per-column stop at ||b - Kh x||_2 / ||b||_2 <= cg_rtol (recurrence
+ *              residual, FP64 norms).
+ *  refine_rtol: outer tolerance of mixed-precision iterative refinement (used
+ *              when prec != FP32; <= 0 disables refinement).
+ *  seed:       probe seed; probe (row i, column c) = +1 if the top bit of
+ *              SplitMix64(seed ^ (c << 40) ^ i) is 0, else -1.
+ *  prec:       contraction precision of the inner products (gp_precision).
+ *  probes:     optional device n x nprobe float32 probe block; NULL = generated
+ *              from `seed` by the rule above.
+ *  refine_maxit: cap on outer refinement steps (<= 0: 10). */
+typedef struct {
+  int32_t nprobe;
+  int32_t nlanczos;
+  int32_t cg_maxit;
+  int32_t prec;
+  double cg_rtol;
+  double refine_rtol;
+  uint64_t seed;
+  const float* probes;
+  int32_t refine_maxit;
+  int32_t reserved;
+} gp_solve_opts;
+
+/* Diagnostics of one loss/gradient evaluation (host struct, filled on GP_OK). */
+typedef struct {
+  double yalpha;           /* y^T Kh^-1 y */
+  double logdet;           /* SLQ estimate of log|Kh| (Eq. 1, M = I) */
+  double logdet_stderr;    /* standard error of the probe mean */
+  double quad[3];          /* alpha^T dKh/dtheta alpha, theta = s, f, l */
+  double trace[3];         /* Hutchinson tr(Kh^-1 dKh/dtheta) (Eq. 2, M = I) */
+  double trace_stderr[3];
+  int32_t cg_iters;        /* largest CG iteration count over the columns */
+  int32_t refine_steps;    /* outer refinement steps taken (0 for FP32) */
+  double relres_y;         /* final recurrence relres of the y column */
+  double relres_max;       /* largest final relres over all columns */
+} gp_loss_info;
+
+/* Library version string (static storage). */
+const char* gp_version(void);
+/* Thread-local message of the calling thread's last non-OK status ("" if none). */
+const char* gp_last_error(void);
+/* Static name of a status code. */
+const char* gp_status_string(gp_status st);
+
+/* Workspace bytes needed by `op` for this problem.  w is the multivector width
+ * for MATMUL / GRAD_MATMUL / PCG (ignored otherwise); opts may be NULL for the
+ * matmul ops.  For PREDICT, w is the number of test points m.  Returns 0 on an
+ * invalid argument (see gp_last_error). */
+size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_solve_opts* opts);
+
+/* Y = Kh V  (the on-the-fly MatVec, §Statement of Need).
+ * V, Y: device n x w float32 (may not alias).  prec selects the contraction
+ * arithmetic.  Asynchronous on `stream`. */
+gp_status gp_kernel_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y,
+                           int32_t prec, void* ws, size_t ws_bytes, void* stream);
+
+/* Fused product of Kh and its derivatives with one multivector, sharing one
+ * distance/kernel evaluation per entry (the "kernel matrices and its
+ * derivatives" of §Design and Implementation):
+ *   Y = Kh V,  dY_f = (dKh/df) V = 2 f K V,  dY_l = (dKh/dl) V = f^2 D_l V,
+ * and (dKh/ds) V = V, which is not written.  dY_f or dY_l may be NULL to skip.
+ * Asynchronous on `stream`. */
+gp_status gp_kernel_grad_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y,
+                                float* dY_f, float* dY_l, int32_t prec, void* ws,
+                                size_t ws_bytes, void* stream);
+
+/* Column-wise CG for Kh Xsol = B from Xsol = 0 (PCG of §Gaussian Processes with
+ * M = I).  B, Xsol: device n x w.  iters[w], relres[w]: host outputs (iterations
+ * and final recurrence relres per column).  Stops each column at opts->cg_rtol
+ * or opts->cg_maxit.  With opts->prec != FP32 and refine_rtol > 0 the inner
+ * products run on tensor cores and an outer FP32-compensated residual loop
+ * refines Xsol until ||B - Kh Xsol|| / ||B|| <= refine_rtol per column.
+ * Returns GP_ERR_NOT_CONVERGED (with iters/relres/Xsol written) if a column
+ * misses its tolerance.  Synchronises `stream`. */
+gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol,
+                       const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
+                       size_t ws_bytes, void* stream);
+
+/* SLQ estimate of log|Kh| (Eq. 1 with M = I; stochastic Lanczos quadrature):
+ * the Lanczos tridiagonal T_k of each probe z_i is read off the first k CG
+ * step coefficients of the column z_i, eigen-decomposed on the device in FP64,
+ * and logdet = (1/p) sum_i ||z_i||^2 sum_j U_1j^2 log(lambda_j).
+ * logdet_stderr = sample std / sqrt(p).  Synchronises `stream`. */
+gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, double* logdet,
+                        double* logdet_stderr, void* ws, size_t ws_bytes, void* stream);
+
+/* L(Theta) = 1/2 (y^T Kh^-1 y + log|Kh| + n log 2 pi) and dL/d(s, f, l) =
+ * 1/2 (-alpha^T dKh alpha + tr(Kh^-1 dKh))   (§Gaussian Processes: the NLL and
+ * gradient equations; Eq. 1 and Eq. 2 with M = I).  One block CG on [y | Z],
+ * SLQ from the probe columns, and one fused derivative product with [alpha | Z].
+ * y: device n float32.  loss, grad[3] (s, f, l), info (may be NULL): host.
+ * Synchronises `stream`. */
+gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
+                           double* loss, double* grad, gp_loss_info* info, void* ws,
+                           size_t ws_bytes, void* stream);
+
+/* The forward half of gp_loss_and_grad: block CG on [y | Z] and SLQ.  Writes the
+ * solutions W = Kh^-1 [y | Z] to the device n x (1 + nprobe) array `W` (kept by
+ * the caller for the backward half) and the loss.  Synchronises `stream`. */
+gp_status gp_nll_forward(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
+                         float* W, double* loss, gp_loss_info* info, void* ws,
+                         size_t ws_bytes, void* stream);
+
+/* The backward half: from W of gp_nll_forward (same problem, same opts, so the
+ * same probes Z are regenerated rather than stored), one fused derivative
+ * product with [alpha | Z] gives grad[3] = dL/d(s, f, l).  Synchronises. */
+gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, const float* W,
+                          double* grad, gp_loss_info* info, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* Posterior mean mu = f^2 K(Xstar, X) alpha at m test points (noise-free test
+ * outputs, §Gaussian Processes; the prediction call of §Design and
+ * Implementation).  alpha: device n; Xstar: device m x d; mu: device m.
+ * Workspace: gp_workspace_bytes(GP_OP_PREDICT, prob, m, NULL).  Asynchronous. */
+gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const float* Xstar,
+                          int64_t m, float* mu, int32_t prec, void* ws, size_t ws_bytes,
+                          void* stream);
+
+/* Z[i][c] = +-1 (the probe rule of gp_solve_opts.seed) for i < n, c < p, into the
+ * device array Z with leading dimension ldz >= p.  Asynchronous. */
+gp_status gp_generate_probes(int64_t n, int32_t p, uint64_t seed, float* Z, int64_t ldz,
+                             void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper; used by the benchmark).
+ * Between gp_profile_begin and gp_profile_end on one host thread, the library
+ * records a CUDA event pair around every launch of the dominant on-the-fly
+ * product kernel on the caller's stream, and counts every kernel it launches.
+ * gp_profile_end synchronises those events and returns the summed device time
+ * of the product kernels (ms), their launch count and the total launch count.
+ * At most 65536 product launches are timed per window.
+ * ------------------------------------------------------------------------- */
+gp_status gp_profile_begin(void);
+gp_status gp_profile_end(double* product_ms, int64_t* product_launches, int64_t* total_launches);
+
+/* ---------------------------------------------------------------------------
+ * Serving: a continuous-batching request server on one device.
+ * Requests carry HOST arrays that are copied in at submit; the server owns its
+ * device memory, bounded by hbm_budget_bytes (admission by footprint).
+ * ------------------------------------------------------------------------- */
+typedef struct gp_server gp_server;
+
+typedef struct {
+  int32_t kind;            /* 0 = loss + gradient, 1 = posterior-mean prediction */
+  int32_t d;
+  int64_t n;
+  int32_t kernel;
+  int32_t nprobe;          /* probes for kind 0 */
+  gp_theta theta;
+  const float* X;          /* host n x d */
+  const float* y;          /* host n */
+  const float* Xstar;      /* host m x d (kind 1) */
+  int64_t m;
+  int32_t cg_maxit;        /* CG iteration budget */
+  int32_t nlanczos;
+  double cg_rtol;
+  uint64_t seed;
+  int32_t prec;
+  int32_t reserved;
+} gp_request;
+
+typedef struct {
+  gp_status status;
+  int32_t cg_iters;
+  double loss;
+  double grad[3];
+  double relres;
+  double t_submit_s;       /* server clock (seconds) at submit */
+  double t_start_s;        /* admitted to the device */
+  double t_done_s;         /* result ready */
+  float* mu;               /* caller's host buffer of m floats (kind 1), set before poll */
+} gp_result;
+
+/* Create a server on the current device with a device-memory budget and a
+ * maximum number of concurrently resident requests. */
+gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server** out);
+/* Queue a request (host arrays copied at submit); returns a ticket.
+ * GP_ERR_OOM if the request can never fit the budget. */
+gp_status gp_server_submit(gp_server* srv, const gp_request* req, uint64_t* ticket);
+/* Non-blocking: GP_OK and *res filled if the ticket is done (res->mu, if non-NULL,
+ * receives the prediction), GP_ERR_TIMEOUT if still pending. */
+gp_status gp_server_poll(gp_server* srv, uint64_t ticket, gp_result* res);
+/* Block until every submitted request is done or timeout_s elapses. */
+gp_status gp_server_drain(gp_server* srv, double timeout_s);
+gp_status gp_server_destroy(gp_server* srv);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GP_H */

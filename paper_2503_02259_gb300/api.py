@@ -1,0 +1,181 @@
+"""Python calls with the names of the C ABI, on torch CUDA tensors.
+
+Each function validates shapes, allocates its outputs and the library's
+workspace with torch on the input's device, and calls the C entry point on
+torch's current stream.  No arithmetic of the method happens here.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import byref, c_double, c_int32
+
+import torch
+
+from . import _binding as B
+from ._binding import check, lib
+
+
+def _stream(dev) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    return t.contiguous()
+
+
+def problem(X: torch.Tensor, kernel: int, theta) -> tuple[B.gp_problem, torch.Tensor]:
+    """gp_problem for device points X (n, d) float32 and theta = (s, f, l)."""
+    X = _f32(X, "X")
+    if X.dim() != 2:
+        raise ValueError("X must be (n, d)")
+    s, f, l = (float(v) for v in theta)
+    p = B.gp_problem(X.data_ptr(), X.shape[0], X.shape[1], int(kernel), B.gp_theta(s, f, l))
+    return p, X
+
+
+def solve_opts(nprobe: int = 0, nlanczos: int = 30, cg_maxit: int = 0, cg_rtol: float = 1e-8,
+               seed: int = 0, prec: int = B.PREC_FP32, refine_rtol: float = 0.0,
+               probes: torch.Tensor | None = None, refine_maxit: int = 0) -> B.gp_solve_opts:
+    return B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
+                           float(refine_rtol), int(seed) & (2**64 - 1),
+                           0 if probes is None else probes.data_ptr(), int(refine_maxit), 0)
+
+
+def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None, device) -> torch.Tensor:
+    nbytes = lib().gp_workspace_bytes(op, byref(prob), int(w), None if opts is None else byref(opts))
+    if nbytes == 0:
+        raise B.GPError(B.GP_ERR_ARG, "gp_workspace_bytes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=device)
+    if ws.data_ptr() % 256:
+        raise RuntimeError("workspace allocation is not 256-byte aligned")
+    return ws
+
+
+def gp_kernel_matmul(X, V, kernel, theta, prec=B.PREC_FP32, ws=None) -> torch.Tensor:
+    """Y = Kh V on the device."""
+    prob, X = problem(X, kernel, theta)
+    V = _f32(V, "V")
+    if V.dim() == 1:
+        V = V[:, None]
+    n, w = V.shape
+    if n != X.shape[0]:
+        raise ValueError("V must have n rows")
+    Y = torch.empty_like(V)
+    if ws is None:
+        ws = workspace(B.OP_MATMUL, prob, w, B.gp_solve_opts(prec=prec) if prec else None, X.device)
+    check(lib().gp_kernel_matmul(byref(prob), _ptr(V), w, _ptr(Y), int(prec), _ptr(ws), ws.numel(),
+                                 _stream(X.device)), "gp_kernel_matmul")
+    return Y
+
+
+def gp_kernel_grad_matmul(X, V, kernel, theta, ws=None):
+    """(Kh V, dKh/df V, dKh/dl V) from one fused pass (dKh/ds V = V)."""
+    prob, X = problem(X, kernel, theta)
+    V = _f32(V, "V")
+    if V.dim() == 1:
+        V = V[:, None]
+    n, w = V.shape
+    Y = torch.empty_like(V)
+    dYf = torch.empty_like(V)
+    dYl = torch.empty_like(V)
+    if ws is None:
+        ws = workspace(B.OP_GRAD_MATMUL, prob, w, None, X.device)
+    check(lib().gp_kernel_grad_matmul(byref(prob), _ptr(V), w, _ptr(Y), _ptr(dYf), _ptr(dYl),
+                                      B.PREC_FP32, _ptr(ws), ws.numel(), _stream(X.device)),
+          "gp_kernel_grad_matmul")
+    return Y, dYf, dYl
+
+
+def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True):
+    """Column-wise CG: returns (Xsol, iters (w,), relres (w,), status)."""
+    prob, X = problem(X, kernel, theta)
+    Bm = _f32(Bm, "B")
+    if Bm.dim() == 1:
+        Bm = Bm[:, None]
+    n, w = Bm.shape
+    Xsol = torch.empty_like(Bm)
+    iters = (c_int32 * w)()
+    relres = (c_double * w)()
+    ws = workspace(B.OP_PCG, prob, w, opts, X.device)
+    st = lib().gp_pcg_solve(byref(prob), _ptr(Bm), w, _ptr(Xsol), byref(opts), iters, relres,
+                            _ptr(ws), ws.numel(), _stream(X.device))
+    if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
+        check(st, "gp_pcg_solve")
+    return Xsol, list(iters), list(relres), st
+
+
+def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts):
+    prob, X = problem(X, kernel, theta)
+    ld = c_double()
+    se = c_double()
+    ws = workspace(B.OP_SLQ, prob, 0, opts, X.device)
+    check(lib().gp_slq_logdet(byref(prob), byref(opts), byref(ld), byref(se), _ptr(ws), ws.numel(),
+                              _stream(X.device)), "gp_slq_logdet")
+    return ld.value, se.value
+
+
+def gp_loss_and_grad(X, y, kernel, theta, opts: B.gp_solve_opts, ws=None):
+    """(loss, [dL/ds, dL/df, dL/dl], info dict)."""
+    prob, X = problem(X, kernel, theta)
+    y = _f32(y, "y").reshape(-1)
+    loss = c_double()
+    grad = (c_double * 3)()
+    info = B.gp_loss_info()
+    if ws is None:
+        ws = workspace(B.OP_LOSS_GRAD, prob, 0, opts, X.device)
+    check(lib().gp_loss_and_grad(byref(prob), _ptr(y), byref(opts), byref(loss), grad, byref(info),
+                                 _ptr(ws), ws.numel(), _stream(X.device)), "gp_loss_and_grad")
+    return loss.value, list(grad), info.as_dict()
+
+
+def gp_nll_forward(X, y, kernel, theta, opts: B.gp_solve_opts):
+    """(loss, W = Kh^-1 [y | Z] (n, 1 + p), info)."""
+    prob, X = problem(X, kernel, theta)
+    y = _f32(y, "y").reshape(-1)
+    W = torch.empty((X.shape[0], 1 + opts.nprobe), dtype=torch.float32, device=X.device)
+    loss = c_double()
+    info = B.gp_loss_info()
+    ws = workspace(B.OP_LOSS_GRAD, prob, 0, opts, X.device)
+    check(lib().gp_nll_forward(byref(prob), _ptr(y), byref(opts), _ptr(W), byref(loss), byref(info),
+                               _ptr(ws), ws.numel(), _stream(X.device)), "gp_nll_forward")
+    return loss.value, W, info.as_dict()
+
+
+def gp_nll_backward(X, W, kernel, theta, opts: B.gp_solve_opts):
+    """[dL/ds, dL/df, dL/dl] from the forward's W (probes regenerated, not stored)."""
+    prob, X = problem(X, kernel, theta)
+    W = _f32(W, "W")
+    grad = (c_double * 3)()
+    info = B.gp_loss_info()
+    ws = workspace(B.OP_LOSS_GRAD, prob, 0, opts, X.device)
+    check(lib().gp_nll_backward(byref(prob), byref(opts), _ptr(W), grad, byref(info), _ptr(ws),
+                                ws.numel(), _stream(X.device)), "gp_nll_backward")
+    return list(grad), info.as_dict()
+
+
+def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32):
+    """mu = f^2 K(X*, X) alpha."""
+    prob, X = problem(X, kernel, theta)
+    alpha = _f32(alpha, "alpha").reshape(-1)
+    Xstar = _f32(Xstar, "Xstar")
+    m = Xstar.shape[0]
+    mu = torch.empty(m, dtype=torch.float32, device=X.device)
+    ws = workspace(B.OP_PREDICT, prob, m, None, X.device)
+    check(lib().gp_predict_mean(byref(prob), _ptr(alpha), _ptr(Xstar), m, _ptr(mu), int(prec),
+                                _ptr(ws), ws.numel(), _stream(X.device)), "gp_predict_mean")
+    return mu
+
+
+def gp_generate_probes(n: int, p: int, seed: int, device="cuda") -> torch.Tensor:
+    Z = torch.empty((n, p), dtype=torch.float32, device=device)
+    check(lib().gp_generate_probes(n, p, int(seed) & (2**64 - 1), _ptr(Z), p,
+                                   _stream(Z.device)), "gp_generate_probes")
+    return Z

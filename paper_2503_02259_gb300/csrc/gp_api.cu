@@ -1,0 +1,859 @@
+// C ABI of libgp.so (include/gp.h): argument checks, launch planning,
+// workspace carving and the host loop of the block CG.  Every arithmetic step
+// of the path runs in the kernels of kmv_simt.cuh / kmv_tc.cu / vec_kernels.cu;
+// this file only sequences them.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <utility>
+#include <vector>
+
+#include "gp_api_internal.h"
+#include "kmv_tc.cuh"
+#include "vec_kernels.cuh"
+
+namespace gp {
+
+// Per-(kernel, grad) instantiation units (kmv_simt_inst.cu).
+cudaError_t launch_simt_k0_g0(const SimtPlan&, const SimtArgs&, cudaStream_t);
+cudaError_t launch_simt_k0_g1(const SimtPlan&, const SimtArgs&, cudaStream_t);
+cudaError_t launch_simt_k1_g0(const SimtPlan&, const SimtArgs&, cudaStream_t);
+cudaError_t launch_simt_k1_g1(const SimtPlan&, const SimtArgs&, cudaStream_t);
+int occupancy_simt_k0_g0(int, int, int);
+int occupancy_simt_k0_g1(int, int, int);
+int occupancy_simt_k1_g0(int, int, int);
+int occupancy_simt_k1_g1(int, int, int);
+
+namespace {
+thread_local std::string t_err;
+
+// Measurement window state (per host thread).
+struct ProfileState {
+  bool on = false;
+  int64_t launches = 0;
+  int64_t product_launches = 0;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  size_t used = 0;
+};
+thread_local ProfileState t_prof;
+constexpr size_t kMaxProfiled = 65536;
+std::mutex g_mu;
+std::map<std::tuple<int, int, int, int, int, int>, int> g_occ;
+std::map<int, int> g_nsm;
+}  // namespace
+
+void set_error(const std::string& msg) { t_err = msg; }
+
+void count_launch() { ++t_prof.launches; }
+
+void profile_product_begin(cudaStream_t st) {
+  if (!t_prof.on) return;
+  ++t_prof.product_launches;
+  if (t_prof.used >= kMaxProfiled) return;
+  if (t_prof.used == t_prof.ev.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    t_prof.ev.emplace_back(a, b);
+  }
+  cudaEventRecord(t_prof.ev[t_prof.used].first, st);
+}
+
+void profile_product_end(cudaStream_t st) {
+  if (!t_prof.on || t_prof.used >= t_prof.ev.size()) return;
+  cudaEventRecord(t_prof.ev[t_prof.used].second, st);
+  ++t_prof.used;
+}
+const char* last_error_cstr() { return t_err.c_str(); }
+
+KernelConsts kernel_consts(int kernel, double l) {
+  KernelConsts k;
+  const double log2e = 1.4426950408889634;
+  if (kernel == GP_KERNEL_GAUSSIAN) {
+    k.cs = static_cast<float>(sqrt(log2e / 2.0) / l);
+    k.cD = 2.0 / (l * log2e);
+  } else {
+    k.cs = static_cast<float>(sqrt(3.0) / l);
+    k.cD = 1.0 / l;
+  }
+  return k;
+}
+
+int dim_template(int d) {
+  if (d <= 4) return d;
+  if (d <= 8) return 8;
+  return 16;
+}
+
+int dim_padded(int dt) { return dt <= 2 ? 2 : ((dt + 3) / 4) * 4; }
+
+int num_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = g_nsm.find(dev);
+  if (it != g_nsm.end()) return it->second;
+  int nsm = 0;
+  if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm <= 0)
+    nsm = 152;
+  g_nsm[dev] = nsm;
+  return nsm;
+}
+
+int simt_occupancy(int kernel, bool grad, int dt, int tw, int w_pad, int) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const auto key = std::make_tuple(dev, kernel, grad ? 1 : 0, dt, tw, w_pad);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_occ.find(key);
+    if (it != g_occ.end()) return it->second;
+  }
+  int occ = 1;
+  if (kernel == 0)
+    occ = grad ? occupancy_simt_k0_g1(dt, tw, w_pad) : occupancy_simt_k0_g0(dt, tw, w_pad);
+  else
+    occ = grad ? occupancy_simt_k1_g1(dt, tw, w_pad) : occupancy_simt_k1_g0(dt, tw, w_pad);
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_occ[key] = occ;
+  return occ;
+}
+
+static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+SimtPlan plan_simt(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel) {
+  SimtPlan p;
+  p.dt = dim_template(d);
+  p.dp = dim_padded(p.dt);
+  p.ng = w <= 32 ? 1 : (w <= 64 ? 2 : 4);
+  const int per = (w + p.ng - 1) / p.ng;
+  p.tw = static_cast<int>(round_up(per, 4));
+  p.w_pad = p.ng * p.tw;
+  p.bm = kBM / p.ng;
+  p.nr_pad = round_up(nr, kPad);
+  p.nc_pad = round_up(nc, kPad);
+  p.row_tiles = static_cast<int>(p.nr_pad / p.bm);
+  p.jtiles = static_cast<int>(p.nc_pad / kBN);
+  // Split the j range so that the CTAs spread evenly over the SMs: minimise
+  // (most CTAs on one SM) x (tiles per CTA + fixed cost), lightly penalising
+  // the extra partial-sum traffic of each split.
+  const int nsm = num_sms();
+  int best_s = 1;
+  double best = 1e300;
+  const int smax = std::min(p.jtiles, kMaxSplit);
+  for (int s = 1; s <= smax; ++s) {
+    const int jps = (p.jtiles + s - 1) / s;
+    const int s_eff = (p.jtiles + jps - 1) / jps;
+    if (s_eff != s) continue;
+    const int64_t units = static_cast<int64_t>(p.row_tiles) * s_eff;
+    const double per_sm = static_cast<double>((units + nsm - 1) / nsm);
+    const double cost = per_sm * (jps + 0.5) * (1.0 + 0.002 * s);
+    if (cost < best) {
+      best = cost;
+      best_s = s;
+    }
+  }
+  p.jt_per_split = (p.jtiles + best_s - 1) / best_s;
+  p.split = (p.jtiles + p.jt_per_split - 1) / p.jt_per_split;
+  (void)grad;
+  (void)kernel;
+  return p;
+}
+
+SimtPlan plan_for(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel, int prec) {
+  if (prec == GP_PREC_FP32) return plan_simt(nr, nc, d, w, grad, kernel);
+  return plan_tc(nr, nc, d, w, kernel, prec);
+}
+
+cudaError_t launch_simt(const SimtPlan& p, int kernel, bool grad, const SimtArgs& a,
+                        cudaStream_t st) {
+  if (kernel == 0) return grad ? launch_simt_k0_g1(p, a, st) : launch_simt_k0_g0(p, a, st);
+  return grad ? launch_simt_k1_g1(p, a, st) : launch_simt_k1_g0(p, a, st);
+}
+
+// ---------------------------------------------------------------------------
+// Workspace carving: a bump allocator over the caller's buffer (256-B aligned).
+// ---------------------------------------------------------------------------
+struct Carve {
+  char* base;
+  size_t off = 0;
+  explicit Carve(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+// Layout of the product workspace (matmul / grad matmul / predict).
+struct ProdWs {
+  float* xr;      // row points (== xc for a square product)
+  float* xc;
+  float* vp;
+  float* part_k;
+  float* part_d;
+  int* err;
+  size_t bytes;
+};
+
+static ProdWs carve_product(void* ws, const SimtPlan& p, bool grad, bool rect) {
+  Carve c(ws);
+  ProdWs w;
+  w.xc = c.take<float>(static_cast<size_t>(p.nc_pad) * p.dp);
+  w.xr = rect ? c.take<float>(static_cast<size_t>(p.nr_pad) * p.dp) : w.xc;
+  w.vp = c.take<float>(static_cast<size_t>(p.nc_pad) * p.w_pad);
+  w.part_k = c.take<float>(static_cast<size_t>(p.split) * p.nr_pad * p.w_pad);
+  w.part_d = grad ? c.take<float>(static_cast<size_t>(p.split) * p.nr_pad * p.w_pad) : nullptr;
+  w.err = c.take<int>(64);
+  w.bytes = c.off + 256;
+  return w;
+}
+
+// Layout of the solver workspace (pcg / slq / loss).
+struct SolveWs {
+  float* xs;
+  float* B;
+  float* X;
+  float* R;
+  float* P;
+  float* Q;
+  float* part;     // max(split_cg, 2 * split_grad) planes
+  double* red;
+  CgState* S;
+  size_t bytes;
+};
+
+static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, bool with_grad) {
+  Carve c(ws);
+  SolveWs w;
+  const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
+  w.xs = c.take<float>(static_cast<size_t>(pc.nc_pad) * pc.dp);
+  w.B = c.take<float>(plane);
+  w.X = c.take<float>(plane);
+  w.R = c.take<float>(plane);
+  w.P = c.take<float>(plane);
+  w.Q = c.take<float>(plane);
+  const size_t planes = std::max<size_t>(pc.split, with_grad ? 2 * static_cast<size_t>(pg.split) : 0);
+  w.part = c.take<float>(planes * plane);
+  w.red = c.take<double>(3 * static_cast<size_t>(red_blocks(pc.nr_pad)) * pc.w_pad);
+  w.S = c.take<CgState>(1);
+  w.bytes = c.off + 256;
+  return w;
+}
+
+}  // namespace gp
+
+using namespace gp;
+
+// ---------------------------------------------------------------------------
+// Argument checks.
+// ---------------------------------------------------------------------------
+static gp_status fail(gp_status st, const std::string& msg) {
+  set_error(msg);
+  return st;
+}
+
+static gp_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(GP_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define GP_CUDA(call)                              \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+static gp_status check_problem(const gp_problem* prob) {
+  if (prob == nullptr) return fail(GP_ERR_ARG, "problem is NULL");
+  if (prob->X == nullptr) return fail(GP_ERR_ARG, "problem->X is NULL");
+  if (prob->n < 1) return fail(GP_ERR_ARG, "n must be >= 1");
+  if (prob->d < 1 || prob->d > GP_MAX_DIM) return fail(GP_ERR_ARG, "d must be in [1, 16]");
+  if (prob->kernel != GP_KERNEL_GAUSSIAN && prob->kernel != GP_KERNEL_MATERN32)
+    return fail(GP_ERR_ARG, "unknown kernel");
+  const gp_theta& t = prob->theta;
+  if (!(t.s > 0) || !(t.f > 0) || !(t.l > 0) || !isfinite(t.s) || !isfinite(t.f) || !isfinite(t.l))
+    return fail(GP_ERR_ARG, "theta: s, f, l must be finite and > 0");
+  if (prob->n > (int64_t(1) << 31) - 4096) return fail(GP_ERR_ARG, "n too large");
+  return GP_OK;
+}
+
+static gp_status check_width(int32_t w) {
+  if (w < 1 || w > GP_MAX_COLS) return fail(GP_ERR_ARG, "w must be in [1, 128]");
+  return GP_OK;
+}
+
+static gp_status check_opts(const gp_solve_opts* o, bool need_probes) {
+  if (o == nullptr) return fail(GP_ERR_ARG, "opts is NULL");
+  if (o->nprobe < 0 || o->nprobe + 1 > GP_MAX_COLS) return fail(GP_ERR_ARG, "nprobe must be in [0, 127]");
+  if (need_probes && o->nprobe < 1) return fail(GP_ERR_ARG, "nprobe must be >= 1");
+  if (o->nlanczos < 1 || o->nlanczos > GP_MAX_LANCZOS)
+    return fail(GP_ERR_ARG, "nlanczos must be in [1, 64]");
+  if (!(o->cg_rtol >= 0)) return fail(GP_ERR_ARG, "cg_rtol must be >= 0");
+  if (o->prec != GP_PREC_FP32 && o->prec != GP_PREC_TF32 && o->prec != GP_PREC_BF16)
+    return fail(GP_ERR_ARG, "unknown precision");
+  return GP_OK;
+}
+
+static gp_status check_prec(int32_t prec) {
+  if (prec != GP_PREC_FP32 && prec != GP_PREC_TF32 && prec != GP_PREC_BF16)
+    return fail(GP_ERR_ARG, "unknown precision");
+  return GP_OK;
+}
+
+static gp_status check_ws(void* ws, size_t have, size_t need) {
+  if (ws == nullptr) return fail(GP_ERR_ARG, "workspace is NULL");
+  if ((reinterpret_cast<uintptr_t>(ws) & 255) != 0)
+    return fail(GP_ERR_ARG, "workspace must be 256-byte aligned");
+  if (have < need)
+    return fail(GP_ERR_OOM, "workspace too small: need " + std::to_string(need) + " bytes, have " +
+                                std::to_string(have));
+  return GP_OK;
+}
+
+static gp_status device_status(const int* err_dev, cudaStream_t st) {
+  int h = 0;
+  GP_CUDA(cudaMemcpyAsync(&h, err_dev, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  if (h == kDevTimeout) return fail(GP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h == kDevBreakdown) return fail(GP_ERR_BREAKDOWN, "CG breakdown (p^T Kh p <= 0 or non-finite)");
+  if (h == kDevNumeric) return fail(GP_ERR_NUMERIC, "non-positive Lanczos eigenvalue");
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Products.
+// ---------------------------------------------------------------------------
+namespace gp {
+
+// One fused product Kh-sums of V into part_k / part_d (square, points staged).
+gp_status run_product(const SimtPlan& p, int kernel, bool grad, int prec, const float* xr,
+                      const float* xc, const float* vp, float* part_k, float* part_d,
+                      const int* active, int* err, cudaStream_t st) {
+  if (prec != GP_PREC_FP32) {
+    TcArgs ta{xr, xc, vp, part_k, part_d, active, err};
+    profile_product_begin(st);
+    cudaError_t e = launch_tc(p, kernel, grad, prec, ta, st);
+    profile_product_end(st);
+    if (e == cudaErrorNotSupported)
+      return fail(GP_ERR_UNIMPLEMENTED, "tensor-core path not available for this shape");
+    if (e != cudaSuccess) return cuda_fail(e, "launch_tc");
+    return GP_OK;
+  }
+  SimtArgs a{xr, xc, vp, part_k, part_d, active, err};
+  profile_product_begin(st);
+  cudaError_t e = launch_simt(p, kernel, grad, a, st);
+  profile_product_end(st);
+  if (e != cudaSuccess) return cuda_fail(e, "launch_simt");
+  return GP_OK;
+}
+
+}  // namespace gp
+
+static gp_status product_call(const gp_problem* prob, const float* V, int32_t w, float* Y,
+                              float* dYf, float* dYl, bool grad, int32_t prec, void* ws,
+                              size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if ((s = check_prec(prec)) != GP_OK) return s;
+  if (V == nullptr || Y == nullptr) return fail(GP_ERR_ARG, "V and Y must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  const SimtPlan p = plan_for(n, n, prob->d, w, grad, prob->kernel, prec);
+  ProdWs L = carve_product(nullptr, p, grad, false);
+  if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
+  L = carve_product(ws, p, grad, false);
+  const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
+  GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
+  if (w != p.w_pad) GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
+  GP_CUDA(launch_pad_block(V, n, w, w, L.vp, p.nc_pad, p.w_pad, 0, st));
+  if ((s = run_product(p, prob->kernel, grad, prec, L.xc, L.xc, L.vp, L.part_k, L.part_d, nullptr,
+                       L.err, st)) != GP_OK)
+    return s;
+  const double f = prob->theta.f;
+  EpiArgs e{};
+  e.part_k = L.part_k;
+  e.part_d = L.part_d;
+  e.split = p.split;
+  e.nr_pad = p.nr_pad;
+  e.w_pad = p.w_pad;
+  e.v = L.vp;
+  e.n = n;
+  e.w = w;
+  e.cK = f * f;
+  e.cV = prob->theta.s;
+  e.cF = 2.0 * f;
+  e.cL = f * f * kc.cD;
+  e.y = Y;
+  e.ldy = w;
+  e.dyf = grad ? dYf : nullptr;
+  e.ldf = w;
+  e.dyl = grad ? dYl : nullptr;
+  e.ldl = w;
+  e.err = L.err;
+  GP_CUDA(launch_epilogue(e, st));
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Block CG host loop.
+// ---------------------------------------------------------------------------
+namespace gp {
+
+gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W, int w, int maxit,
+                 double rtol, cudaStream_t st) {
+  const int64_t n = prob->n;
+  const double f2 = prob->theta.f * prob->theta.f;
+  GP_CUDA(launch_cg_init(W.S, W.B, W.X, W.R, W.P, p.nr_pad, p.w_pad, w, maxit, rtol, W.red, st));
+  int chunk = 4;
+  int issued = 0;
+  struct {
+    int n_active;
+    int err;
+  } h{1, 0};
+  while (issued < maxit) {
+    const int todo = std::min(chunk, maxit - issued);
+    for (int k = 0; k < todo; ++k) {
+      gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.part, nullptr,
+                                &W.S->n_active, &W.S->err, st);
+      if (s != GP_OK) return s;
+      GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
+                                  prob->theta.s, W.red, st));
+      GP_CUDA(launch_cg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
+      GP_CUDA(launch_cg_pupdate(W.S, W.R, W.P, p.nr_pad, p.w_pad, st));
+    }
+    issued += todo;
+    GP_CUDA(cudaMemcpyAsync(&h, W.S, sizeof(h), cudaMemcpyDeviceToHost, st));
+    GP_CUDA(cudaStreamSynchronize(st));
+    if (h.n_active == 0 || h.err != 0) break;
+    if (chunk < 32) chunk *= 2;
+  }
+  if (h.err == kDevTimeout) return fail(GP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (h.err == kDevBreakdown) return fail(GP_ERR_BREAKDOWN, "CG breakdown (p^T Kh p <= 0 or non-finite)");
+  return GP_OK;
+}
+
+}  // namespace gp
+
+struct HostCg {
+  int iters[kMaxW];
+  double relres[kMaxW];
+};
+
+static gp_status read_cg(const CgState* S, HostCg& h, cudaStream_t st) {
+  GP_CUDA(cudaMemcpyAsync(h.iters, S->iters, sizeof(h.iters), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaMemcpyAsync(h.relres, S->relres, sizeof(h.relres), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  return GP_OK;
+}
+
+// Common set-up of the solver calls: stage points, build B = [y | Z] (or B = user).
+struct SolveSetup {
+  SimtPlan pc, pg;
+  SolveWs W;
+  KernelConsts kc;
+};
+
+static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, void* ws,
+                             size_t ws_bytes, cudaStream_t st, SolveSetup& out) {
+  gp_status s;
+  const int64_t n = prob->n;
+  out.pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+  out.pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
+  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad);
+  if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
+  out.W = carve_solve(ws, out.pc, out.pg, with_grad);
+  out.kc = kernel_consts(prob->kernel, prob->theta.l);
+  GP_CUDA(cudaMemsetAsync(out.W.S, 0, sizeof(CgState), st));
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.cs, out.pc.dp,
+                              out.pc.nc_pad, out.W.xs, st));
+  GP_CUDA(cudaMemsetAsync(out.W.B, 0, sizeof(float) * out.pc.nr_pad * out.pc.w_pad, st));
+  return GP_OK;
+}
+
+static gp_status fill_probes(const gp_problem* prob, const gp_solve_opts* o, float* B, int64_t n_pad,
+                             int w_pad, int col_off, cudaStream_t st) {
+  if (o->nprobe <= 0) return GP_OK;
+  if (o->probes != nullptr) {
+    GP_CUDA(launch_pad_block(o->probes, prob->n, o->nprobe, o->nprobe, B, n_pad, w_pad, col_off, st));
+  } else {
+    GP_CUDA(launch_probes(prob->n, o->nprobe, o->seed, B, w_pad, col_off, n_pad, st));
+  }
+  return GP_OK;
+}
+
+static int effective_maxit(const gp_problem* prob, const gp_solve_opts* o) {
+  int64_t m = o->cg_maxit > 0 ? o->cg_maxit : prob->n;
+  if (m > 1000000) m = 1000000;
+  return static_cast<int>(m);
+}
+
+// Forward: CG on [y | Z], SLQ, y^T alpha, loss assembly.  Leaves X = Kh^-1 B.
+static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_solve_opts* o,
+                              bool with_grad, void* ws, size_t ws_bytes, cudaStream_t st,
+                              SolveSetup& ss, gp_status& cg_status) {
+  gp_status s;
+  const int p = o->nprobe;
+  const int w = 1 + p;
+  if ((s = setup_solve(prob, w, with_grad, o->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  SolveWs& W = ss.W;
+  GP_CUDA(launch_pad_block(y, prob->n, 1, 1, W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  if ((s = fill_probes(prob, o, W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;
+  s = run_cg(prob, ss.pc, o->prec, W, w, effective_maxit(prob, o), o->cg_rtol, st);
+  if (s != GP_OK) return s;
+  GP_CUDA(launch_slq(W.S, 1, p, o->nlanczos, st));
+  GP_CUDA(launch_yalpha(W.S, W.B, W.X, ss.pc.nr_pad, ss.pc.w_pad, W.red, st));
+  GP_CUDA(launch_assemble(W.S, prob->n, p, st));
+  cg_status = GP_OK;
+  return GP_OK;
+}
+
+// Backward: fused product with V = [alpha | Z] against W = X; gradient assembly.
+static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, SolveSetup& ss,
+                               cudaStream_t st) {
+  gp_status s;
+  SolveWs& W = ss.W;
+  const int p = o->nprobe;
+  const int w = 1 + p;
+  const SimtPlan& pg = ss.pg;
+  // V = B with column 0 replaced by alpha (reuse Q as V).
+  GP_CUDA(cudaMemcpyAsync(W.Q, W.B, sizeof(float) * pg.nr_pad * pg.w_pad, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(launch_copy_col0(W.X, W.Q, pg.nr_pad, pg.w_pad, st));
+  float* part_k = W.part;
+  float* part_d = W.part + static_cast<size_t>(pg.split) * pg.nr_pad * pg.w_pad;
+  if ((s = run_product(pg, prob->kernel, true, GP_PREC_FP32, W.xs, W.xs, W.Q, part_k, part_d,
+                       nullptr, &W.S->err, st)) != GP_OK)
+    return s;
+  const double f = prob->theta.f;
+  GP_CUDA(launch_grad_dots(W.S, part_k, part_d, pg.split, W.Q, W.X, pg.nr_pad, pg.w_pad, w, 2.0 * f,
+                           f * f * ss.kc.cD, W.red, st));
+  GP_CUDA(launch_assemble(W.S, prob->n, p, st));
+  return GP_OK;
+}
+
+static gp_status read_outputs(const CgState* S, int w, double out[16], gp_loss_info* info,
+                              cudaStream_t st) {
+  HostCg h;
+  gp_status s;
+  if ((s = read_cg(S, h, st)) != GP_OK) return s;
+  GP_CUDA(cudaMemcpyAsync(out, S->out, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  int err = 0;
+  GP_CUDA(cudaMemcpyAsync(&err, &S->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  if (info != nullptr) {
+    info->yalpha = out[15];
+    info->logdet = out[0];
+    info->logdet_stderr = out[1];
+    for (int t = 0; t < 3; ++t) {
+      info->quad[t] = out[6 + t];
+      info->trace[t] = out[9 + t];
+      info->trace_stderr[t] = out[12 + t];
+    }
+    int mx = 0;
+    double rmax = 0.0;
+    for (int c = 0; c < w; ++c) {
+      mx = std::max(mx, h.iters[c]);
+      rmax = std::max(rmax, h.relres[c]);
+    }
+    info->cg_iters = mx;
+    info->refine_steps = 0;
+    info->relres_y = h.relres[0];
+    info->relres_max = rmax;
+  }
+  if (err == kDevTimeout) return fail(GP_ERR_TIMEOUT, "a bounded device wait gave up");
+  if (err == kDevBreakdown) return fail(GP_ERR_BREAKDOWN, "CG breakdown");
+  if (err == kDevNumeric) return fail(GP_ERR_NUMERIC, "non-positive Lanczos eigenvalue");
+  return GP_OK;
+}
+
+static gp_status check_conv(const CgState* S, int w, int maxit, double rtol, cudaStream_t st) {
+  HostCg h;
+  gp_status s;
+  if ((s = read_cg(S, h, st)) != GP_OK) return s;
+  for (int c = 0; c < w; ++c)
+    if (h.relres[c] > rtol && h.iters[c] >= maxit)
+      return fail(GP_ERR_NOT_CONVERGED, "CG reached cg_maxit before cg_rtol (column " +
+                                            std::to_string(c) + ", relres " +
+                                            std::to_string(h.relres[c]) + ")");
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Exported entry points.
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* gp_version(void) { return "libgp 0.1 (sm_103a)"; }
+
+const char* gp_last_error(void) { return last_error_cstr(); }
+
+const char* gp_status_string(gp_status st) {
+  switch (st) {
+    case GP_OK: return "GP_OK";
+    case GP_ERR_ARG: return "GP_ERR_ARG";
+    case GP_ERR_CUDA: return "GP_ERR_CUDA";
+    case GP_ERR_OOM: return "GP_ERR_OOM";
+    case GP_ERR_NOT_CONVERGED: return "GP_ERR_NOT_CONVERGED";
+    case GP_ERR_BREAKDOWN: return "GP_ERR_BREAKDOWN";
+    case GP_ERR_TIMEOUT: return "GP_ERR_TIMEOUT";
+    case GP_ERR_UNIMPLEMENTED: return "GP_ERR_UNIMPLEMENTED";
+    case GP_ERR_NUMERIC: return "GP_ERR_NUMERIC";
+  }
+  return "GP_ERR_UNKNOWN";
+}
+
+size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_solve_opts* opts) {
+  if (check_problem(prob) != GP_OK) return 0;
+  const int64_t n = prob->n;
+  const int prec = opts != nullptr ? opts->prec : GP_PREC_FP32;
+  switch (op) {
+    case GP_OP_MATMUL:
+    case GP_OP_GRAD_MATMUL: {
+      if (check_width(w) != GP_OK) return 0;
+      const bool grad = op == GP_OP_GRAD_MATMUL;
+      return carve_product(nullptr, plan_for(n, n, prob->d, w, grad, prob->kernel, prec), grad, false)
+          .bytes;
+    }
+    case GP_OP_PREDICT: {
+      if (w < 1) {
+        set_error("predict: m must be >= 1");
+        return 0;
+      }
+      return carve_product(nullptr, plan_for(w, n, prob->d, 1, false, prob->kernel, GP_PREC_FP32),
+                           false, true)
+          .bytes;
+    }
+    case GP_OP_PCG: {
+      if (check_width(w) != GP_OK) return 0;
+      const SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+      return carve_solve(nullptr, pc, pc, false).bytes;
+    }
+    case GP_OP_SLQ:
+    case GP_OP_LOSS_GRAD: {
+      if (check_opts(opts, op == GP_OP_SLQ) != GP_OK) return 0;
+      const int ww = op == GP_OP_SLQ ? opts->nprobe : 1 + opts->nprobe;
+      const SimtPlan pc = plan_for(n, n, prob->d, ww, false, prob->kernel, prec);
+      const SimtPlan pg = plan_for(n, n, prob->d, ww, true, prob->kernel, GP_PREC_FP32);
+      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD).bytes;
+    }
+  }
+  set_error("unknown op");
+  return 0;
+}
+
+gp_status gp_kernel_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y, int32_t prec,
+                           void* ws, size_t ws_bytes, void* stream) {
+  return product_call(prob, V, w, Y, nullptr, nullptr, false, prec, ws, ws_bytes, stream);
+}
+
+gp_status gp_kernel_grad_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y,
+                                float* dY_f, float* dY_l, int32_t prec, void* ws, size_t ws_bytes,
+                                void* stream) {
+  if (prec != GP_PREC_FP32 && (dY_f != nullptr || dY_l != nullptr)) {
+    // The tensor-core product carries the K tile only.
+    return fail(GP_ERR_UNIMPLEMENTED, "derivative products are FP32 only");
+  }
+  return product_call(prob, V, w, Y, dY_f, dY_l, true, prec, ws, ws_bytes, stream);
+}
+
+gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol,
+                       const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
+                       size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (B == nullptr || Xsol == nullptr) return fail(GP_ERR_ARG, "B and Xsol must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
+    return refine_solve(prob, B, w, Xsol, opts, iters, relres, ws, ws_bytes, st);
+  SolveSetup ss;
+  if ((s = setup_solve(prob, w, false, opts->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  const int maxit = effective_maxit(prob, opts);
+  s = run_cg(prob, ss.pc, opts->prec, ss.W, w, maxit, opts->cg_rtol, st);
+  if (s != GP_OK) return s;
+  GP_CUDA(launch_unpad_block(ss.W.X, prob->n, w, ss.pc.w_pad, Xsol, w, 0, st));
+  HostCg h;
+  if ((s = read_cg(ss.W.S, h, st)) != GP_OK) return s;
+  for (int c = 0; c < w; ++c) {
+    if (iters) iters[c] = h.iters[c];
+    if (relres) relres[c] = h.relres[c];
+  }
+  return check_conv(ss.W.S, w, maxit, opts->cg_rtol, st);
+}
+
+gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, double* logdet,
+                        double* logdet_stderr, void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_opts(opts, true)) != GP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int p = opts->nprobe;
+  SolveSetup ss;
+  if ((s = setup_solve(prob, p, false, opts->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st)) != GP_OK) return s;
+  // Only the first k CG steps enter the quadrature.
+  int maxit = std::min(effective_maxit(prob, opts), opts->nlanczos);
+  s = run_cg(prob, ss.pc, opts->prec, ss.W, p, maxit, opts->cg_rtol, st);
+  if (s != GP_OK) return s;
+  GP_CUDA(launch_slq(ss.W.S, 0, p, opts->nlanczos, st));
+  double out[16];
+  if ((s = read_outputs(ss.W.S, p, out, nullptr, st)) != GP_OK) return s;
+  if (logdet) *logdet = out[0];
+  if (logdet_stderr) *logdet_stderr = out[1];
+  return GP_OK;
+}
+
+gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
+                           double* loss, double* grad, gp_loss_info* info, void* ws, size_t ws_bytes,
+                           void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (y == nullptr) return fail(GP_ERR_ARG, "y is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SolveSetup ss;
+  gp_status cgs = GP_OK;
+  if ((s = forward_impl(prob, y, opts, true, ws, ws_bytes, st, ss, cgs)) != GP_OK) return s;
+  if ((s = backward_impl(prob, opts, ss, st)) != GP_OK) return s;
+  double out[16];
+  if ((s = read_outputs(ss.W.S, 1 + opts->nprobe, out, info, st)) != GP_OK) return s;
+  if (loss) *loss = out[2];
+  if (grad)
+    for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
+  return check_conv(ss.W.S, 1 + opts->nprobe, effective_maxit(prob, opts), opts->cg_rtol, st);
+}
+
+gp_status gp_nll_forward(const gp_problem* prob, const float* y, const gp_solve_opts* opts, float* W,
+                         double* loss, gp_loss_info* info, void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (y == nullptr || W == nullptr) return fail(GP_ERR_ARG, "y and W must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  SolveSetup ss;
+  gp_status cgs = GP_OK;
+  if ((s = forward_impl(prob, y, opts, true, ws, ws_bytes, st, ss, cgs)) != GP_OK) return s;
+  const int w = 1 + opts->nprobe;
+  GP_CUDA(launch_unpad_block(ss.W.X, prob->n, w, ss.pc.w_pad, W, w, 0, st));
+  double out[16];
+  if ((s = read_outputs(ss.W.S, w, out, info, st)) != GP_OK) return s;
+  if (loss) *loss = out[2];
+  return check_conv(ss.W.S, w, effective_maxit(prob, opts), opts->cg_rtol, st);
+}
+
+gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, const float* Wsol,
+                          double* grad, gp_loss_info* info, void* ws, size_t ws_bytes,
+                          void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (Wsol == nullptr) return fail(GP_ERR_ARG, "W is NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int w = 1 + opts->nprobe;
+  SolveSetup ss;
+  if ((s = setup_solve(prob, w, true, GP_PREC_FP32, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  // B = [alpha | Z] (alpha = column 0 of W), X = W.
+  GP_CUDA(launch_pad_block(Wsol, prob->n, 1, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;
+  GP_CUDA(cudaMemsetAsync(ss.W.X, 0, sizeof(float) * ss.pc.nr_pad * ss.pc.w_pad, st));
+  GP_CUDA(launch_pad_block(Wsol, prob->n, w, w, ss.W.X, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  if ((s = backward_impl(prob, opts, ss, st)) != GP_OK) return s;
+  double out[16];
+  GP_CUDA(cudaMemcpyAsync(out, ss.W.S->out, sizeof(out), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  if (grad)
+    for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
+  if (info != nullptr) {
+    for (int t = 0; t < 3; ++t) {
+      info->quad[t] = out[6 + t];
+      info->trace[t] = out[9 + t];
+      info->trace_stderr[t] = out[12 + t];
+    }
+  }
+  return device_status(&ss.W.S->err, st);
+}
+
+gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const float* Xstar, int64_t m,
+                          float* mu, int32_t prec, void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_prec(prec)) != GP_OK) return s;
+  if (alpha == nullptr || Xstar == nullptr || mu == nullptr)
+    return fail(GP_ERR_ARG, "alpha, Xstar and mu must be non-NULL");
+  if (m < 1 || m > (int64_t(1) << 31) - 4096) return fail(GP_ERR_ARG, "m out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  const SimtPlan p = plan_for(m, n, prob->d, 1, false, prob->kernel, GP_PREC_FP32);
+  ProdWs L = carve_product(nullptr, p, false, true);
+  if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
+  L = carve_product(ws, p, false, true);
+  const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
+  GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
+  GP_CUDA(launch_stage_points(Xstar, m, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nr_pad, L.xr, st));
+  GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
+  GP_CUDA(launch_pad_block(alpha, n, 1, 1, L.vp, p.nc_pad, p.w_pad, 0, st));
+  if ((s = run_product(p, prob->kernel, false, GP_PREC_FP32, L.xr, L.xc, L.vp, L.part_k, nullptr,
+                       nullptr, L.err, st)) != GP_OK)
+    return s;
+  EpiArgs e{};
+  e.part_k = L.part_k;
+  e.split = p.split;
+  e.nr_pad = p.nr_pad;
+  e.w_pad = p.w_pad;
+  e.n = m;
+  e.w = 1;
+  e.cK = prob->theta.f * prob->theta.f;
+  e.y = mu;
+  e.ldy = 1;
+  e.err = L.err;
+  GP_CUDA(launch_epilogue(e, st));
+  return GP_OK;
+}
+
+gp_status gp_profile_begin(void) {
+  t_prof.on = true;
+  t_prof.launches = 0;
+  t_prof.product_launches = 0;
+  t_prof.used = 0;
+  return GP_OK;
+}
+
+gp_status gp_profile_end(double* product_ms, int64_t* product_launches, int64_t* total_launches) {
+  double ms = 0.0;
+  for (size_t i = 0; i < t_prof.used; ++i) {
+    GP_CUDA(cudaEventSynchronize(t_prof.ev[i].second));
+    float e = 0.f;
+    GP_CUDA(cudaEventElapsedTime(&e, t_prof.ev[i].first, t_prof.ev[i].second));
+    ms += e;
+  }
+  if (product_ms) *product_ms = ms;
+  if (product_launches) *product_launches = t_prof.product_launches;
+  if (total_launches) *total_launches = t_prof.launches;
+  t_prof.on = false;
+  t_prof.used = 0;
+  return GP_OK;
+}
+
+gp_status gp_generate_probes(int64_t n, int32_t p, uint64_t seed, float* Z, int64_t ldz,
+                             void* stream) {
+  if (n < 1 || p < 1 || Z == nullptr || ldz < p) return fail(GP_ERR_ARG, "bad probe arguments");
+  GP_CUDA(launch_probes(n, p, seed, Z, ldz, 0, n, static_cast<cudaStream_t>(stream)));
+  return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,110 @@
+// Instantiations of the SIMT product for one (kernel family, grad) pair.
+// Compiled once per pair with -DGP_KIND=<0|1> -DGP_GRAD=<0|1> so that the
+// instantiations build in parallel translation units.
+#include <atomic>
+
+#include "kmv_simt.cuh"
+
+#ifndef GP_KIND
+#error "GP_KIND must be defined"
+#endif
+#ifndef GP_GRAD
+#error "GP_GRAD must be defined"
+#endif
+
+#define GP_CAT4(a, b, c, d) a##b##c##d
+#define GP_FN(prefix, k, g) GP_CAT4(prefix, k, _g, g)
+#define GP_LAUNCH GP_FN(launch_simt_k, GP_KIND, GP_GRAD)
+#define GP_OCC GP_FN(occupancy_simt_k, GP_KIND, GP_GRAD)
+
+namespace gp {
+
+namespace {
+
+constexpr size_t kMaxDynSmem = 160 * 1024;
+
+template <int DT, int TW>
+auto kernel_ptr() {
+  return kmv_simt_kernel<GP_KIND, (GP_GRAD != 0), DT, TW>;
+}
+
+// Raise the dynamic shared-memory cap once per device and instantiation.
+template <int DT, int TW>
+cudaError_t ensure_attr() {
+  static std::atomic<uint64_t> done{0};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = 1ull << (dev & 63);
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel_ptr<DT, TW>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(kMaxDynSmem));
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
+}
+
+template <int DT, int TW>
+cudaError_t launch_one(const SimtPlan& p, const SimtArgs& a, cudaStream_t st) {
+  cudaError_t e = ensure_attr<DT, TW>();
+  if (e != cudaSuccess) return e;
+  const size_t smem = simt_smem_bytes(DimTraits<DT>::DP, p.w_pad);
+  dim3 grid(p.row_tiles, p.split);
+  auto fn = kernel_ptr<DT, TW>();
+  fn<<<grid, kThreads, smem, st>>>(a, p.w_pad, p.ng, p.nr_pad, p.jtiles, p.jt_per_split);
+  count_launch();
+  return cudaGetLastError();
+}
+
+template <int DT, int TW>
+int occ_one(int w_pad) {
+  if (ensure_attr<DT, TW>() != cudaSuccess) return 1;
+  int nb = 0;
+  const size_t smem = simt_smem_bytes(DimTraits<DT>::DP, w_pad);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel_ptr<DT, TW>(), kThreads, smem) !=
+      cudaSuccess)
+    return 1;
+  return nb > 0 ? nb : 1;
+}
+
+#define GP_TW_SWITCH(DT, CALL)                 \
+  switch (tw) {                                \
+    case 4: return CALL(DT, 4);                \
+    case 8: return CALL(DT, 8);                \
+    case 12: return CALL(DT, 12);              \
+    case 16: return CALL(DT, 16);              \
+    case 20: return CALL(DT, 20);              \
+    case 24: return CALL(DT, 24);              \
+    case 28: return CALL(DT, 28);              \
+    case 32: return CALL(DT, 32);              \
+    default: break;                            \
+  }
+
+#define GP_DT_SWITCH(CALL)                      \
+  switch (dt) {                                 \
+    case 1: GP_TW_SWITCH(1, CALL) break;        \
+    case 2: GP_TW_SWITCH(2, CALL) break;        \
+    case 3: GP_TW_SWITCH(3, CALL) break;        \
+    case 4: GP_TW_SWITCH(4, CALL) break;        \
+    case 8: GP_TW_SWITCH(8, CALL) break;        \
+    case 16: GP_TW_SWITCH(16, CALL) break;      \
+    default: break;                             \
+  }
+
+}  // namespace
+
+cudaError_t GP_LAUNCH(const SimtPlan& p, const SimtArgs& a, cudaStream_t st) {
+  const int dt = p.dt, tw = p.tw;
+#define GP_CALL_LAUNCH(D, W) launch_one<D, W>(p, a, st)
+  GP_DT_SWITCH(GP_CALL_LAUNCH)
+#undef GP_CALL_LAUNCH
+  return cudaErrorInvalidValue;
+}
+
+int GP_OCC(int dt, int tw, int w_pad) {
+#define GP_CALL_OCC(D, W) occ_one<D, W>(w_pad)
+  GP_DT_SWITCH(GP_CALL_OCC)
+#undef GP_CALL_OCC
+  return 1;
+}
+
+}  // namespace gp

@@ -1,0 +1,545 @@
+// O(n w) kernels around the on-the-fly product: staging, epilogues, block CG
+// (per-column CG with FP64 step scalars), probe generation, SLQ and the
+// loss/gradient assembly.  All reductions are deterministic: per-block FP64
+// partials in a fixed order, summed by the last block to finish.
+#include <math.h>
+
+#include "tridiag.cuh"
+#include "vec_kernels.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr int kEltThreads = 256;
+
+inline int elt_blocks(int64_t total) {
+  int64_t b = (total + kEltThreads - 1) / kEltThreads;
+  if (b > 152 * 32) b = 152 * 32;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+// ---------------------------------------------------------------- reduction --
+// Thread t of a block covers column c = t % w_pad and row lane t / w_pad.
+struct RedLayout {
+  int c, rl, nrl;
+  bool live;
+};
+
+__device__ __forceinline__ RedLayout red_layout(int w_pad) {
+  RedLayout L;
+  L.nrl = kRedThreads / w_pad;
+  L.c = threadIdx.x % w_pad;
+  L.rl = threadIdx.x / w_pad;
+  L.live = L.rl < L.nrl;
+  return L;
+}
+
+__device__ __forceinline__ void block_rows(int64_t n_rows, int64_t& r0, int64_t& r1) {
+  const int64_t per = (n_rows + gridDim.x - 1) / gridDim.x;
+  r0 = static_cast<int64_t>(blockIdx.x) * per;
+  r1 = r0 + per < n_rows ? r0 + per : n_rows;
+}
+
+// Combine the per-thread partials of NQ quantities into red[q][block][c].
+template <int NQ>
+__device__ __forceinline__ void block_store(const double (&acc)[NQ], const RedLayout& L, int w_pad,
+                                            double* red) {
+  __shared__ double sm[kRedThreads];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    sm[threadIdx.x] = L.live ? acc[q] : 0.0;
+    __syncthreads();
+    if (threadIdx.x < w_pad) {
+      double s = 0.0;
+      for (int k = 0; k < L.nrl; ++k) s += sm[k * w_pad + threadIdx.x];
+      red[(static_cast<int64_t>(q) * gridDim.x + blockIdx.x) * w_pad + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// True in exactly one block: the last one to arrive (its reads of red see all).
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x - 1);
+    if (am_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+__device__ __forceinline__ double final_sum(const double* red, int q, int c, int w_pad) {
+  double s = 0.0;
+  for (int b = 0; b < static_cast<int>(gridDim.x); ++b)
+    s += red[(static_cast<int64_t>(q) * gridDim.x + b) * w_pad + c];
+  return s;
+}
+
+// ------------------------------------------------------------------ staging --
+
+__global__ void stage_points_kernel(const float* X, int64_t n, int d, int64_t ld, const float* ref,
+                                    float cs, int dp, int64_t n_pad, float* out) {
+  const int64_t total = n_pad * dp;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / dp;
+    const int t = static_cast<int>(e - i * dp);
+    float v = 0.f;
+    if (i < n && t < d) v = (X[i * ld + t] - ref[t]) * cs;
+    out[e] = v;
+  }
+}
+
+__global__ void pad_block_kernel(const float* V, int64_t n, int w, int64_t ldv, float* out,
+                                 int64_t n_pad, int w_pad, int col_off) {
+  const int64_t total = n_pad * w;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / w;
+    const int c = static_cast<int>(e - i * w);
+    out[i * w_pad + col_off + c] = (i < n) ? V[i * ldv + c] : 0.f;
+  }
+}
+
+__global__ void unpad_block_kernel(const float* in, int64_t n, int w, int w_pad, float* out,
+                                   int64_t ldo, int col_off) {
+  const int64_t total = n * w;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / w;
+    const int c = static_cast<int>(e - i * w);
+    out[i * ldo + c] = in[i * w_pad + col_off + c];
+  }
+}
+
+// SplitMix64 finaliser of (key + golden gamma): the first output of SplitMix64
+// started from state `key` (Steele, Lea & Flood 2014).
+__device__ __forceinline__ uint64_t splitmix64_first(uint64_t key) {
+  uint64_t z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+__global__ void probes_kernel(int64_t n, int p, uint64_t seed, float* Z, int64_t ldz, int col_off) {
+  const int64_t total = n * p;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / p;
+    const int c = static_cast<int>(e - i * p);
+    const uint64_t key = seed ^ (static_cast<uint64_t>(c) << 40) ^ static_cast<uint64_t>(i);
+    Z[i * ldz + col_off + c] = (splitmix64_first(key) >> 63) ? -1.f : 1.f;
+  }
+}
+
+// ----------------------------------------------------------------- epilogue --
+
+__global__ void epilogue_kernel(EpiArgs a) {
+  const bool bad = (a.err != nullptr) && (*a.err != 0);
+  const int64_t total = a.n * a.w;
+  const float qnan = __int_as_float(0x7fc00000);
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t i = e / a.w;
+    const int c = static_cast<int>(e - i * a.w);
+    const int64_t idx = i * a.w_pad + c;
+    const int64_t plane = a.nr_pad * a.w_pad;
+    double sk = 0.0, sd = 0.0;
+    for (int s = 0; s < a.split; ++s) sk += a.part_k[s * plane + idx];
+    if (a.dyl != nullptr)
+      for (int s = 0; s < a.split; ++s) sd += a.part_d[s * plane + idx];
+    if (a.y != nullptr) {
+      double yv = a.cK * sk;
+      if (a.cV != 0.0) yv += a.cV * static_cast<double>(a.v[idx]);
+      a.y[i * a.ldy + c] = bad ? qnan : static_cast<float>(yv);
+    }
+    if (a.dyf != nullptr) a.dyf[i * a.ldf + c] = bad ? qnan : static_cast<float>(a.cF * sk);
+    if (a.dyl != nullptr) a.dyl[i * a.ldl + c] = bad ? qnan : static_cast<float>(a.cL * sd);
+  }
+}
+
+// ----------------------------------------------------------------- block CG --
+
+__global__ void cg_init_kernel(CgState* S, const float* B, float* X, float* R, float* P,
+                               int64_t n_pad, int w_pad, int w, int maxit, double rtol,
+                               double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      const float b = B[idx];
+      X[idx] = 0.f;
+      R[idx] = b;
+      P[idx] = b;
+      acc[0] += static_cast<double>(b) * b;
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (threadIdx.x < kMaxW) {
+    const int c = threadIdx.x;
+    double bn2 = 0.0;
+    if (c < w_pad) bn2 = final_sum(red, 0, c, w_pad);
+    const bool act = (c < w) && (bn2 > 0.0);
+    S->bn2[c] = bn2;
+    S->rr[c] = bn2;
+    S->active[c] = act ? 1 : 0;
+    S->iters[c] = 0;
+    S->alpha[c] = 0.0;
+    S->beta[c] = 0.0;
+    S->relres[c] = act ? 1.0 : 0.0;
+    if (act) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->n_active = cnt;
+    S->err = 0;
+    S->iter = 0;
+    S->maxit = maxit;
+    S->w = w;
+    S->rtol = rtol;
+  }
+}
+
+__global__ void cg_epi_alpha_kernel(CgState* S, const float* part_k, int split, const float* P,
+                                    float* Q, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                    double snoise, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  const int64_t plane = n_pad * w_pad;
+  double acc[1] = {0.0};
+  if (L.live) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      float q = 0.f;
+      if (r < n) {
+        double sk = 0.0;
+        for (int s = 0; s < split; ++s) sk += part_k[s * plane + idx];
+        const double pv = P[idx];
+        const double qd = f2 * sk + snoise * pv;
+        q = static_cast<float>(qd);
+        acc[0] += pv * static_cast<double>(q);
+      }
+      Q[idx] = q;
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    const double pap = final_sum(red, 0, c, w_pad);
+    double al = 0.0;
+    if (S->active[c]) {
+      if (!(pap > 0.0) || !isfinite(pap)) {
+        S->err = kDevBreakdown;
+        S->active[c] = 0;
+      } else {
+        al = S->rr[c] / pap;
+        const int it = S->iters[c];
+        if (it < kMaxK) S->ahist[it][c] = al;
+      }
+    }
+    S->alpha[c] = al;
+  }
+}
+
+__global__ void cg_update_kernel(CgState* S, float* X, float* R, const float* P, const float* Q,
+                                 int64_t n_pad, int w_pad, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live) {
+    const int act = S->active[L.c];
+    const float al = static_cast<float>(S->alpha[L.c]);
+    if (act) {
+      for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+        const int64_t idx = r * w_pad + L.c;
+        X[idx] = fmaf(al, P[idx], X[idx]);
+        const float rn = fmaf(-al, Q[idx], R[idx]);
+        R[idx] = rn;
+        acc[0] += static_cast<double>(rn) * rn;
+      }
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    if (S->active[c]) {
+      const double rr_new = final_sum(red, 0, c, w_pad);
+      const double be = rr_new / S->rr[c];
+      const int it = S->iters[c];
+      if (it < kMaxK) S->bhist[it][c] = be;
+      S->iters[c] = it + 1;
+      S->rr[c] = rr_new;
+      S->beta[c] = be;
+      const double rel = sqrt(rr_new / S->bn2[c]);
+      S->relres[c] = rel;
+      if (!(rel > S->rtol) || it + 1 >= S->maxit || !isfinite(rel)) {
+        S->active[c] = 0;
+      } else {
+        atomicAdd(&cnt, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->n_active = cnt;
+    S->iter = S->iter + 1;
+  }
+}
+
+__global__ void cg_pupdate_kernel(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad) {
+  if (S->n_active == 0) return;
+  const int64_t total = n_pad * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e % w_pad);
+    if (S->active[c]) P[e] = fmaf(static_cast<float>(S->beta[c]), P[e], R[e]);
+  }
+}
+
+// ---------------------------------------------------------------------- SLQ --
+
+__global__ void slq_kernel(CgState* S, int col0, int p, int k) {
+  __shared__ double vals[kMaxW];
+  __shared__ int bad;
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const int i = threadIdx.x;
+  if (i < p) {
+    const int c = col0 + i;
+    int m = S->iters[c];
+    if (m > k) m = k;
+    double a[kMaxK], b[kMaxK], q[kMaxK];
+    bool ok = true;
+    const double v = cg_lanczos_logquad(&S->ahist[0][c], &S->bhist[0][c], kMaxW, m, S->bn2[c], a,
+                                        b, q, &ok);
+    vals[i] = v;
+    S->slq_val[i] = v;
+    if (!ok) atomicExch(&bad, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double mean = 0.0;
+    for (int j = 0; j < p; ++j) mean += vals[j];
+    mean = p > 0 ? mean / p : 0.0;
+    double var = 0.0;
+    for (int j = 0; j < p; ++j) var += (vals[j] - mean) * (vals[j] - mean);
+    const double se = p > 1 ? sqrt(var / (p - 1) / p) : 0.0;
+    S->out[0] = mean;
+    S->out[1] = se;
+    if (bad) S->err = kDevNumeric;
+  }
+}
+
+// ------------------------------------------------------------ gradient pass --
+
+__global__ void grad_dots_kernel(CgState* S, const float* part_k, const float* part_d, int split,
+                                 const float* V, const float* W, int64_t n_pad, int w_pad, int w,
+                                 double cF, double cL, double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  const int64_t plane = n_pad * w_pad;
+  double acc[3] = {0.0, 0.0, 0.0};
+  if (L.live && L.c < w) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      const double wv = W[idx];
+      if (wv == 0.0) continue;
+      double sk = 0.0, sd = 0.0;
+      for (int s = 0; s < split; ++s) {
+        sk += part_k[s * plane + idx];
+        sd += part_d[s * plane + idx];
+      }
+      acc[0] += wv * static_cast<double>(V[idx]);
+      acc[1] += wv * (cF * sk);
+      acc[2] += wv * (cL * sd);
+    }
+  }
+  block_store<3>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    for (int q = 0; q < 3; ++q) S->dots[q][c] = final_sum(red, q, c, w_pad);
+  }
+}
+
+__global__ void yalpha_kernel(CgState* S, const float* B, const float* X, int64_t n_pad, int w_pad,
+                              double* red) {
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x)
+    acc[0] += static_cast<double>(B[r * w_pad]) * static_cast<double>(X[r * w_pad]);
+  RedLayout L;
+  L.nrl = kRedThreads;
+  L.c = 0;
+  L.rl = threadIdx.x;
+  L.live = true;
+  block_store<1>(acc, L, 1, red);
+  if (!last_block(&S->ticket)) return;
+  if (threadIdx.x == 0) S->yalpha = final_sum(red, 0, 0, 1);
+}
+
+// out: [0] logdet [1] logdet_stderr [2] loss [3..5] grad [6..8] quad [9..11] trace
+//      [12..14] trace_stderr [15] y^T alpha
+__global__ void assemble_kernel(CgState* S, int64_t n, int p) {
+  if (threadIdx.x != 0) return;
+  const double log2pi = 1.8378770664093454835606594728112;
+  const double ya = S->yalpha;
+  const double logdet = S->out[0];
+  S->out[2] = 0.5 * (ya + logdet + static_cast<double>(n) * log2pi);
+  for (int t = 0; t < 3; ++t) {
+    const double quad = S->dots[t][0];
+    double mean = 0.0;
+    for (int i = 1; i <= p; ++i) mean += S->dots[t][i];
+    mean = p > 0 ? mean / p : 0.0;
+    double var = 0.0;
+    for (int i = 1; i <= p; ++i) var += (S->dots[t][i] - mean) * (S->dots[t][i] - mean);
+    S->out[6 + t] = quad;
+    S->out[9 + t] = mean;
+    S->out[12 + t] = p > 1 ? sqrt(var / (p - 1) / p) : 0.0;
+    S->out[3 + t] = 0.5 * (-quad + mean);
+  }
+  S->out[15] = ya;
+}
+
+__global__ void copy_col0_kernel(const float* X, float* V, int64_t n_pad, int w_pad) {
+  for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < n_pad;
+       r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    V[r * w_pad] = X[r * w_pad];
+}
+
+}  // namespace
+
+int red_blocks(int64_t n_pad) {
+  int64_t b = n_pad / 256;
+  if (b > 608) b = 608;
+  if (b < 1) b = 1;
+  return static_cast<int>(b);
+}
+
+cudaError_t launch_stage_points(const float* X, int64_t n, int d, int64_t ld, const float* ref,
+                                float cs, int dp, int64_t n_pad, float* out, cudaStream_t st) {
+  stage_points_kernel<<<elt_blocks(n_pad * dp), kEltThreads, 0, st>>>(X, n, d, ld, ref, cs, dp,
+                                                                      n_pad, out);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_block(const float* V, int64_t n, int w, int64_t ldv, float* out,
+                             int64_t n_pad, int w_pad, int col_off, cudaStream_t st) {
+  pad_block_kernel<<<elt_blocks(n_pad * w), kEltThreads, 0, st>>>(V, n, w, ldv, out, n_pad, w_pad,
+                                                                  col_off);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpad_block(const float* in, int64_t n, int w, int w_pad, float* out,
+                               int64_t ldo, int col_off, cudaStream_t st) {
+  unpad_block_kernel<<<elt_blocks(n * w), kEltThreads, 0, st>>>(in, n, w, w_pad, out, ldo, col_off);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_probes(int64_t n, int p, uint64_t seed, float* Z, int64_t ldz, int col_off,
+                          int64_t, cudaStream_t st) {
+  if (n <= 0 || p <= 0) return cudaSuccess;
+  probes_kernel<<<elt_blocks(n * p), kEltThreads, 0, st>>>(n, p, seed, Z, ldz, col_off);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t st) {
+  epilogue_kernel<<<elt_blocks(a.n * a.w), kEltThreads, 0, st>>>(a);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(CgState* S, const float* B, float* X, float* R, float* P, int64_t n_pad,
+                           int w_pad, int w, int maxit, double rtol, double* red, cudaStream_t st) {
+  cg_init_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, X, R, P, n_pad, w_pad, w, maxit,
+                                                            rtol, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_epi_alpha(CgState* S, const float* part_k, int split, const float* P,
+                                float* Q, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                double snoise, double* red, cudaStream_t st) {
+  cg_epi_alpha_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, part_k, split, P, Q, n_pad, n,
+                                                                 w_pad, f2, snoise, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(CgState* S, float* X, float* R, const float* P, const float* Q,
+                             int64_t n_pad, int w_pad, double* red, cudaStream_t st) {
+  cg_update_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, X, R, P, Q, n_pad, w_pad, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad,
+                              cudaStream_t st) {
+  cg_pupdate_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, R, P, n_pad, w_pad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slq(CgState* S, int col0, int p, int k, cudaStream_t st) {
+  slq_kernel<<<1, kMaxW, 0, st>>>(S, col0, p, k);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_dots(CgState* S, const float* part_k, const float* part_d, int split,
+                             const float* V, const float* W, int64_t n_pad, int w_pad, int w,
+                             double cF, double cL, double* red, cudaStream_t st) {
+  grad_dots_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, part_k, part_d, split, V, W, n_pad,
+                                                              w_pad, w, cF, cL, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_yalpha(CgState* S, const float* B, const float* X, int64_t n_pad, int w_pad,
+                          double* red, cudaStream_t st) {
+  yalpha_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, X, n_pad, w_pad, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st) {
+  assemble_kernel<<<1, 32, 0, st>>>(S, n, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy_col0(const float* X, float* V, int64_t n_pad, int w_pad, cudaStream_t st) {
+  copy_col0_kernel<<<elt_blocks(n_pad), kEltThreads, 0, st>>>(X, V, n_pad, w_pad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,104 @@
+// Declarations of the O(n w) kernels around the product: staging, epilogues,
+// block-CG vector updates and reductions, probe generation, Lanczos/SLQ and the
+// loss/gradient assembly.
+#pragma once
+
+#include "gp_internal.cuh"
+
+namespace gp {
+
+// Block-CG scalar state, resident in the workspace (one per solve).
+constexpr int kMaxW = GP_MAX_COLS;
+constexpr int kMaxK = GP_MAX_LANCZOS;
+
+struct CgState {
+  int n_active;          // columns still iterating
+  int err;               // DevErr
+  unsigned ticket;       // last-block counter of the current reduction
+  int iter;              // iterations issued
+  int maxit;
+  int w;                 // live columns
+  double rtol;
+  int active[kMaxW];
+  int iters[kMaxW];
+  double rr[kMaxW];      // r^T r of the current residual
+  double bn2[kMaxW];     // ||b||^2
+  double alpha[kMaxW];
+  double beta[kMaxW];
+  double relres[kMaxW];
+  double ahist[kMaxK][kMaxW];
+  double bhist[kMaxK][kMaxW];
+  // SLQ / gradient outputs
+  double slq_val[kMaxW];     // per-probe SLQ values
+  double dots[3][kMaxW];     // per-column W^T (dKh/dtheta V)
+  double yalpha;
+  double out[16];            // assembled results (see assemble kernel)
+  unsigned ticket2;
+};
+
+// Reduction geometry for the O(n w) kernels.
+constexpr int kRedThreads = 256;
+int red_blocks(int64_t n_pad);
+
+// Launchers (all asynchronous on `st`).
+cudaError_t launch_stage_points(const float* X, int64_t n, int d, int64_t ld, const float* ref,
+                                float cs, int dp, int64_t n_pad, float* out, cudaStream_t st);
+cudaError_t launch_pad_block(const float* V, int64_t n, int w, int64_t ldv, float* out,
+                             int64_t n_pad, int w_pad, int col_off, cudaStream_t st);
+cudaError_t launch_unpad_block(const float* in, int64_t n, int w, int w_pad, float* out,
+                               int64_t ldo, int col_off, cudaStream_t st);
+cudaError_t launch_probes(int64_t n, int p, uint64_t seed, float* Z, int64_t ldz, int col_off,
+                          int64_t n_rows_fill, cudaStream_t st);
+
+// Epilogue of a product: Y = cK * sum_s partK + cV * V;  dYf = cF * sum_s partK;
+// dYl = cL * sum_s partD.  Outputs with a NULL pointer are skipped.  If *err != 0
+// the outputs are filled with NaN (an asynchronous error report).
+struct EpiArgs {
+  const float* part_k;
+  const float* part_d;
+  int split;
+  int64_t nr_pad;
+  int w_pad;
+  const float* v;        // padded V for the cV term (may be NULL if cV == 0)
+  int64_t n;             // live rows
+  int w;                 // live columns
+  double cK, cV, cF, cL;
+  float* y;  int64_t ldy;
+  float* dyf; int64_t ldf;
+  float* dyl; int64_t ldl;
+  const int* err;
+};
+cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t st);
+
+// Block CG (per-column CG with FP64 scalars) on padded [n_pad][w_pad] arrays.
+cudaError_t launch_cg_init(CgState* S, const float* B, float* X, float* R, float* P, int64_t n_pad,
+                           int w_pad, int w, int maxit, double rtol, double* red, cudaStream_t st);
+// Q = f^2 sum partK + s P; pAp partials; alpha.
+cudaError_t launch_cg_epi_alpha(CgState* S, const float* part_k, int split, const float* P,
+                                float* Q, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                double snoise, double* red, cudaStream_t st);
+// X += alpha P; R -= alpha Q; beta, convergence.
+cudaError_t launch_cg_update(CgState* S, float* X, float* R, const float* P, const float* Q,
+                             int64_t n_pad, int w_pad, double* red, cudaStream_t st);
+// P = R + beta P.
+cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad,
+                              cudaStream_t st);
+
+// SLQ from the CG coefficients of columns [col0, col0 + p): per-probe values
+// into S->slq_val and (mean, stderr) into S->out[0..1].
+cudaError_t launch_slq(CgState* S, int col0, int p, int k, cudaStream_t st);
+
+// Gradient epilogue: sums of the fused product with V = [alpha | Z] dotted with
+// W = [alpha | U] per column -> S->dots (scaled: s, f, l).
+cudaError_t launch_grad_dots(CgState* S, const float* part_k, const float* part_d, int split,
+                             const float* V, const float* W, int64_t n_pad, int w_pad, int w,
+                             double cF, double cL, double* red, cudaStream_t st);
+// y^T alpha -> S->yalpha (column 0 of B and X).
+cudaError_t launch_yalpha(CgState* S, const float* B, const float* X, int64_t n_pad, int w_pad,
+                          double* red, cudaStream_t st);
+// Final assembly of loss and gradient into S->out (see vec_kernels.cu).
+cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st);
+// Replace column 0 of V (padded) by column 0 of X.
+cudaError_t launch_copy_col0(const float* X, float* V, int64_t n_pad, int w_pad, cudaStream_t st);
+
+}  // namespace gp

@@ -1,0 +1,158 @@
+"""GPU parity of block CG, SLQ, Hutchinson and L(Theta) / dL/dTheta against the
+FP64 oracle, through the C ABI.
+
+Tolerances:
+  * loss and each gradient component vs the oracle's same-probe estimator
+    (O-est): |delta| / max(|ref|, 1e-3 ||g_ref||) <= 1e-4;
+  * vs the exact Cholesky values (O-exact): y^T alpha and the quadratic
+    gradient terms at 1e-4; log-det and traces within 4 standard errors of the
+    probe mean (they are stochastic estimates);
+  * CG: recurrence relres <= cg_rtol; true residual checked in FP64.
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel(a, b, floor=0.0):
+    return abs(a - b) / max(abs(b), floor, 1e-300)
+
+
+@pytest.fixture(scope="module")
+def small():
+    prob = inputs.small_problem(seed=0)
+    Z = O.rademacher_probes(prob.n, 10, 1234)
+    est = O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 30)
+    ex = O.exact_nll(prob.X, prob.y, prob.kind, prob.theta)
+    return prob, est, ex
+
+
+def test_pcg_matches_cholesky(api):
+    prob = inputs.small_problem(seed=1)
+    Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 4, seed=3)]).astype(np.float32)
+    opts = api.solve_opts(cg_rtol=1e-8)
+    Xs, iters, relres, st = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts)
+    assert st == 0
+    assert max(relres) <= 1e-8
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    Xg = Xs.cpu().numpy().astype(np.float64)
+    true_res = np.linalg.norm(Bm - Kh @ Xg, axis=0) / np.linalg.norm(Bm, axis=0)
+    assert true_res.max() <= 1e-5, true_res
+    ref = sla.cho_solve(sla.cho_factor(Kh), Bm.astype(np.float64))
+    err = np.linalg.norm(Xg - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= 1e-4, err
+    # Iteration counts within a few percent of FP64 CG with the same start and rule.
+    _, it_ref, _, _, _ = O.cg(Kh, Bm, 1e-8, 5000)
+    assert np.all(np.abs(np.array(iters) - it_ref) <= 0.1 * it_ref + 5)
+
+
+def test_pcg_reports_not_converged(api):
+    prob = inputs.small_problem(seed=2)
+    opts = api.solve_opts(cg_rtol=1e-12, cg_maxit=5)
+    _, iters, relres, st = api.gp_pcg_solve(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts,
+                                            raise_not_converged=False)
+    assert st == 4  # GP_ERR_NOT_CONVERGED
+    assert iters == [5] and relres[0] > 1e-12
+
+
+def test_slq_matches_same_probe_estimator(api, small):
+    prob, est, ex = small
+    opts = api.solve_opts(nprobe=10, nlanczos=30, cg_rtol=1e-10, seed=1234)
+    ld, se = api.gp_slq_logdet(_dev(prob.X), prob.kind, prob.theta, opts)
+    assert rel(ld, est["logdet"]) <= 1e-4, (ld, est["logdet"])
+    assert abs(ld - ex["logdet"]) <= 4 * se + 1e-4 * abs(ex["logdet"])
+
+
+def test_loss_and_grad_small_config(api, small):
+    prob, est, ex = small
+    opts = api.solve_opts(nprobe=10, nlanczos=30, cg_rtol=1e-8, seed=1234)
+    loss, grad, info = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    gref = est["grad"]
+    gfloor = 1e-3 * np.linalg.norm(gref)
+    assert rel(loss, est["loss"]) <= 1e-4, (loss, est["loss"])
+    for t in range(3):
+        assert rel(grad[t], gref[t], gfloor) <= 1e-4, (t, grad, gref)
+    # Against the exact (Cholesky) values: deterministic terms tight, stochastic in band.
+    assert rel(info["yalpha"], ex["yalpha"]) <= 1e-4
+    for t in range(3):
+        assert rel(info["quad"][t], ex["quad"][t], 1e-3 * np.abs(ex["quad"]).max()) <= 1e-4
+        assert abs(info["trace"][t] - ex["trace"][t]) <= 4 * info["trace_stderr"][t] + 1e-6
+    assert abs(info["logdet"] - ex["logdet"]) <= 4 * info["logdet_stderr"]
+    assert info["relres_max"] <= 1e-8
+
+
+def test_forward_backward_split_equals_fused(api, small):
+    prob, est, _ = small
+    opts = api.solve_opts(nprobe=10, nlanczos=30, cg_rtol=1e-8, seed=1234)
+    X, y = _dev(prob.X), _dev(prob.y)
+    loss, grad, _ = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, opts)
+    loss2, W, _ = api.gp_nll_forward(X, y, prob.kind, prob.theta, opts)
+    grad2, _ = api.gp_nll_backward(X, W, prob.kind, prob.theta, opts)
+    assert loss2 == loss
+    np.testing.assert_allclose(grad2, grad, rtol=1e-12, atol=0)
+
+
+def test_autograd_function(api, small):
+    import torch
+    from paper_2503_02259_gb300.autograd import neg_log_likelihood
+    prob, est, _ = small
+    X, y = _dev(prob.X), _dev(prob.y)
+    for recompute in (False, True):
+        theta = torch.tensor(prob.theta, dtype=torch.float64, requires_grad=True)
+        L = neg_log_likelihood(theta, X, y, prob.kind, nprobe=10, nlanczos=30, cg_rtol=1e-8,
+                               seed=1234, recompute=recompute)
+        (2.0 * L).backward()
+        g = theta.grad.numpy() / 2.0
+        gfloor = 1e-3 * np.linalg.norm(est["grad"])
+        for t in range(3):
+            assert rel(g[t], est["grad"][t], gfloor) <= 1e-4
+        assert rel(float(L), est["loss"]) <= 1e-4
+
+
+def test_differentiation_config_subsample(api):
+    # n = 4000 subsample of the d = 8, 0.5 N(0, I) differentiation problem;
+    # Gaussian s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps.
+    prob = inputs.diff_problem(seed=0, n=4000)
+    Z = O.rademacher_probes(prob.n, 32, 77)
+    est = O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 40)
+    opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-8, seed=77)
+    loss, grad, info = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    gfloor = 1e-3 * np.linalg.norm(est["grad"])
+    assert rel(loss, est["loss"]) <= 1e-4, (loss, est["loss"])
+    for t in range(3):
+        assert rel(grad[t], est["grad"][t], gfloor) <= 1e-4, (t, grad, est["grad"])
+
+
+def test_loss_matern_and_user_probes(api):
+    prob = inputs.uniform_problem(1500, 2, O.MATERN32, (0.05, 1.2, 0.25), seed=5)
+    Z = O.rademacher_probes(prob.n, 8, 99).astype(np.float32)
+    Zd = _dev(Z)
+    est = O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 25)
+    opts = api.solve_opts(nprobe=8, nlanczos=25, cg_rtol=1e-8, seed=0, probes=Zd)
+    loss, grad, _ = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    gfloor = 1e-3 * np.linalg.norm(est["grad"])
+    assert rel(loss, est["loss"]) <= 1e-4
+    for t in range(3):
+        assert rel(grad[t], est["grad"][t], gfloor) <= 1e-4
