@@ -229,12 +229,15 @@ struct SolveWs {
   float* P;
   float* Q;
   float* part;     // max(split_cg, 2 * split_grad) planes
+  float* Lq;       // Lanczos basis: lz_k planes (NULL when no SLQ)
   double* red;
-  CgState* S;
+  CgState* S;      // block-CG state
+  CgState* S2;     // Lanczos state
   size_t bytes;
 };
 
-static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, bool with_grad) {
+static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, bool with_grad,
+                           int lz_k) {
   Carve c(ws);
   SolveWs w;
   const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
@@ -246,8 +249,10 @@ static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, boo
   w.Q = c.take<float>(plane);
   const size_t planes = std::max<size_t>(pc.split, with_grad ? 2 * static_cast<size_t>(pg.split) : 0);
   w.part = c.take<float>(planes * plane);
-  w.red = c.take<double>(3 * static_cast<size_t>(red_blocks(pc.nr_pad)) * pc.w_pad);
+  w.Lq = lz_k > 0 ? c.take<float>(static_cast<size_t>(lz_k) * plane) : nullptr;
+  w.red = c.take<double>(red_doubles(pc.nr_pad, pc.w_pad));
   w.S = c.take<CgState>(1);
+  w.S2 = c.take<CgState>(1);
   w.bytes = c.off + 256;
   return w;
 }
@@ -445,6 +450,33 @@ gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W
   return GP_OK;
 }
 
+// k Lanczos steps with full reorthogonalisation on columns [col0, col0 + p) of
+// W.B, one process per column, then the Gauss quadrature of log (SLQ) into
+// W.S2->out[0..1].  Uses W.R as the work vector and W.Lq as the basis.
+gp_status run_lanczos(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W, int col0,
+                      int np, int k, cudaStream_t st) {
+  const int64_t n = prob->n;
+  const double f2 = prob->theta.f * prob->theta.f;
+  const int64_t plane = p.nr_pad * p.w_pad;
+  CgState* S = W.S2;
+  GP_CUDA(cudaMemsetAsync(S, 0, sizeof(CgState), st));
+  GP_CUDA(launch_lz_init(S, W.B, W.Lq, p.nr_pad, p.w_pad, col0, np, W.red, st));
+  for (int j = 0; j < k; ++j) {
+    const float* Qj = W.Lq + j * plane;
+    gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, Qj, W.part, nullptr,
+                              &S->n_active, &S->err, st);
+    if (s != GP_OK) return s;
+    GP_CUDA(launch_lz_epi_alpha(S, W.part, p.split, Qj, W.R, p.nr_pad, n, p.w_pad, f2,
+                                prob->theta.s, j, W.red, st));
+    GP_CUDA(launch_lz_three_term(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, st));
+    GP_CUDA(launch_lz_reorth(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, W.red, st));
+    GP_CUDA(launch_lz_reorth(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, W.red, st));
+    GP_CUDA(launch_lz_norm_next(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, k, W.red, st));
+  }
+  GP_CUDA(launch_slq(S, col0, np, k, st));
+  return GP_OK;
+}
+
 }  // namespace gp
 
 struct HostCg {
@@ -466,15 +498,15 @@ struct SolveSetup {
   KernelConsts kc;
 };
 
-static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, void* ws,
-                             size_t ws_bytes, cudaStream_t st, SolveSetup& out) {
+static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, int lz_k,
+                             void* ws, size_t ws_bytes, cudaStream_t st, SolveSetup& out) {
   gp_status s;
   const int64_t n = prob->n;
   out.pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
   out.pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
-  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad);
+  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad, lz_k);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
-  out.W = carve_solve(ws, out.pc, out.pg, with_grad);
+  out.W = carve_solve(ws, out.pc, out.pg, with_grad, lz_k);
   out.kc = kernel_consts(prob->kernel, prob->theta.l);
   GP_CUDA(cudaMemsetAsync(out.W.S, 0, sizeof(CgState), st));
   GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.cs, out.pc.dp,
@@ -507,13 +539,17 @@ static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_s
   gp_status s;
   const int p = o->nprobe;
   const int w = 1 + p;
-  if ((s = setup_solve(prob, w, with_grad, o->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  const int lz_k = p > 0 ? o->nlanczos : 0;
+  if ((s = setup_solve(prob, w, with_grad, o->prec, lz_k, ws, ws_bytes, st, ss)) != GP_OK) return s;
   SolveWs& W = ss.W;
   GP_CUDA(launch_pad_block(y, prob->n, 1, 1, W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   if ((s = fill_probes(prob, o, W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;
   s = run_cg(prob, ss.pc, o->prec, W, w, effective_maxit(prob, o), o->cg_rtol, st);
   if (s != GP_OK) return s;
-  GP_CUDA(launch_slq(W.S, 1, p, o->nlanczos, st));
+  if (p > 0) {
+    if ((s = run_lanczos(prob, ss.pc, o->prec, W, 1, p, o->nlanczos, st)) != GP_OK) return s;
+    GP_CUDA(cudaMemcpyAsync(W.S->out, W.S2->out, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
   GP_CUDA(launch_yalpha(W.S, W.B, W.X, ss.pc.nr_pad, ss.pc.w_pad, W.red, st));
   GP_CUDA(launch_assemble(W.S, prob->n, p, st));
   cg_status = GP_OK;
@@ -543,15 +579,18 @@ static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, S
   return GP_OK;
 }
 
-static gp_status read_outputs(const CgState* S, int w, double out[16], gp_loss_info* info,
-                              cudaStream_t st) {
+static gp_status read_outputs(const CgState* S, const CgState* S2, int w, double out[16],
+                              gp_loss_info* info, cudaStream_t st) {
   HostCg h;
   gp_status s;
   if ((s = read_cg(S, h, st)) != GP_OK) return s;
   GP_CUDA(cudaMemcpyAsync(out, S->out, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  int err = 0;
+  int err = 0, err2 = 0;
   GP_CUDA(cudaMemcpyAsync(&err, &S->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (S2 != nullptr)
+    GP_CUDA(cudaMemcpyAsync(&err2, &S2->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   GP_CUDA(cudaStreamSynchronize(st));
+  if (err == 0) err = err2;
   if (info != nullptr) {
     info->yalpha = out[15];
     info->logdet = out[0];
@@ -638,7 +677,7 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
       const SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
-      return carve_solve(nullptr, pc, pc, false).bytes;
+      return carve_solve(nullptr, pc, pc, false, 0).bytes;
     }
     case GP_OP_SLQ:
     case GP_OP_LOSS_GRAD: {
@@ -646,7 +685,8 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
       const int ww = op == GP_OP_SLQ ? opts->nprobe : 1 + opts->nprobe;
       const SimtPlan pc = plan_for(n, n, prob->d, ww, false, prob->kernel, prec);
       const SimtPlan pg = plan_for(n, n, prob->d, ww, true, prob->kernel, GP_PREC_FP32);
-      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD).bytes;
+      const int lz_k = opts->nprobe > 0 ? opts->nlanczos : 0;
+      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD, lz_k).bytes;
     }
   }
   set_error("unknown op");
@@ -680,7 +720,7 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
     return refine_solve(prob, B, w, Xsol, opts, iters, relres, ws, ws_bytes, st);
   SolveSetup ss;
-  if ((s = setup_solve(prob, w, false, opts->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, false, opts->prec, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
   GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   const int maxit = effective_maxit(prob, opts);
   s = run_cg(prob, ss.pc, opts->prec, ss.W, w, maxit, opts->cg_rtol, st);
@@ -703,15 +743,13 @@ gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, doubl
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int p = opts->nprobe;
   SolveSetup ss;
-  if ((s = setup_solve(prob, p, false, opts->prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, p, false, opts->prec, opts->nlanczos, ws, ws_bytes, st, ss)) != GP_OK)
+    return s;
   if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st)) != GP_OK) return s;
-  // Only the first k CG steps enter the quadrature.
-  int maxit = std::min(effective_maxit(prob, opts), opts->nlanczos);
-  s = run_cg(prob, ss.pc, opts->prec, ss.W, p, maxit, opts->cg_rtol, st);
-  if (s != GP_OK) return s;
-  GP_CUDA(launch_slq(ss.W.S, 0, p, opts->nlanczos, st));
+  if ((s = run_lanczos(prob, ss.pc, opts->prec, ss.W, 0, p, opts->nlanczos, st)) != GP_OK) return s;
   double out[16];
-  if ((s = read_outputs(ss.W.S, p, out, nullptr, st)) != GP_OK) return s;
+  GP_CUDA(cudaMemcpyAsync(out, ss.W.S2->out, sizeof(out), cudaMemcpyDeviceToHost, st));
+  if ((s = device_status(&ss.W.S2->err, st)) != GP_OK) return s;
   if (logdet) *logdet = out[0];
   if (logdet_stderr) *logdet_stderr = out[1];
   return GP_OK;
@@ -730,7 +768,9 @@ gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solv
   if ((s = forward_impl(prob, y, opts, true, ws, ws_bytes, st, ss, cgs)) != GP_OK) return s;
   if ((s = backward_impl(prob, opts, ss, st)) != GP_OK) return s;
   double out[16];
-  if ((s = read_outputs(ss.W.S, 1 + opts->nprobe, out, info, st)) != GP_OK) return s;
+  if ((s = read_outputs(ss.W.S, opts->nprobe > 0 ? ss.W.S2 : nullptr, 1 + opts->nprobe, out, info,
+                        st)) != GP_OK)
+    return s;
   if (loss) *loss = out[2];
   if (grad)
     for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
@@ -750,7 +790,8 @@ gp_status gp_nll_forward(const gp_problem* prob, const float* y, const gp_solve_
   const int w = 1 + opts->nprobe;
   GP_CUDA(launch_unpad_block(ss.W.X, prob->n, w, ss.pc.w_pad, W, w, 0, st));
   double out[16];
-  if ((s = read_outputs(ss.W.S, w, out, info, st)) != GP_OK) return s;
+  if ((s = read_outputs(ss.W.S, opts->nprobe > 0 ? ss.W.S2 : nullptr, w, out, info, st)) != GP_OK)
+    return s;
   if (loss) *loss = out[2];
   return check_conv(ss.W.S, w, effective_maxit(prob, opts), opts->cg_rtol, st);
 }
@@ -765,7 +806,7 @@ gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, con
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int w = 1 + opts->nprobe;
   SolveSetup ss;
-  if ((s = setup_solve(prob, w, true, GP_PREC_FP32, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, true, GP_PREC_FP32, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
   // B = [alpha | Z] (alpha = column 0 of W), X = W.
   GP_CUDA(launch_pad_block(Wsol, prob->n, 1, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;

@@ -31,13 +31,13 @@ template <int KIND, bool GRAD>
 __device__ __forceinline__ void eval_entry(float q, float& kv, float& dv) {
   if constexpr (KIND == GP_KERNEL_GAUSSIAN) {
     kv = dev::ex2_approx(-q);
-    if constexpr (GRAD) dv = kv * q;
+    if constexpr (GRAD) dv = __fmul_rn(kv, q);
   } else {
+    // Explicit roundings so that every variant evaluates bit-identical entries.
     const float a = dev::sqrt_approx(q);
-    const float e = dev::ex2_approx(a * -1.4426950408889634f);
-    const float ae = a * e;
-    kv = ae + e;
-    if constexpr (GRAD) dv = a * ae;
+    const float e = dev::ex2_approx(__fmul_rn(a, -1.4426950408889634f));
+    kv = __fmaf_rn(a, e, e);
+    if constexpr (GRAD) dv = __fmul_rn(a, __fmul_rn(a, e));
   }
 }
 

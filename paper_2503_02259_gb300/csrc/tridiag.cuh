@@ -85,19 +85,17 @@ GP_HD bool tridiag_eig_first_row(double* a, double* b, double* q, int m) {
   return true;
 }
 
-// Gauss quadrature of log from the CG step coefficients of one column.
-// The Lanczos matrix hidden in CG: diag_j = 1/alpha_j + beta_{j-1}/alpha_{j-1},
-// off_j = sqrt(beta_j)/alpha_j.  alpha/beta are read with stride `stride`.
-// Returns ||z||^2 * sum_j U_1j^2 log(lambda_j); sets *ok = false on a
-// non-positive eigenvalue or a non-converged iteration.
-GP_HD double cg_lanczos_logquad(const double* alpha, const double* beta, int stride, int m,
-                                double znorm2, double* a, double* b, double* q, bool* ok) {
+// Gauss quadrature of log from one probe's Lanczos coefficients: T has
+// diagonal alpha[0..m-1] and off-diagonal beta[0..m-2] (read with stride
+// `stride`).  Returns ||z||^2 * sum_j U_1j^2 log(lambda_j); sets *ok = false on
+// a non-positive eigenvalue or a non-converged eigen-iteration.
+GP_HD double lanczos_logquad(const double* alpha, const double* beta, int stride, int m,
+                             double znorm2, double* a, double* b, double* q, bool* ok) {
   *ok = true;
   if (m <= 0) return 0.0;
   for (int j = 0; j < m; ++j) {
-    const double aj = alpha[j * stride];
-    a[j] = 1.0 / aj + (j > 0 ? beta[(j - 1) * stride] / alpha[(j - 1) * stride] : 0.0);
-    if (j + 1 < m) b[j] = sqrt(beta[j * stride]) / aj;
+    a[j] = alpha[j * stride];
+    if (j + 1 < m) b[j] = beta[j * stride];
   }
   if (!tridiag_eig_first_row(a, b, q, m)) *ok = false;
   double acc = 0.0;

@@ -4,6 +4,8 @@
 // partials in a fixed order, summed by the last block to finish.
 #include <math.h>
 
+#include <algorithm>
+
 #include "tridiag.cuh"
 #include "vec_kernels.cuh"
 
@@ -318,6 +320,198 @@ __global__ void cg_pupdate_kernel(CgState* S, const float* R, float* P, int64_t 
   }
 }
 
+// ------------------------------------------------------------------ Lanczos --
+// One independent Lanczos process per active column, with full
+// reorthogonalisation by two classical Gram-Schmidt passes per step, the steps
+// of stochastic Lanczos quadrature (Ubaru et al. 2017) from q_0 = z/||z||.
+
+__global__ void lz_init_kernel(CgState* S, const float* B, int64_t n_pad, int w_pad, int col0, int p,
+                               double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live)
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const double b = B[r * w_pad + L.c];
+      acc[0] += b * b;
+    }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (threadIdx.x < kMaxW) {
+    const int c = threadIdx.x;
+    const double bn2 = c < w_pad ? final_sum(red, 0, c, w_pad) : 0.0;
+    const bool act = c >= col0 && c < col0 + p && bn2 > 0.0;
+    S->bn2[c] = bn2;
+    S->active[c] = act ? 1 : 0;
+    S->iters[c] = 0;
+    S->tnorm[c] = 0.0;
+    S->alpha[c] = 0.0;
+    S->beta[c] = 0.0;
+    if (act) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->n_active = cnt;
+    S->err = 0;
+    S->iter = 0;
+  }
+}
+
+// dst = src * scale_c for active columns, 0 otherwise; scale = 1/sqrt(bn2) (j < 0)
+// or 1/beta_j.
+__global__ void lz_scale_kernel(const CgState* S, const float* src, float* dst, int64_t n_pad,
+                                int w_pad, int j) {
+  const int64_t total = n_pad * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e % w_pad);
+    float v = 0.f;
+    if (S->active[c]) {
+      const double sc = j < 0 ? 1.0 / sqrt(S->bn2[c]) : 1.0 / S->bhist[j][c];
+      v = static_cast<float>(static_cast<double>(src[e]) * sc);
+    }
+    dst[e] = v;
+  }
+}
+
+__global__ void lz_epi_alpha_kernel(CgState* S, const float* part_k, int split, const float* Qj,
+                                    float* W, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                    double snoise, int j, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  const int64_t plane = n_pad * w_pad;
+  double acc[1] = {0.0};
+  if (L.live) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      float wv = 0.f;
+      if (r < n) {
+        double sk = 0.0;
+        for (int s = 0; s < split; ++s) sk += part_k[s * plane + idx];
+        const double qv = Qj[idx];
+        wv = static_cast<float>(f2 * sk + snoise * qv);
+        acc[0] += qv * static_cast<double>(wv);
+      }
+      W[idx] = wv;
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    const double al = final_sum(red, 0, c, w_pad);
+    if (S->active[c]) S->ahist[j][c] = al;
+  }
+}
+
+__global__ void lz_three_term_kernel(const CgState* S, float* W, const float* Q, int64_t n_pad,
+                                     int w_pad, int j) {
+  if (S->n_active == 0) return;
+  const int64_t plane = n_pad * w_pad;
+  const float* Qj = Q + static_cast<int64_t>(j) * plane;
+  const float* Qm = j > 0 ? Q + static_cast<int64_t>(j - 1) * plane : nullptr;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < plane;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e % w_pad);
+    if (!S->active[c]) continue;
+    double v = static_cast<double>(W[e]) - S->ahist[j][c] * static_cast<double>(Qj[e]);
+    if (j > 0) v -= S->bhist[j - 1][c] * static_cast<double>(Qm[e]);
+    W[e] = static_cast<float>(v);
+  }
+}
+
+// h[i][c] = sum_r Q_i[r][c] W[r][c] for i < nq.
+__global__ void lz_dots_kernel(CgState* S, const float* W, const float* Q, int64_t n_pad, int w_pad,
+                               int nq, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  const int64_t plane = n_pad * w_pad;
+  __shared__ double sm[kRedThreads];
+  for (int i = 0; i < nq; ++i) {
+    double acc = 0.0;
+    if (L.live) {
+      const float* Qi = Q + static_cast<int64_t>(i) * plane;
+      for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+        const int64_t idx = r * w_pad + L.c;
+        acc += static_cast<double>(Qi[idx]) * static_cast<double>(W[idx]);
+      }
+    }
+    sm[threadIdx.x] = L.live ? acc : 0.0;
+    __syncthreads();
+    if (threadIdx.x < w_pad) {
+      double s = 0.0;
+      for (int q = 0; q < L.nrl; ++q) s += sm[q * w_pad + threadIdx.x];
+      red[(static_cast<int64_t>(i) * gridDim.x + blockIdx.x) * w_pad + threadIdx.x] = s;
+    }
+    __syncthreads();
+  }
+  if (!last_block(&S->ticket)) return;
+  for (int t = threadIdx.x; t < nq * w_pad; t += blockDim.x) {
+    const int i = t / w_pad;
+    const int c = t - i * w_pad;
+    S->h[i][c] = final_sum(red, i, c, w_pad);
+  }
+}
+
+__global__ void lz_sub_kernel(const CgState* S, float* W, const float* Q, int64_t n_pad, int w_pad,
+                              int nq) {
+  if (S->n_active == 0) return;
+  const int64_t plane = n_pad * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < plane;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e % w_pad);
+    if (!S->active[c]) continue;
+    double v = W[e];
+    for (int i = 0; i < nq; ++i) v -= S->h[i][c] * static_cast<double>(Q[i * plane + e]);
+    W[e] = static_cast<float>(v);
+  }
+}
+
+__global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_pad, int j, int k,
+                               double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live)
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const double v = W[r * w_pad + L.c];
+      acc[0] += v * v;
+    }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    if (S->active[c]) {
+      const double be = sqrt(final_sum(red, 0, c, w_pad));
+      const double bprev = j > 0 ? S->bhist[j - 1][c] : 0.0;
+      const double tn = fmax(S->tnorm[c], fabs(S->ahist[j][c]) + be + bprev);
+      S->tnorm[c] = tn;
+      S->bhist[j][c] = be;
+      S->iters[c] = j + 1;
+      if (j + 1 >= k || !(be >= 1e-14 * tn)) {
+        S->active[c] = 0;
+      } else {
+        atomicAdd(&cnt, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) S->n_active = cnt;
+}
+
 // ---------------------------------------------------------------------- SLQ --
 
 __global__ void slq_kernel(CgState* S, int col0, int p, int k) {
@@ -332,8 +526,8 @@ __global__ void slq_kernel(CgState* S, int col0, int p, int k) {
     if (m > k) m = k;
     double a[kMaxK], b[kMaxK], q[kMaxK];
     bool ok = true;
-    const double v = cg_lanczos_logquad(&S->ahist[0][c], &S->bhist[0][c], kMaxW, m, S->bn2[c], a,
-                                        b, q, &ok);
+    const double v = lanczos_logquad(&S->ahist[0][c], &S->bhist[0][c], kMaxW, m, S->bn2[c], a, b,
+                                     q, &ok);
     vals[i] = v;
     S->slq_val[i] = v;
     if (!ok) atomicExch(&bad, 1);
@@ -506,6 +700,60 @@ cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pa
   cg_pupdate_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, R, P, n_pad, w_pad);
   count_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_lz_init(CgState* S, const float* B, float* Q0, int64_t n_pad, int w_pad, int col0,
+                           int p, double* red, cudaStream_t st) {
+  lz_init_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, n_pad, w_pad, col0, p, red);
+  count_launch();
+  lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, B, Q0, n_pad, w_pad, -1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_epi_alpha(CgState* S, const float* part_k, int split, const float* Qj,
+                                float* W, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                double snoise, int j, double* red, cudaStream_t st) {
+  lz_epi_alpha_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, part_k, split, Qj, W, n_pad, n,
+                                                                 w_pad, f2, snoise, j, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_three_term(CgState* S, float* W, const float* Q, int64_t n_pad, int w_pad,
+                                 int j, cudaStream_t st) {
+  lz_three_term_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, W, Q, n_pad, w_pad, j);
+  count_launch();
+  return cudaGetLastError();
+}
+
+int lz_dot_blocks(int64_t n_pad) { return std::min(red_blocks(n_pad), kLzDotBlocks); }
+
+cudaError_t launch_lz_reorth(CgState* S, float* W, const float* Q, int64_t n_pad, int w_pad, int j,
+                             double* red, cudaStream_t st) {
+  lz_dots_kernel<<<lz_dot_blocks(n_pad), kRedThreads, 0, st>>>(S, W, Q, n_pad, w_pad, j + 1, red);
+  count_launch();
+  lz_sub_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, W, Q, n_pad, w_pad, j + 1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_norm_next(CgState* S, const float* W, float* Q, int64_t n_pad, int w_pad,
+                                int j, int k, double* red, cudaStream_t st) {
+  lz_norm_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, W, n_pad, w_pad, j, k, red);
+  count_launch();
+  if (j + 1 < k) {
+    float* Qn = Q + static_cast<int64_t>(j + 1) * n_pad * w_pad;
+    lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, W, Qn, n_pad, w_pad, j);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+size_t red_doubles(int64_t n_pad, int w_pad) {
+  const size_t a = 3 * static_cast<size_t>(red_blocks(n_pad));
+  const size_t b = static_cast<size_t>(kMaxK + 1) * lz_dot_blocks(n_pad);
+  return std::max(a, b) * w_pad;
 }
 
 cudaError_t launch_slq(CgState* S, int col0, int p, int k, cudaStream_t st) {

@@ -26,8 +26,10 @@ struct CgState {
   double alpha[kMaxW];
   double beta[kMaxW];
   double relres[kMaxW];
-  double ahist[kMaxK][kMaxW];
-  double bhist[kMaxK][kMaxW];
+  double ahist[kMaxK][kMaxW];   // CG: alpha_j; Lanczos: diagonal alpha_j
+  double bhist[kMaxK][kMaxW];   // CG: beta_j;  Lanczos: off-diagonal beta_j
+  double h[kMaxK + 1][kMaxW];   // Lanczos: reorthogonalisation coefficients
+  double tnorm[kMaxW];          // Lanczos: running estimate of ||T||
   // SLQ / gradient outputs
   double slq_val[kMaxW];     // per-probe SLQ values
   double dots[3][kMaxW];     // per-column W^T (dKh/dtheta V)
@@ -38,7 +40,10 @@ struct CgState {
 
 // Reduction geometry for the O(n w) kernels.
 constexpr int kRedThreads = 256;
+constexpr int kLzDotBlocks = 128;
 int red_blocks(int64_t n_pad);
+// Doubles of reduction scratch needed by every kernel below for this shape.
+size_t red_doubles(int64_t n_pad, int w_pad);
 
 // Launchers (all asynchronous on `st`).
 cudaError_t launch_stage_points(const float* X, int64_t n, int d, int64_t ld, const float* ref,
@@ -84,8 +89,27 @@ cudaError_t launch_cg_update(CgState* S, float* X, float* R, const float* P, con
 cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad,
                               cudaStream_t st);
 
-// SLQ from the CG coefficients of columns [col0, col0 + p): per-probe values
-// into S->slq_val and (mean, stderr) into S->out[0..1].
+// Lanczos with full reorthogonalisation, one independent process per column of
+// a padded [n_pad][w_pad] block (columns [col0, col0 + p) active).
+// Q: (k+1) planes of [n_pad][w_pad]; plane j holds q_j.
+cudaError_t launch_lz_init(CgState* S, const float* B, float* Q0, int64_t n_pad, int w_pad, int col0,
+                           int p, double* red, cudaStream_t st);
+// W = f^2 sum partK + s q_j (rows < n); alpha_j = q_j^T W.
+cudaError_t launch_lz_epi_alpha(CgState* S, const float* part_k, int split, const float* Qj,
+                                float* W, int64_t n_pad, int64_t n, int w_pad, double f2,
+                                double snoise, int j, double* red, cudaStream_t st);
+// W -= alpha_j q_j + beta_{j-1} q_{j-1}.
+cudaError_t launch_lz_three_term(CgState* S, float* W, const float* Q, int64_t n_pad, int w_pad,
+                                 int j, cudaStream_t st);
+// One classical Gram-Schmidt pass against q_0..q_j: h = Q^T W; W -= Q h.
+cudaError_t launch_lz_reorth(CgState* S, float* W, const float* Q, int64_t n_pad, int w_pad, int j,
+                             double* red, cudaStream_t st);
+// beta_j = ||W||; truncation; q_{j+1} = W / beta_j.
+cudaError_t launch_lz_norm_next(CgState* S, const float* W, float* Q, int64_t n_pad, int w_pad,
+                                int j, int k, double* red, cudaStream_t st);
+
+// SLQ from the Lanczos coefficients of columns [col0, col0 + p): per-probe
+// values into S->slq_val and (mean, stderr) into S->out[0..1].
 cudaError_t launch_slq(CgState* S, int col0, int p, int k, cudaStream_t st);
 
 // Gradient epilogue: sums of the fused product with V = [alpha | Z] dotted with

@@ -100,7 +100,7 @@ def tri(tmp_path_factory):
                    '{ return gp::tridiag_eig_first_row(a, b, q, m) ? 1 : 0; }\n'
                    'extern "C" double quad(const double* al, const double* be, int m, double z2)'
                    '{ double a[64], b[64], q[64]; bool ok; '
-                   'double v = gp::cg_lanczos_logquad(al, be, 1, m, z2, a, b, q, &ok); '
+                   'double v = gp::lanczos_logquad(al, be, 1, m, z2, a, b, q, &ok); '
                    'return ok ? v : -1e300; }\n'
                    % os.path.join(ROOT, "paper_2503_02259_gb300", "csrc", "tridiag.cuh"))
     so = d / "tri.so"
@@ -130,17 +130,18 @@ def test_device_eigensolver_host_build_matches_lapack(tri, m):
         np.testing.assert_allclose(Q[idx] ** 2, U[0] ** 2, atol=1e-12)
 
 
-def test_device_gauss_quadrature_host_build_matches_oracle_rule(tri):
-    # The CG/Lanczos correspondence and the Gauss rule, host build vs LAPACK.
+def test_device_gauss_quadrature_host_build_matches_lapack_rule(tri):
+    # The device's Gauss rule from Lanczos coefficients, host build, vs the same
+    # rule through LAPACK's tridiagonal eigensolver on the same coefficients.
     import oracle as O
     from paper_2503_02259_gb300 import inputs
     X = inputs.points(150, 3, seed=3)
     A = O.khat_dense(X, O.GAUSSIAN, (0.1, 1.0, 0.3))
     z = O.rademacher_probes(150, 1, 9)[:, 0]
-    _, _, _, al, be = O.cg(A, z, 1e-14, 25)
+    a, b = O.lanczos(A, z, 20)
+    bb = np.append(b, 0.0)
     tri.quad.restype = ctypes.c_double
-    v = tri.quad(ctypes.c_void_p(al[0].ctypes.data), ctypes.c_void_p(be[0].ctypes.data), 20,
+    v = tri.quad(ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(bb.ctypes.data), a.size,
                  ctypes.c_double(150.0))
-    a, b = O.lanczos_from_cg(al[0], be[0], 20)
     ref = O.gauss_quadrature_log(a, b, 150.0)
     assert v == pytest.approx(ref, rel=1e-11)

