@@ -153,6 +153,36 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
 gp_status gp_kernel_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y,
                            int32_t prec, void* ws, size_t ws_bytes, void* stream);
 
+/* Y = Kh V exactly like gp_kernel_matmul with FP32 arithmetic, but without any
+ * device allocation and without a caller workspace.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory at the point of the call -- for example a plug-in running
+ * inside a host application (an inference server, another framework's
+ * custom-op hook) that owns the device allocator and forbids cudaMalloc in
+ * its execute callback, or a fixed-budget loop that must not allocate once it
+ * has started.  They still own V and Y.
+ *  - Scratch: a file-scope static device array of GP_NOALLOC_SCRATCH_BYTES
+ *    (32 MiB), which every GPU that loads the library keeps until the process
+ *    exits.  Problems whose scratch (staged points, padded V and the partial
+ *    sums of the product) does not fit are rejected with GP_ERR_ARG and a
+ *    message giving the bytes needed; the product is first re-planned with
+ *    fewer j-splits to fit.  At one split about n * (d_pad + 2 * w_pad) * 4
+ *    bytes are needed (d_pad = 2 for d <= 2, else d rounded up to a multiple
+ *    of 4; w_pad >= w, a multiple of 4), so n can reach about 120,000 at
+ *    d = 3, w = 32.
+ *  - Set-up: the first call on each device (with that device current) looks
+ *    up the array's device address once; make that first call before any
+ *    stream capture.
+ *  - Sharing: every call on a device uses the same array, which keeps the
+ *    previous call's contents (each call clears what must start at zero).
+ *    Calls whose work overlaps on the GPU (different streams or host threads
+ *    without ordering) race on the array; order them.
+ *  - Calls no cudaMalloc, cudaFree or allocating library routine.
+ *    Asynchronous on `stream`. */
+#define GP_NOALLOC_SCRATCH_BYTES (32u << 20)
+gp_status gp_kernel_matmul_noalloc(const gp_problem* prob, const float* V, int32_t w, float* Y,
+                                   void* stream);
+
 /* Fused product of Kh and its derivatives with one multivector, sharing one
  * distance/kernel evaluation per entry (the "kernel matrices and its
  * derivatives" of §Design and Implementation):

@@ -94,6 +94,8 @@ PROTOTYPES = {
     "gp_workspace_bytes": (c_size_t, [c_int32, POINTER(gp_problem), c_int32, POINTER(gp_solve_opts)]),
     "gp_kernel_matmul": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p, c_int32,
                                    c_void_p, c_size_t, c_void_p]),
+    "gp_kernel_matmul_noalloc": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,
+                                           c_void_p]),
     "gp_kernel_grad_matmul": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p, c_void_p,
                                         c_void_p, c_int32, c_void_p, c_size_t, c_void_p]),
     "gp_pcg_solve": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,

@@ -31,6 +31,7 @@ UNITS = [
     ("vec_kernels", "vec_kernels.cu", []),
     ("refine", "refine.cu", []),
     ("server", "server.cu", []),
+    ("static_scratch", "static_scratch.cu", []),
     ("gp_api", "gp_api.cu", []),
 ]
 
