@@ -65,10 +65,23 @@ typedef enum {
 
 typedef enum { GP_KERNEL_GAUSSIAN = 0, GP_KERNEL_MATERN32 = 1 } gp_kernel;
 
-/* Arithmetic of the K-tile x V-tile contraction.  FP32: CUDA-core FP32 FMA.
- * TF32 / BF16: tcgen05 tensor cores with operands rounded to that type and FP32
- * accumulation in tensor memory. */
-typedef enum { GP_PREC_FP32 = 0, GP_PREC_TF32 = 1, GP_PREC_BF16 = 2 } gp_precision;
+/* Arithmetic of the K-tile x V-tile contraction.
+ *  FP32:   CUDA-core FP32 FMA.
+ *  TF32:   tcgen05 tensor cores, kernel tile and V rounded to TF32, FP32
+ *          accumulation in tensor memory (about 3e-4 relative).
+ *  BF16:   kernel tile rounded to BF16, V as a BF16 high part plus a BF16
+ *          remainder (two products; a few 1e-3 relative).
+ *  TF32X3, BF16X3: both operands split into a high part and a rounded
+ *          remainder, accumulating hi*hi + hi*lo + lo*hi (FP32-level accuracy).
+ * Tensor-core accumulation restarts every 512 columns j and is summed in FP32.
+ * The tensor-core modes need w <= 128. */
+typedef enum {
+  GP_PREC_FP32 = 0,
+  GP_PREC_TF32 = 1,
+  GP_PREC_BF16 = 2,
+  GP_PREC_TF32X3 = 3,
+  GP_PREC_BF16X3 = 4
+} gp_precision;
 
 typedef enum {
   GP_OP_MATMUL = 0,       /* gp_kernel_matmul */

@@ -30,6 +30,8 @@ MATERN32 = 1
 PREC_FP32 = 0
 PREC_TF32 = 1
 PREC_BF16 = 2
+PREC_TF32X3 = 3
+PREC_BF16X3 = 4
 
 OP_MATMUL = 0
 OP_GRAD_MATMUL = 1

@@ -28,6 +28,10 @@ UNITS = [
     ("kmv_simt_k1_g0", "kmv_simt_inst.cu", ["-DGP_KIND=1", "-DGP_GRAD=0"]),
     ("kmv_simt_k1_g1", "kmv_simt_inst.cu", ["-DGP_KIND=1", "-DGP_GRAD=1"]),
     ("kmv_tc", "kmv_tc.cu", []),
+    ("kmv_tc_m1", "kmv_tc_inst.cu", ["-DGP_TC_MODE=1"]),
+    ("kmv_tc_m2", "kmv_tc_inst.cu", ["-DGP_TC_MODE=2"]),
+    ("kmv_tc_m3", "kmv_tc_inst.cu", ["-DGP_TC_MODE=3"]),
+    ("kmv_tc_m4", "kmv_tc_inst.cu", ["-DGP_TC_MODE=4"]),
     ("vec_kernels", "vec_kernels.cu", []),
     ("refine", "refine.cu", []),
     ("server", "server.cu", []),

@@ -203,11 +203,12 @@ struct ProdWs {
   float* vp;
   float* part_k;
   float* part_d;
+  void* vt;       // tensor-core B-operand tiles (NULL for FP32)
   int* err;
   size_t bytes;
 };
 
-static ProdWs carve_product(void* ws, const SimtPlan& p, bool grad, bool rect) {
+static ProdWs carve_product(void* ws, const SimtPlan& p, bool grad, bool rect, int prec) {
   Carve c(ws);
   ProdWs w;
   w.xc = c.take<float>(static_cast<size_t>(p.nc_pad) * p.dp);
@@ -215,9 +216,19 @@ static ProdWs carve_product(void* ws, const SimtPlan& p, bool grad, bool rect) {
   w.vp = c.take<float>(static_cast<size_t>(p.nc_pad) * p.w_pad);
   w.part_k = c.take<float>(static_cast<size_t>(p.split) * p.nr_pad * p.w_pad);
   w.part_d = grad ? c.take<float>(static_cast<size_t>(p.split) * p.nr_pad * p.w_pad) : nullptr;
+  const size_t vtb = tc_vt_bytes(p, prec);
+  w.vt = vtb ? static_cast<void*>(c.take<unsigned char>(vtb)) : nullptr;
   w.err = c.take<int>(64);
   w.bytes = c.off + 256;
   return w;
+}
+
+// The CG product (pc, possibly tensor-core) and the FP32 derivative product (pg)
+// share the solver arrays: give both the wider padded width.
+static void unify_width(SimtPlan& pc, SimtPlan& pg) {
+  const int w = std::max(pc.w_pad, pg.w_pad);
+  pc.w_pad = w;
+  pg.w_pad = w;
 }
 
 // Layout of the solver workspace (pcg / slq / loss).
@@ -230,6 +241,7 @@ struct SolveWs {
   float* Q;
   float* part;     // max(split_cg, 2 * split_grad) planes
   float* Lq;       // Lanczos basis: lz_k planes (NULL when no SLQ)
+  void* vt;        // tensor-core B-operand tiles (NULL for FP32)
   double* red;
   CgState* S;      // block-CG state
   CgState* S2;     // Lanczos state
@@ -237,7 +249,7 @@ struct SolveWs {
 };
 
 static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, bool with_grad,
-                           int lz_k) {
+                           int lz_k, int prec) {
   Carve c(ws);
   SolveWs w;
   const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
@@ -250,6 +262,8 @@ static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, boo
   const size_t planes = std::max<size_t>(pc.split, with_grad ? 2 * static_cast<size_t>(pg.split) : 0);
   w.part = c.take<float>(planes * plane);
   w.Lq = lz_k > 0 ? c.take<float>(static_cast<size_t>(lz_k) * plane) : nullptr;
+  const size_t vtb = tc_vt_bytes(pc, prec);
+  w.vt = vtb ? static_cast<void*>(c.take<unsigned char>(vtb)) : nullptr;
   w.red = c.take<double>(red_doubles(pc.nr_pad, pc.w_pad));
   w.S = c.take<CgState>(1);
   w.S2 = c.take<CgState>(1);
@@ -305,14 +319,12 @@ static gp_status check_opts(const gp_solve_opts* o, bool need_probes) {
   if (o->nlanczos < 1 || o->nlanczos > GP_MAX_LANCZOS)
     return fail(GP_ERR_ARG, "nlanczos must be in [1, 64]");
   if (!(o->cg_rtol >= 0)) return fail(GP_ERR_ARG, "cg_rtol must be >= 0");
-  if (o->prec != GP_PREC_FP32 && o->prec != GP_PREC_TF32 && o->prec != GP_PREC_BF16)
-    return fail(GP_ERR_ARG, "unknown precision");
+  if (o->prec < GP_PREC_FP32 || o->prec > GP_PREC_BF16X3) return fail(GP_ERR_ARG, "unknown precision");
   return GP_OK;
 }
 
 static gp_status check_prec(int32_t prec) {
-  if (prec != GP_PREC_FP32 && prec != GP_PREC_TF32 && prec != GP_PREC_BF16)
-    return fail(GP_ERR_ARG, "unknown precision");
+  if (prec < GP_PREC_FP32 || prec > GP_PREC_BF16X3) return fail(GP_ERR_ARG, "unknown precision");
   return GP_OK;
 }
 
@@ -343,13 +355,11 @@ namespace gp {
 
 // One fused product Kh-sums of V into part_k / part_d (square, points staged).
 gp_status run_product(const SimtPlan& p, int kernel, bool grad, int prec, const float* xr,
-                      const float* xc, const float* vp, float* part_k, float* part_d,
+                      const float* xc, const float* vp, void* vt, float* part_k, float* part_d,
                       const int* active, int* err, cudaStream_t st) {
   if (prec != GP_PREC_FP32) {
-    TcArgs ta{xr, xc, vp, part_k, part_d, active, err};
-    profile_product_begin(st);
+    TcArgs ta{xr, xc, vp, vt, part_k, part_d, active, err};
     cudaError_t e = launch_tc(p, kernel, grad, prec, ta, st);
-    profile_product_end(st);
     if (e == cudaErrorNotSupported)
       return fail(GP_ERR_UNIMPLEMENTED, "tensor-core path not available for this shape");
     if (e != cudaSuccess) return cuda_fail(e, "launch_tc");
@@ -376,16 +386,16 @@ static gp_status product_call(const gp_problem* prob, const float* V, int32_t w,
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = prob->n;
   const SimtPlan p = plan_for(n, n, prob->d, w, grad, prob->kernel, prec);
-  ProdWs L = carve_product(nullptr, p, grad, false);
+  ProdWs L = carve_product(nullptr, p, grad, false, prec);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
-  L = carve_product(ws, p, grad, false);
+  L = carve_product(ws, p, grad, false, prec);
   const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
   GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
   GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
   if (w != p.w_pad) GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
   GP_CUDA(launch_pad_block(V, n, w, w, L.vp, p.nc_pad, p.w_pad, 0, st));
-  if ((s = run_product(p, prob->kernel, grad, prec, L.xc, L.xc, L.vp, L.part_k, L.part_d, nullptr,
-                       L.err, st)) != GP_OK)
+  if ((s = run_product(p, prob->kernel, grad, prec, L.xc, L.xc, L.vp, L.vt, L.part_k, L.part_d,
+                       nullptr, L.err, st)) != GP_OK)
     return s;
   const double f = prob->theta.f;
   EpiArgs e{};
@@ -431,7 +441,7 @@ gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W
   while (issued < maxit) {
     const int todo = std::min(chunk, maxit - issued);
     for (int k = 0; k < todo; ++k) {
-      gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.part, nullptr,
+      gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.vt, W.part, nullptr,
                                 &W.S->n_active, &W.S->err, st);
       if (s != GP_OK) return s;
       GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
@@ -463,7 +473,7 @@ gp_status run_lanczos(const gp_problem* prob, const SimtPlan& p, int prec, Solve
   GP_CUDA(launch_lz_init(S, W.B, W.Lq, p.nr_pad, p.w_pad, col0, np, W.red, st));
   for (int j = 0; j < k; ++j) {
     const float* Qj = W.Lq + j * plane;
-    gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, Qj, W.part, nullptr,
+    gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, Qj, W.vt, W.part, nullptr,
                               &S->n_active, &S->err, st);
     if (s != GP_OK) return s;
     GP_CUDA(launch_lz_epi_alpha(S, W.part, p.split, Qj, W.R, p.nr_pad, n, p.w_pad, f2,
@@ -504,9 +514,10 @@ static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int 
   const int64_t n = prob->n;
   out.pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
   out.pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
-  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad, lz_k);
+  unify_width(out.pc, out.pg);
+  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad, lz_k, prec);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
-  out.W = carve_solve(ws, out.pc, out.pg, with_grad, lz_k);
+  out.W = carve_solve(ws, out.pc, out.pg, with_grad, lz_k, prec);
   out.kc = kernel_consts(prob->kernel, prob->theta.l);
   GP_CUDA(cudaMemsetAsync(out.W.S, 0, sizeof(CgState), st));
   GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.cs, out.pc.dp,
@@ -569,7 +580,7 @@ static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, S
   GP_CUDA(launch_copy_col0(W.X, W.Q, pg.nr_pad, pg.w_pad, st));
   float* part_k = W.part;
   float* part_d = W.part + static_cast<size_t>(pg.split) * pg.nr_pad * pg.w_pad;
-  if ((s = run_product(pg, prob->kernel, true, GP_PREC_FP32, W.xs, W.xs, W.Q, part_k, part_d,
+  if ((s = run_product(pg, prob->kernel, true, GP_PREC_FP32, W.xs, W.xs, W.Q, nullptr, part_k, part_d,
                        nullptr, &W.S->err, st)) != GP_OK)
     return s;
   const double f = prob->theta.f;
@@ -662,7 +673,7 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
     case GP_OP_GRAD_MATMUL: {
       if (check_width(w) != GP_OK) return 0;
       const bool grad = op == GP_OP_GRAD_MATMUL;
-      return carve_product(nullptr, plan_for(n, n, prob->d, w, grad, prob->kernel, prec), grad, false)
+      return carve_product(nullptr, plan_for(n, n, prob->d, w, grad, prob->kernel, prec), grad, false, prec)
           .bytes;
     }
     case GP_OP_PREDICT: {
@@ -671,22 +682,23 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
         return 0;
       }
       return carve_product(nullptr, plan_for(w, n, prob->d, 1, false, prob->kernel, GP_PREC_FP32),
-                           false, true)
+                           false, true, GP_PREC_FP32)
           .bytes;
     }
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
       const SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
-      return carve_solve(nullptr, pc, pc, false, 0).bytes;
+      return carve_solve(nullptr, pc, pc, false, 0, prec).bytes;
     }
     case GP_OP_SLQ:
     case GP_OP_LOSS_GRAD: {
       if (check_opts(opts, op == GP_OP_SLQ) != GP_OK) return 0;
       const int ww = op == GP_OP_SLQ ? opts->nprobe : 1 + opts->nprobe;
-      const SimtPlan pc = plan_for(n, n, prob->d, ww, false, prob->kernel, prec);
-      const SimtPlan pg = plan_for(n, n, prob->d, ww, true, prob->kernel, GP_PREC_FP32);
+      SimtPlan pc = plan_for(n, n, prob->d, ww, false, prob->kernel, prec);
+      SimtPlan pg = plan_for(n, n, prob->d, ww, true, prob->kernel, GP_PREC_FP32);
+      unify_width(pc, pg);
       const int lz_k = opts->nprobe > 0 ? opts->nlanczos : 0;
-      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD, lz_k).bytes;
+      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD, lz_k, prec).bytes;
     }
   }
   set_error("unknown op");
@@ -701,10 +713,6 @@ gp_status gp_kernel_matmul(const gp_problem* prob, const float* V, int32_t w, fl
 gp_status gp_kernel_grad_matmul(const gp_problem* prob, const float* V, int32_t w, float* Y,
                                 float* dY_f, float* dY_l, int32_t prec, void* ws, size_t ws_bytes,
                                 void* stream) {
-  if (prec != GP_PREC_FP32 && (dY_f != nullptr || dY_l != nullptr)) {
-    // The tensor-core product carries the K tile only.
-    return fail(GP_ERR_UNIMPLEMENTED, "derivative products are FP32 only");
-  }
   return product_call(prob, V, w, Y, dY_f, dY_l, true, prec, ws, ws_bytes, stream);
 }
 
@@ -839,16 +847,16 @@ gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const floa
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = prob->n;
   const SimtPlan p = plan_for(m, n, prob->d, 1, false, prob->kernel, GP_PREC_FP32);
-  ProdWs L = carve_product(nullptr, p, false, true);
+  ProdWs L = carve_product(nullptr, p, false, true, GP_PREC_FP32);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
-  L = carve_product(ws, p, false, true);
+  L = carve_product(ws, p, false, true, GP_PREC_FP32);
   const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
   GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
   GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
   GP_CUDA(launch_stage_points(Xstar, m, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nr_pad, L.xr, st));
   GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
   GP_CUDA(launch_pad_block(alpha, n, 1, 1, L.vp, p.nc_pad, p.w_pad, 0, st));
-  if ((s = run_product(p, prob->kernel, false, GP_PREC_FP32, L.xr, L.xc, L.vp, L.part_k, nullptr,
+  if ((s = run_product(p, prob->kernel, false, GP_PREC_FP32, L.xr, L.xc, L.vp, nullptr, L.part_k, nullptr,
                        nullptr, L.err, st)) != GP_OK)
     return s;
   EpiArgs e{};

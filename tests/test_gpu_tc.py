@@ -1,0 +1,113 @@
+"""GPU parity of the tcgen05 tensor-core product against the FP64 oracle.
+
+Tolerances (norm-wise per column, as for the FP32 tests):
+  * TF32 operands, FP32 accumulation: <= 3e-3 (the mixed-precision tile bound);
+  * BF16 kernel tile with a hi/lo BF16 V: <= 1e-2 (each entry rounded to BF16
+    carries up to 2^-9 relative error; the derivative sums cancel more);
+  * split TF32 (hi*hi + hi*lo + lo*hi): <= 1e-5, the FP32 bound;
+  * split BF16: <= 3e-5 (a 16-bit hi + lo pair leaves 2^-17 per entry).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = {1: 3e-3, 2: 1e-2, 3: 1e-5, 4: 3e-5}   # TF32, BF16, TF32X3, BF16X3
+MODES = [1, 2, 3, 4]
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def colwise_relerr(got, ref):
+    got = np.asarray(got, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    if got.ndim == 1:
+        got, ref = got[:, None], ref[:, None]
+    num = np.linalg.norm(got - ref, axis=0)
+    den = np.linalg.norm(ref, axis=0)
+    return float(np.max(num / np.where(den > 0, den, 1.0)))
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_tc_smallest_tile(api, prec):
+    # One 128-row tile, four 32-point column tiles, N = 16.
+    n, w = 128, 16
+    X = inputs.points(n, 3, seed=1)
+    V = inputs.gaussian_block(n, w, seed=1)
+    theta = (0.1, 1.0, 0.3)
+    Y = api.gp_kernel_matmul(_dev(X), _dev(V), O.GAUSSIAN, theta, prec=prec).cpu().numpy()
+    rY, _, _ = O.kmv_rows(X, V, O.GAUSSIAN, theta)
+    assert colwise_relerr(Y, rY) <= TOL[prec]
+
+
+CASES = [
+    (1, 2, 1, O.GAUSSIAN),
+    (127, 3, 17, O.MATERN32),
+    (300, 8, 32, O.GAUSSIAN),
+    (2000, 3, 11, O.GAUSSIAN),
+    (2000, 2, 64, O.MATERN32),
+    (1537, 16, 33, O.MATERN32),
+    (1031, 4, 128, O.GAUSSIAN),
+]
+
+
+@pytest.mark.parametrize("prec", MODES)
+@pytest.mark.parametrize("n,d,w,kind", CASES)
+def test_tc_grad_matmul_matches_oracle(api, prec, n, d, w, kind):
+    theta = (0.05, 1.5, 0.2) if kind == O.MATERN32 else (0.1, 1.0, 0.3)
+    X = inputs.points(n, d, seed=n + d)
+    V = inputs.gaussian_block(n, w, seed=w)
+    import torch
+    Xd, Vd = _dev(X), _dev(V)
+    prob, _ = api.problem(Xd, kind, theta)
+    Y = torch.empty_like(Vd)
+    dYf = torch.empty_like(Vd)
+    dYl = torch.empty_like(Vd)
+    from paper_2503_02259_gb300 import _binding as B
+    ws = api.workspace(B.OP_GRAD_MATMUL, prob, w, api.solve_opts(prec=prec), Xd.device)
+    B.check(B.lib().gp_kernel_grad_matmul(B.ctypes.byref(prob), api._ptr(Vd), w, api._ptr(Y),
+                                          api._ptr(dYf), api._ptr(dYl), prec, api._ptr(ws),
+                                          ws.numel(), api._stream(Xd.device)), "grad_matmul")
+    rY, rF, rL = O.kmv_rows(X, V, kind, theta)
+    assert colwise_relerr(Y.cpu().numpy(), rY) <= TOL[prec]
+    assert colwise_relerr(dYf.cpu().numpy(), rF) <= TOL[prec]
+    if n > 1:
+        assert colwise_relerr(dYl.cpu().numpy(), rL) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", MODES)
+def test_tc_precision_config_sampled_rows(api, prec):
+    # n = 1e6, d = 2 uniform, Gaussian f = 1, l = 0.05, s = 0.01, V width 64.
+    prob = inputs.precision_problem(seed=0)
+    V = inputs.multivector(prob.y, 64, seed=0)
+    Y = api.gp_kernel_matmul(_dev(prob.X), _dev(V), prob.kind, prob.theta, prec=prec).cpu().numpy()
+    rows = np.sort(np.random.default_rng(3).choice(prob.n, 1000, replace=False))
+    rY, _, _ = O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows, block=20)
+    assert colwise_relerr(Y[rows], rY) <= TOL[prec]
+
+
+@pytest.mark.parametrize("prec", [3, 4])
+def test_tc_split_matches_oracle_at_fused_matvec_size(api, prec):
+    # n = 1e5, d = 3 uniform, Matern-3/2: long accumulation chains per row.
+    prob = inputs.matvec_problem(seed=0)
+    V = inputs.multivector(prob.y, 32, seed=0)
+    Y = api.gp_kernel_matmul(_dev(prob.X), _dev(V), prob.kind, prob.theta, prec=prec).cpu().numpy()
+    rows = np.sort(np.random.default_rng(5).choice(prob.n, 500, replace=False))
+    rY, _, _ = O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows, block=100)
+    assert colwise_relerr(Y[rows], rY) <= TOL[prec]
