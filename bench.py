@@ -163,6 +163,49 @@ def run_reference(args) -> int:
     return 0
 
 
+PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
+
+
+def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
+    """Each tensor-core mode on the bench workload: product-kernel throughput and the
+    norm-wise error of K.V and dK/dl.V against the FP64 oracle on 100 sampled rows."""
+    import oracle as O
+    rows = np.sort(np.random.default_rng(11).choice(prob.n, 100, replace=False))
+    rY, _, rL = O.kmv_rows(prob.X, V.cpu().numpy(), prob.kind, prob.theta, rows=rows, block=50)
+    L = B.lib()
+    out = {}
+    for name, prec in PRECS.items():
+        pr, _ = api.problem(X, prob.kind, prob.theta)
+        ws = api.workspace(B.OP_GRAD_MATMUL, pr, W, api.solve_opts(prec=prec), dev)
+        Y = torch.empty_like(V)
+        dYf = torch.empty_like(V)
+        dYl = torch.empty_like(V)
+
+        def step():
+            B.check(L.gp_kernel_grad_matmul(B.ctypes.byref(pr), api._ptr(V), W, api._ptr(Y),
+                                            api._ptr(dYf), api._ptr(dYl), prec, api._ptr(ws),
+                                            ws.numel(), api._stream(dev)), "grad_matmul")
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+        B.check(L.gp_profile_begin(), "profile")
+        for _ in range(steps):
+            step()
+        torch.cuda.synchronize()
+        ms = B.c_double()
+        n1 = B.c_int64()
+        n2 = B.c_int64()
+        B.check(L.gp_profile_end(B.ctypes.byref(ms), B.ctypes.byref(n1), B.ctypes.byref(n2)), "profile")
+        kms = ms.value / max(1, n1.value)
+        yh = Y.cpu().numpy()[rows].astype(np.float64)
+        lh = dYl.cpu().numpy()[rows].astype(np.float64)
+        err = float(np.max(np.linalg.norm(yh - rY, axis=0) / np.linalg.norm(rY, axis=0)))
+        errl = float(np.max(np.linalg.norm(lh - rL, axis=0) / np.linalg.norm(rL, axis=0)))
+        out[name] = {"kernel_ms": kms, "value": N_PTS * N_PTS * W / (kms * 1e-3), "unit": UNIT,
+                     "relerr_Y": err, "relerr_dYl": errl}
+    return out
+
+
 def loss_grad_small(api, torch, reps: int = 3) -> dict:
     """Loss + gradient per Theta on the small configuration (n=2000, d=3, Gaussian)."""
     from paper_2503_02259_gb300 import inputs
@@ -191,6 +234,7 @@ def main() -> int:
     ap.add_argument("--impl", default="gp", choices=["gp", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--prec", default="fp32", choices=list(PRECS), help="arithmetic of the product")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -221,14 +265,15 @@ def main() -> int:
     dYf = torch.empty_like(V)
     dYl = torch.empty_like(V)
     pr, _ = api.problem(X, prob.kind, prob.theta)
-    ws = api.workspace(B.OP_GRAD_MATMUL, pr, W, None, dev)
+    prec = PRECS[args.prec]
+    ws = api.workspace(B.OP_GRAD_MATMUL, pr, W, api.solve_opts(prec=prec), dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     L = B.lib()
     stream = torch.cuda.current_stream(dev)
 
     def step():
         B.check(L.gp_kernel_grad_matmul(B.ctypes.byref(pr), api._ptr(V), W, api._ptr(Y),
-                                        api._ptr(dYf), api._ptr(dYl), B.PREC_FP32, api._ptr(ws),
+                                        api._ptr(dYf), api._ptr(dYl), prec, api._ptr(ws),
                                         ws.numel(), api._stream(dev)), "gp_kernel_grad_matmul")
 
     for _ in range(max(3, args.warmup)):
@@ -281,7 +326,7 @@ def main() -> int:
         Xd.copy_(Xp, non_blocking=True)
         Vd.copy_(Vp, non_blocking=True)
         B.check(L.gp_kernel_grad_matmul(B.ctypes.byref(pr2), api._ptr(Vd), W, api._ptr(Y),
-                                        api._ptr(dYf), api._ptr(dYl), B.PREC_FP32, api._ptr(ws),
+                                        api._ptr(dYf), api._ptr(dYl), prec, api._ptr(ws),
                                         ws.numel(), api._stream(dev)), "gp_kernel_grad_matmul")
         for o, src in zip(outs, (Y, dYf, dYl)):
             o.copy_(src, non_blocking=True)
@@ -294,6 +339,7 @@ def main() -> int:
     extras = {}
     if rank == 0 and not args.no_extras:
         extras["loss_grad"] = loss_grad_small(api, torch)
+        extras["precision_modes"] = precision_modes(api, B, torch, prob, X, V, dev)
 
     if rank != 0:
         if dist:
@@ -306,15 +352,31 @@ def main() -> int:
     peaks = _peaks()
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
     kern_ms = prod_ms.value / max(1, prod_n.value)
-    flops_per_launch = N_PTS * N_PTS * (4 * W + 3 * D + 6)
+    if prec == 0:
+        # FP32 pipe: evaluation (3d + 6 flops per entry, Matern) + contraction (4w per entry).
+        flops_per_launch = N_PTS * N_PTS * (4 * W + 3 * D + 6)
+        peak = 2 * 128 * 152 * sm_mhz * 1e6 / 1e12
+        tr = _traffic().get("kmv_simt_matern_d3_w32_grad")
+        kname = "kmv_simt_kernel<MATERN32,grad,D=3,TW=32>"
+        bound = "alu"
+        psrc = (f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled SM "
+                "clock in the timed region)")
+    else:
+        # Tensor pipe: products per entry = NPROD x 2 (K and D) x 2w flops.
+        nprod = {1: 1, 2: 2, 3: 3, 4: 3}[prec]
+        flops_per_launch = N_PTS * N_PTS * 2 * W * nprod * 2
+        ratio = 0.5 if prec in (1, 3) else 1.0
+        peak = peaks.get("bf16_tflops", 1900.0) * ratio
+        tr = _traffic().get(f"kmv_tc_matern_d3_w32_grad_{args.prec}")
+        kname = f"kmv_tc_kernel<MATERN32,grad,D=3,{args.prec}>"
+        bound = "tensor"
+        psrc = ("measured cuBLAS bf16 dense peak (MEASURED_PEAKS.json)"
+                + (" x 0.5, the nominal tf32:bf16 ratio" if ratio != 1.0 else ""))
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
-    peak = 2 * 128 * 152 * sm_mhz * 1e6 / 1e12
-    tr = _traffic().get("kmv_simt_matern_d3_w32_grad")
-    roofline = {"bound": "alu", "kernel": "kmv_simt_kernel<MATERN32,grad,D=3,TW=32>",
+    roofline = {"bound": bound, "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tr.get("bytes_per_launch") if tr else None,
-                "peak_source": f"FP32 pipe: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median "
-                               "sampled SM clock in the timed region)",
+                "peak_source": psrc,
                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops_per_launch,
                 "kernel_share_of_step": kern_ms / per_step_ms}
     cpu = None
@@ -322,7 +384,9 @@ def main() -> int:
         cpu = cpu_oracle_rate()
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step_ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f32", 1: "tf32", 2: "bf16", 3: "tf32x3", 4: "bf16x3"}[prec],
+            "data": "synthetic",
             "config": {"workload": WORKLOAD, "l2": "flushed between steps (256 MiB write outside "
                                                    "the timed bracket)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
