@@ -24,7 +24,7 @@ enum DevErr : int { kDevOk = 0, kDevTimeout = 1, kDevBreakdown = 2, kDevNumeric 
 
 // Bounded spin limit for mbarrier waits (iterations of try_wait, each of which
 // may itself suspend for a hardware-defined interval).
-constexpr long long kSpinLimit = 1ll << 26;
+constexpr long long kSpinLimit = 1ll << 22;
 
 // ---------------------------------------------------------------------------
 // Kernel-evaluation constants derived from Theta (host side).

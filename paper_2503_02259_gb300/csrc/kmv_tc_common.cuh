@@ -1,0 +1,202 @@
+// Shared pieces of the tensor-core (tcgen05) product: operand modes, the
+// K-major core-matrix geometry (8 rows x 16 bytes per core matrix, no swizzle),
+// shared- and tensor-memory descriptors, and the PTX wrappers for tcgen05.mma,
+// commit, fences, tensor-memory loads and stores.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kmv_simt.cuh"
+#include "kmv_tc.cuh"
+
+namespace gp {
+
+constexpr int kTcM = 128;        // rows per CTA = MMA M
+constexpr int kTcBK = 32;        // points j per tile = MMA K extent per tile
+constexpr int kTcEvalThreads = 256;  // eval warps 0-7: two threads per row
+constexpr int kTcThreads = 288;      // + one control warp (copies and MMA issue)
+constexpr int kTcBStages = 3;
+constexpr int kTcAStages = 2;
+constexpr int kTcNumBars = 2 * kTcBStages + 2 * kTcAStages + 1;
+constexpr int kTcFlush = 16;     // tiles per accumulation block
+
+// NSA / NSB: parts the A (kernel tile) and B (V tile) operands are split into
+// (hi, or hi + rounded remainder lo); NPROD: MMAs per K-step and accumulator.
+//   TF32:   A tf32,          B tf32          -> A B
+//   BF16:   A bf16,          B bf16 hi + lo  -> A B_hi + A B_lo
+//   TF32x3: A tf32 hi + lo,  B tf32 hi + lo  -> A_hi B_hi + A_hi B_lo + A_lo B_hi
+//   BF16x3: A bf16 hi + lo,  B bf16 hi + lo  -> the same three products
+template <int MODE>
+struct TcTraits;
+template <>
+struct TcTraits<kTcTF32> {
+  static constexpr int ES = 4, NSA = 1, NSB = 1, NPROD = 1;
+  static constexpr uint32_t FMT = 2;  // instruction-descriptor operand format: TF32
+};
+template <>
+struct TcTraits<kTcBF16> {
+  static constexpr int ES = 2, NSA = 1, NSB = 2, NPROD = 2;
+  static constexpr uint32_t FMT = 1;  // BF16
+};
+template <>
+struct TcTraits<kTcTF32x3> {
+  static constexpr int ES = 4, NSA = 2, NSB = 2, NPROD = 3;
+  static constexpr uint32_t FMT = 2;
+};
+template <>
+struct TcTraits<kTcBF16x3> {
+  static constexpr int ES = 2, NSA = 2, NSB = 2, NPROD = 3;
+  static constexpr uint32_t FMT = 1;
+};
+
+// Geometry shared by host and device.
+template <int MODE>
+struct TcGeom {
+  static constexpr int ES = TcTraits<MODE>::ES;
+  static constexpr int EPC = 16 / ES;                 // elements per 16-byte core-matrix row
+  static constexpr int CK = kTcBK / EPC;              // core matrices along K per tile
+  static constexpr uint32_t SBO = CK * 128;           // bytes between 8-row groups
+  static constexpr uint32_t LBO = 128;                // bytes between K-adjacent core matrices
+  static constexpr int KSTEPS = CK / 2;               // MMAs (32 bytes of K each) per tile
+  static constexpr uint32_t A_BYTES = (kTcM / 8) * SBO;
+};
+
+namespace tc {
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr & 0x3FFFFu) >> 4);
+  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
+  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
+  d |= static_cast<uint64_t>(1) << 46;  // descriptor version of tcgen05
+  return d;                             // base offset 0, layout: no swizzle
+}
+
+template <int MODE>
+__device__ __forceinline__ void mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                    uint32_t acc) {
+  if constexpr (TcTraits<MODE>::FMT == 1) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  } else {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc));
+  }
+}
+
+__device__ __forceinline__ void commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          dev::smem_addr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+      "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]),
+      "r"(r[15]));
+}
+
+__device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// Store 16 bytes of one operand row (EPC entries) at `off` of the hi matrix and,
+// when SPLIT, the rounded remainder at `off` of the lo matrix (generic proxy).
+template <int MODE, bool SPLIT>
+__device__ __forceinline__ void store_group(unsigned char* hi, unsigned char* lo, uint32_t off,
+                                            const float (&v)[16 / TcTraits<MODE>::ES]) {
+  if constexpr (TcTraits<MODE>::FMT == 1) {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+      h[u] = *reinterpret_cast<const uint32_t*>(&p);
+      if constexpr (SPLIT) {
+        const float2 back = __bfloat1622float2(p);
+        const __nv_bfloat162 r = __floats2bfloat162_rn(v[2 * u] - back.x, v[2 * u + 1] - back.y);
+        l[u] = *reinterpret_cast<const uint32_t*>(&r);
+      }
+    }
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if constexpr (SPLIT) *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  } else {
+    uint32_t h[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) h[u] = to_tf32(v[u]);
+    *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    if constexpr (SPLIT) {
+      uint32_t l[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) l[u] = to_tf32(v[u] - __uint_as_float(h[u]));
+      *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+  }
+}
+
+}  // namespace tc
+
+// Shared-memory plan of one launch (host and device agree on it).
+struct TcSmem {
+  uint32_t bars, sx, sb, sa, total;
+  uint32_t xbytes, bbytes, abytes;  // per stage / per matrix
+};
+
+template <int MODE, int DT>
+__host__ __device__ inline TcSmem tc_smem(int n, bool grad) {
+  using G = TcGeom<MODE>;
+  constexpr int DP = DimTraits<DT>::DP;
+  TcSmem s;
+  s.xbytes = kTcBK * DP * 4;
+  s.bbytes = static_cast<uint32_t>(n / 8) * G::SBO;
+  s.abytes = G::A_BYTES;
+  s.bars = 0;                                 // kTcNumBars mbarriers, tmem holder, abort flag
+  s.sx = 128;
+  s.sb = s.sx + ((kTcBStages * s.xbytes + 127) / 128) * 128;
+  s.sa = s.sb + kTcBStages * TcTraits<MODE>::NSB * s.bbytes;
+  s.total = s.sa + kTcAStages * (grad ? 2 : 1) * TcTraits<MODE>::NSA * s.abytes;
+  return s;
+}
+
+// Tensor-memory columns: accumulators [0, NMAT*n) and running sums [NMAT*n, 2*NMAT*n).
+__host__ __device__ inline uint32_t tc_tmem_cols(int n, bool grad) {
+  const int need = 2 * (grad ? 2 : 1) * n;
+  uint32_t c = 32;
+  while (c < static_cast<uint32_t>(need)) c <<= 1;
+  return c;
+}
+
+
+}  // namespace gp
