@@ -218,6 +218,21 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
                        const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                        size_t ws_bytes, void* stream);
 
+/* Mixed-precision iterative refinement of Kh Xsol = B with an FP64 solution.
+ * Outer loop: R = B - Kh X with FP64 kernel entries and FP64 sums from the FP32
+ * points, X held in FP64; inner loop: block CG on the product of precision
+ * opts->prec (a tensor-core mode, or FP32) for Kh D = R to opts->cg_rtol, then
+ * X += D; stop each column at ||R|| / ||B|| <= opts->refine_rtol or after
+ * opts->refine_maxit outer steps.  B: device n x w float32; X64: device n x w
+ * float64 (returning the refined solution in FP32 would cost about
+ * u ||Kh|| ||X|| / ||B|| of residual).  iters[w]: total inner CG iterations;
+ * relres[w]: final outer relative residual (FP64).  Workspace:
+ * gp_workspace_bytes(GP_OP_PCG, prob, w, opts) with opts->refine_rtol > 0.
+ * The FP64 residual is O(n^2 w) FP64 work per outer step.  Synchronises. */
+gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w, double* X64,
+                               const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
+                               size_t ws_bytes, void* stream);
+
 /* SLQ estimate of log|Kh| (Eq. 1 with M = I; stochastic Lanczos quadrature):
  * the Lanczos tridiagonal T_k of each probe z_i is read off the first k CG
  * step coefficients of the column z_i, eigen-decomposed on the device in FP64,
@@ -276,11 +291,31 @@ gp_status gp_profile_begin(void);
 gp_status gp_profile_end(double* product_ms, int64_t* product_launches, int64_t* total_launches);
 
 /* ---------------------------------------------------------------------------
- * Serving: a continuous-batching request server on one device.
- * Requests carry HOST arrays that are copied in at submit; the server owns its
- * device memory, bounded by hbm_budget_bytes (admission by footprint).
+ * Serving: a continuous-batching request server on one device (the stateless
+ * loss/gradient and prediction calls of §Design and Implementation, served as
+ * a stream of requests; the paper has no server).
+ *  - gp_server_create reserves one device pool of hbm_budget_bytes and starts
+ *    max_slots worker threads, each with its own CUDA stream.
+ *  - gp_server_submit copies the request's HOST arrays into pinned staging and
+ *    queues it; a request whose footprint (inputs + outputs + solver
+ *    workspace) exceeds the whole budget is refused with GP_ERR_OOM.
+ *  - Admission is first come, first served: the queue head starts as soon as a
+ *    worker is free and its footprint fits the pool's free space, so requests
+ *    that arrive while others run join them on the device; their kernels
+ *    overlap through the workers' streams.
+ *  - Kind 0 runs gp_loss_and_grad; kind 1 solves alpha = Kh^-1 y by block CG and
+ *    returns the posterior mean at Xstar.  With a fixed CG budget (cg_maxit) a
+ *    result may carry GP_ERR_NOT_CONVERGED with its estimates filled in.
+ *  - Results do not depend on what else runs: every kernel is deterministic.
  * ------------------------------------------------------------------------- */
 typedef struct gp_server gp_server;
+
+typedef struct {
+  int64_t submitted, completed, refused;
+  int64_t peak_active;     /* most requests on the device at once */
+  size_t peak_bytes;       /* most pool bytes in use at once */
+  size_t budget_bytes;
+} gp_server_stats;
 
 typedef struct {
   int32_t kind;            /* 0 = loss + gradient, 1 = posterior-mean prediction */
@@ -322,8 +357,15 @@ gp_status gp_server_submit(gp_server* srv, const gp_request* req, uint64_t* tick
 /* Non-blocking: GP_OK and *res filled if the ticket is done (res->mu, if non-NULL,
  * receives the prediction), GP_ERR_TIMEOUT if still pending. */
 gp_status gp_server_poll(gp_server* srv, uint64_t ticket, gp_result* res);
-/* Block until every submitted request is done or timeout_s elapses. */
+/* Block until every submitted request is done (GP_OK) or timeout_s elapses
+ * (GP_ERR_TIMEOUT). */
 gp_status gp_server_drain(gp_server* srv, double timeout_s);
+/* Counters since creation. */
+gp_status gp_server_get_stats(gp_server* srv, gp_server_stats* out);
+/* Footprint in bytes the server charges a request (0 on invalid arguments). */
+size_t gp_server_footprint(const gp_request* req);
+/* Stop the workers after the running requests finish; queued requests are
+ * dropped.  Frees the pool. */
 gp_status gp_server_destroy(gp_server* srv);
 
 #ifdef __cplusplus

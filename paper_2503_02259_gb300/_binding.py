@@ -82,6 +82,11 @@ class gp_request(ctypes.Structure):
                 ("cg_rtol", c_double), ("seed", c_uint64), ("prec", c_int32), ("reserved", c_int32)]
 
 
+class gp_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", c_int64), ("completed", c_int64), ("refused", c_int64),
+                ("peak_active", c_int64), ("peak_bytes", c_size_t), ("budget_bytes", c_size_t)]
+
+
 class gp_result(ctypes.Structure):
     _fields_ = [("status", c_int32), ("cg_iters", c_int32), ("loss", c_double),
                 ("grad", c_double * 3), ("relres", c_double), ("t_submit_s", c_double),
@@ -103,6 +108,9 @@ PROTOTYPES = {
     "gp_pcg_solve": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,
                                POINTER(gp_solve_opts), POINTER(c_int32), POINTER(c_double),
                                c_void_p, c_size_t, c_void_p]),
+    "gp_pcg_solve_refined": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,
+                                       POINTER(gp_solve_opts), POINTER(c_int32), POINTER(c_double),
+                                       c_void_p, c_size_t, c_void_p]),
     "gp_slq_logdet": (c_int32, [POINTER(gp_problem), POINTER(gp_solve_opts), POINTER(c_double),
                                 POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "gp_loss_and_grad": (c_int32, [POINTER(gp_problem), c_void_p, POINTER(gp_solve_opts),
@@ -123,6 +131,8 @@ PROTOTYPES = {
     "gp_server_submit": (c_int32, [c_void_p, POINTER(gp_request), POINTER(c_uint64)]),
     "gp_server_poll": (c_int32, [c_void_p, c_uint64, POINTER(gp_result)]),
     "gp_server_drain": (c_int32, [c_void_p, c_double]),
+    "gp_server_get_stats": (c_int32, [c_void_p, POINTER(gp_server_stats)]),
+    "gp_server_footprint": (c_size_t, [POINTER(gp_request)]),
     "gp_server_destroy": (c_int32, [c_void_p]),
 }
 

@@ -112,6 +112,25 @@ def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converge
     return Xsol, list(iters), list(relres), st
 
 
+def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True):
+    """Mixed-precision iterative refinement with an FP64 solution:
+    returns (X64 (n, w) float64, total inner iterations (w,), final relres (w,), status)."""
+    prob, X = problem(X, kernel, theta)
+    Bm = _f32(Bm, "B")
+    if Bm.dim() == 1:
+        Bm = Bm[:, None]
+    n, w = Bm.shape
+    X64 = torch.empty((n, w), dtype=torch.float64, device=X.device)
+    iters = (c_int32 * w)()
+    relres = (c_double * w)()
+    ws = workspace(B.OP_PCG, prob, w, opts, X.device)
+    st = lib().gp_pcg_solve_refined(byref(prob), _ptr(Bm), w, _ptr(X64), byref(opts), iters, relres,
+                                    _ptr(ws), ws.numel(), _stream(X.device))
+    if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
+        check(st, "gp_pcg_solve_refined")
+    return X64, list(iters), list(relres), st
+
+
 def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts):
     prob, X = problem(X, kernel, theta)
     ld = c_double()

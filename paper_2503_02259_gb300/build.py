@@ -33,7 +33,6 @@ UNITS = [
     ("kmv_tc_m3", "kmv_tc_inst.cu", ["-DGP_TC_MODE=3"]),
     ("kmv_tc_m4", "kmv_tc_inst.cu", ["-DGP_TC_MODE=4"]),
     ("vec_kernels", "vec_kernels.cu", []),
-    ("refine", "refine.cu", []),
     ("server", "server.cu", []),
     ("static_scratch", "static_scratch.cu", []),
     ("gp_api", "gp_api.cu", []),

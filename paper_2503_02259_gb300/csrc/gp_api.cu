@@ -641,6 +641,78 @@ static gp_status check_conv(const CgState* S, int w, int maxit, double rtol, cud
 }
 
 // ---------------------------------------------------------------------------
+// Mixed-precision iterative refinement.  Outer loop: r = B - Kh x with FP64
+// kernel entries and sums (x in FP64); stop when ||r_c|| / ||B_c|| <=
+// refine_rtol for every column.  Inner loop: block CG on the tensor-core
+// product (opts->prec) for Kh d = r to opts->cg_rtol; x += d.
+// Workspace: the solver workspace of the inner CG, then x (FP64), r (FP64) and
+// the padded right-hand side (FP32).
+// ---------------------------------------------------------------------------
+static size_t refine_extra_offset(const SimtPlan& pc, int prec) {
+  return (carve_solve(nullptr, pc, pc, false, 0, prec).bytes + 255) & ~static_cast<size_t>(255);
+}
+
+static size_t refine_bytes(const SimtPlan& pc, int prec) {
+  const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
+  return refine_extra_offset(pc, prec) + 2 * plane * sizeof(double) + plane * sizeof(float) + 1024;
+}
+
+gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol, double* X64,
+                       const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
+                       size_t ws_bytes, cudaStream_t st) {
+  gp_status s;
+  const int64_t n = prob->n;
+  const int prec = opts->prec;
+  SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+  SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
+  unify_width(pc, pg);   // the widths setup_solve uses
+  if ((s = check_ws(ws, ws_bytes, refine_bytes(pc, prec))) != GP_OK) return s;
+  SolveSetup ss;
+  if ((s = setup_solve(prob, w, false, prec, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  const size_t plane = static_cast<size_t>(ss.pc.nr_pad) * ss.pc.w_pad;
+  char* extra = static_cast<char*>(ws) + refine_extra_offset(ss.pc, prec);
+  double* x64 = reinterpret_cast<double*>(extra);
+  double* r64 = x64 + plane;
+  float* Bp = reinterpret_cast<float*>(r64 + plane);
+  GP_CUDA(cudaMemsetAsync(x64, 0, 2 * plane * sizeof(double), st));
+  GP_CUDA(cudaMemsetAsync(Bp, 0, plane * sizeof(float), st));
+  GP_CUDA(cudaMemsetAsync(ss.W.S2, 0, sizeof(CgState), st));
+  GP_CUDA(launch_pad_block(B, n, w, w, Bp, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  const double f2 = prob->theta.f * prob->theta.f;
+  const int max_outer = opts->refine_maxit > 0 ? opts->refine_maxit : 10;
+  const int inner_maxit = effective_maxit(prob, opts);
+  std::vector<int> total_iters(w, 0);
+  HostCg hr;
+  for (int outer = 0;; ++outer) {
+    GP_CUDA(launch_refine_residual(prob->X, n, prob->d, prob->kernel, prob->theta.l, f2,
+                                   prob->theta.s, x64, Bp, r64, ss.pc.nr_pad, ss.pc.w_pad, w, st));
+    GP_CUDA(launch_refine_norms(ss.W.S2, r64, Bp, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, w, ss.W.red, st));
+    if ((s = read_cg(ss.W.S2, hr, st)) != GP_OK) return s;
+    bool done = true;
+    for (int c = 0; c < w; ++c) done = done && !(hr.relres[c] > opts->refine_rtol);
+    if (done || outer >= max_outer) break;
+    if ((s = run_cg(prob, ss.pc, prec, ss.W, w, inner_maxit, opts->cg_rtol, st)) != GP_OK) return s;
+    HostCg hi;
+    if ((s = read_cg(ss.W.S, hi, st)) != GP_OK) return s;
+    for (int c = 0; c < w; ++c) total_iters[c] += hi.iters[c];
+    GP_CUDA(launch_refine_update(x64, ss.W.X, ss.pc.nr_pad, ss.pc.w_pad, w, st));
+  }
+  if (Xsol != nullptr) GP_CUDA(launch_refine_out(x64, Xsol, n, ss.pc.w_pad, w, st));
+  if (X64 != nullptr)
+    GP_CUDA(cudaMemcpy2DAsync(X64, sizeof(double) * w, x64, sizeof(double) * ss.pc.w_pad,
+                              sizeof(double) * w, n, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  bool conv = true;
+  for (int c = 0; c < w; ++c) {
+    if (iters) iters[c] = total_iters[c];
+    if (relres) relres[c] = hr.relres[c];
+    conv = conv && !(hr.relres[c] > opts->refine_rtol);
+  }
+  if (!conv) return fail(GP_ERR_NOT_CONVERGED, "refinement reached refine_maxit before refine_rtol");
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Exported entry points.
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -687,7 +759,11 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
     }
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
-      const SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+      SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+      SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
+      unify_width(pc, pg);
+      if (opts != nullptr && opts->refine_rtol > 0)
+        return refine_bytes(pc, prec);
       return carve_solve(nullptr, pc, pc, false, 0, prec).bytes;
     }
     case GP_OP_SLQ:
@@ -726,7 +802,7 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if (B == nullptr || Xsol == nullptr) return fail(GP_ERR_ARG, "B and Xsol must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
-    return refine_solve(prob, B, w, Xsol, opts, iters, relres, ws, ws_bytes, st);
+    return refine_solve(prob, B, w, Xsol, nullptr, opts, iters, relres, ws, ws_bytes, st);
   SolveSetup ss;
   if ((s = setup_solve(prob, w, false, opts->prec, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
   GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
@@ -741,6 +817,19 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
     if (relres) relres[c] = h.relres[c];
   }
   return check_conv(ss.W.S, w, maxit, opts->cg_rtol, st);
+}
+
+gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w, double* X64,
+                               const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
+                               size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (B == nullptr || X64 == nullptr) return fail(GP_ERR_ARG, "B and X64 must be non-NULL");
+  if (!(opts->refine_rtol > 0)) return fail(GP_ERR_ARG, "refine_rtol must be > 0");
+  return refine_solve(prob, B, w, nullptr, X64, opts, iters, relres, ws, ws_bytes,
+                      static_cast<cudaStream_t>(stream));
 }
 
 gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, double* logdet,

@@ -12,6 +12,7 @@ SimtPlan plan_for(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel, i
 }  // namespace gp
 
 // Mixed-precision iterative refinement (refine.cu).
-gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol,
+// Writes the solution to Xsol (FP32) and/or X64 (FP64); either may be NULL.
+gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol, double* X64,
                        const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                        size_t ws_bytes, cudaStream_t st);

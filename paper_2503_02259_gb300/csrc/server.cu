@@ -1,13 +1,391 @@
-// Continuous-batching request server (placeholder until the server is built).
+// Continuous-batching request server (include/gp.h, "Serving").
+//
+// One device pool of the HBM budget is reserved at creation and sub-allocated
+// first-fit; max_slots worker threads each own a CUDA stream.  A worker takes
+// the queue head as soon as the head's footprint fits the pool's free space,
+// runs the request through the library's own calls on its stream and returns
+// the memory, so requests that arrive while others are running join them on
+// the device and their kernels overlap through the streams.  The paper serves
+// nothing; its stateless loss/gradient and prediction calls (§Design and
+// Implementation) are what each request runs.
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <vector>
+
 #include "gp_api_internal.h"
 
+namespace {
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+// First-fit allocator over [0, size) of the pool, with coalescing frees.
+class PoolAllocator {
+ public:
+  explicit PoolAllocator(size_t size) : size_(size) { free_[0] = size; }
+  bool alloc(size_t bytes, size_t* off) {
+    bytes = align_up(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= bytes) {
+        *off = it->first;
+        const size_t rest = it->second - bytes;
+        const size_t start = it->first + bytes;
+        free_.erase(it);
+        if (rest > 0) free_[start] = rest;
+        in_use_ += bytes;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t bytes) {
+    bytes = align_up(bytes);
+    in_use_ -= bytes;
+    auto it = free_.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != free_.end() && it->first + it->second == next->first) {
+      it->second += next->second;
+      free_.erase(next);
+    }
+    if (it != free_.begin()) {
+      auto prev = std::prev(it);
+      if (prev->first + prev->second == it->first) {
+        prev->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+  size_t in_use() const { return in_use_; }
+
+ private:
+  size_t size_;
+  size_t in_use_ = 0;
+  std::map<size_t, size_t> free_;
+};
+
+// Device sub-buffers of one request inside its pool block.
+struct JobLayout {
+  size_t x, y, xs, mu, alpha, ws, ws_bytes, total;
+};
+
+const float* const kSizingX = reinterpret_cast<const float*>(kAlign);  // never dereferenced
+
+gp_solve_opts opts_of(const gp_request& r, bool loss) {
+  gp_solve_opts o{};
+  o.nprobe = loss ? r.nprobe : 0;
+  o.nlanczos = r.nlanczos > 0 ? r.nlanczos : 20;
+  o.cg_maxit = r.cg_maxit;
+  o.prec = r.prec;
+  o.cg_rtol = r.cg_rtol;
+  o.seed = r.seed;
+  return o;
+}
+
+bool layout_of(const gp_request& r, JobLayout* L) {
+  if (r.n < 1 || r.d < 1 || r.d > GP_MAX_DIM) return false;
+  if (r.kind != 0 && r.kind != 1) return false;
+  if (r.kind == 1 && r.m < 1) return false;
+  gp_problem prob{kSizingX, r.n, r.d, r.kernel, r.theta};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  L->x = take(sizeof(float) * r.n * r.d);
+  L->y = take(sizeof(float) * r.n);
+  L->xs = L->mu = L->alpha = 0;
+  size_t wsb = 0;
+  if (r.kind == 0) {
+    const gp_solve_opts o = opts_of(r, true);
+    wsb = gp_workspace_bytes(GP_OP_LOSS_GRAD, &prob, 0, &o);
+  } else {
+    L->xs = take(sizeof(float) * r.m * r.d);
+    L->mu = take(sizeof(float) * r.m);
+    L->alpha = take(sizeof(float) * r.n);
+    const gp_solve_opts o = opts_of(r, false);
+    wsb = std::max(gp_workspace_bytes(GP_OP_PCG, &prob, 1, &o),
+                   gp_workspace_bytes(GP_OP_PREDICT, &prob, static_cast<int32_t>(r.m), nullptr));
+  }
+  if (wsb == 0) return false;
+  L->ws = take(wsb);
+  L->ws_bytes = wsb;
+  L->total = off;
+  return true;
+}
+
+struct Job {
+  uint64_t ticket = 0;
+  gp_request req{};
+  JobLayout lay{};
+  float* hX = nullptr;   // pinned staging (inputs) and results
+  float* hy = nullptr;
+  float* hXs = nullptr;
+  float* hmu = nullptr;
+  gp_result res{};
+  bool done = false;
+};
+
+double seconds_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+
+struct gp_server {
+  int device = 0;
+  char* pool = nullptr;
+  size_t budget = 0;
+  std::unique_ptr<PoolAllocator> alloc;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::shared_ptr<Job>> queue;
+  std::map<uint64_t, std::shared_ptr<Job>> jobs;
+  std::vector<std::thread> workers;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  int64_t submitted = 0, completed = 0, refused = 0, active = 0, peak_active = 0;
+  size_t peak_bytes = 0;
+  std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+};
+
+namespace {
+
+void free_staging(Job& j) {
+  if (j.hX) cudaFreeHost(j.hX);
+  if (j.hy) cudaFreeHost(j.hy);
+  if (j.hXs) cudaFreeHost(j.hXs);
+  if (j.hmu) cudaFreeHost(j.hmu);
+  j.hX = j.hy = j.hXs = j.hmu = nullptr;
+}
+
+// Run one request on `st` inside its pool block; fills j.res.
+void run_job(gp_server* srv, Job& j, char* base, cudaStream_t st) {
+  const gp_request& r = j.req;
+  float* dX = reinterpret_cast<float*>(base + j.lay.x);
+  float* dy = reinterpret_cast<float*>(base + j.lay.y);
+  void* ws = base + j.lay.ws;
+  gp_status s = GP_OK;
+  cudaError_t e = cudaMemcpyAsync(dX, j.hX, sizeof(float) * r.n * r.d, cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dy, j.hy, sizeof(float) * r.n, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) {
+    j.res.status = GP_ERR_CUDA;
+    return;
+  }
+  gp_problem prob{dX, r.n, r.d, r.kernel, r.theta};
+  if (r.kind == 0) {
+    const gp_solve_opts o = opts_of(r, true);
+    gp_loss_info info{};
+    s = gp_loss_and_grad(&prob, dy, &o, &j.res.loss, j.res.grad, &info, ws, j.lay.ws_bytes, st);
+    j.res.cg_iters = info.cg_iters;
+    j.res.relres = info.relres_max;
+  } else {
+    float* dXs = reinterpret_cast<float*>(base + j.lay.xs);
+    float* dmu = reinterpret_cast<float*>(base + j.lay.mu);
+    float* dalpha = reinterpret_cast<float*>(base + j.lay.alpha);
+    e = cudaMemcpyAsync(dXs, j.hXs, sizeof(float) * r.m * r.d, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+      j.res.status = GP_ERR_CUDA;
+      return;
+    }
+    const gp_solve_opts o = opts_of(r, false);
+    int32_t it = 0;
+    double rel = 0.0;
+    s = gp_pcg_solve(&prob, dy, 1, dalpha, &o, &it, &rel, ws, j.lay.ws_bytes, st);
+    j.res.cg_iters = it;
+    j.res.relres = rel;
+    if (s == GP_OK || s == GP_ERR_NOT_CONVERGED) {
+      const gp_status sp = gp_predict_mean(&prob, dalpha, dXs, r.m, dmu, GP_PREC_FP32, ws,
+                                           j.lay.ws_bytes, st);
+      if (sp != GP_OK) s = sp;
+      if (sp == GP_OK) {
+        e = cudaMemcpyAsync(j.hmu, dmu, sizeof(float) * r.m, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) s = GP_ERR_CUDA;
+      }
+    }
+  }
+  cudaStreamSynchronize(st);
+  j.res.status = s;
+  (void)srv;
+}
+
+void worker_main(gp_server* srv) {
+  cudaSetDevice(srv->device);
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+  for (;;) {
+    std::shared_ptr<Job> job;
+    size_t off = 0;
+    {
+      std::unique_lock<std::mutex> lk(srv->mu);
+      srv->cv_work.wait(lk, [&] {
+        return srv->stop || (!srv->queue.empty() && srv->alloc->alloc(srv->queue.front()->lay.total, &off));
+      });
+      if (srv->stop) break;
+      job = srv->queue.front();
+      srv->queue.pop_front();
+      ++srv->active;
+      srv->peak_active = std::max(srv->peak_active, srv->active);
+      srv->peak_bytes = std::max(srv->peak_bytes, srv->alloc->in_use());
+      job->res.t_start_s = seconds_since(srv->t0);
+    }
+    run_job(srv, *job, srv->pool + off, st);
+    {
+      std::lock_guard<std::mutex> lk(srv->mu);
+      srv->alloc->release(off, job->lay.total);
+      --srv->active;
+      ++srv->completed;
+      job->res.t_done_s = seconds_since(srv->t0);
+      job->done = true;
+    }
+    srv->cv_work.notify_all();
+    srv->cv_done.notify_all();
+  }
+  cudaStreamDestroy(st);
+}
+
+gp_status fail(gp_status st, const char* msg) {
+  gp::set_error(msg);
+  return st;
+}
+
+}  // namespace
+
 extern "C" {
-gp_status gp_server_create(size_t, int32_t, gp_server**) {
-  gp::set_error("server not built yet");
-  return GP_ERR_UNIMPLEMENTED;
+
+size_t gp_server_footprint(const gp_request* req) {
+  JobLayout L;
+  if (req == nullptr || !layout_of(*req, &L)) return 0;
+  return L.total;
 }
-gp_status gp_server_submit(gp_server*, const gp_request*, uint64_t*) { return GP_ERR_UNIMPLEMENTED; }
-gp_status gp_server_poll(gp_server*, uint64_t, gp_result*) { return GP_ERR_UNIMPLEMENTED; }
-gp_status gp_server_drain(gp_server*, double) { return GP_ERR_UNIMPLEMENTED; }
-gp_status gp_server_destroy(gp_server*) { return GP_ERR_UNIMPLEMENTED; }
+
+gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server** out) {
+  if (out == nullptr || max_slots < 1 || max_slots > 256 || hbm_budget_bytes < (1u << 20))
+    return fail(GP_ERR_ARG, "gp_server_create: need out != NULL, 1 <= max_slots <= 256, budget >= 1 MiB");
+  auto* srv = new gp_server();
+  if (cudaGetDevice(&srv->device) != cudaSuccess) {
+    delete srv;
+    return fail(GP_ERR_CUDA, "gp_server_create: no current device");
+  }
+  srv->budget = hbm_budget_bytes & ~(kAlign - 1);
+  void* p = nullptr;
+  if (cudaMalloc(&p, srv->budget) != cudaSuccess) {
+    cudaGetLastError();
+    delete srv;
+    return fail(GP_ERR_OOM, "gp_server_create: cannot reserve the device pool");
+  }
+  srv->pool = static_cast<char*>(p);
+  srv->alloc = std::make_unique<PoolAllocator>(srv->budget);
+  for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back(worker_main, srv);
+  *out = srv;
+  return GP_OK;
 }
+
+gp_status gp_server_submit(gp_server* srv, const gp_request* req, uint64_t* ticket) {
+  if (srv == nullptr || req == nullptr || ticket == nullptr) return fail(GP_ERR_ARG, "NULL argument");
+  const gp_request& r = *req;
+  if (r.X == nullptr || r.y == nullptr || (r.kind == 1 && r.Xstar == nullptr))
+    return fail(GP_ERR_ARG, "gp_server_submit: missing host array");
+  auto job = std::make_shared<Job>();
+  if (!layout_of(r, &job->lay)) return fail(GP_ERR_ARG, "gp_server_submit: invalid request");
+  job->req = r;
+  const double t_submit = seconds_since(srv->t0);
+  if (job->lay.total > srv->budget) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    ++srv->refused;
+    return fail(GP_ERR_OOM, "gp_server_submit: request footprint exceeds the server's budget");
+  }
+  bool ok = cudaMallocHost(reinterpret_cast<void**>(&job->hX), sizeof(float) * r.n * r.d) == cudaSuccess &&
+            cudaMallocHost(reinterpret_cast<void**>(&job->hy), sizeof(float) * r.n) == cudaSuccess;
+  if (ok && r.kind == 1)
+    ok = cudaMallocHost(reinterpret_cast<void**>(&job->hXs), sizeof(float) * r.m * r.d) == cudaSuccess &&
+         cudaMallocHost(reinterpret_cast<void**>(&job->hmu), sizeof(float) * r.m) == cudaSuccess;
+  if (!ok) {
+    free_staging(*job);
+    return fail(GP_ERR_OOM, "gp_server_submit: cannot allocate pinned staging");
+  }
+  memcpy(job->hX, r.X, sizeof(float) * r.n * r.d);
+  memcpy(job->hy, r.y, sizeof(float) * r.n);
+  if (r.kind == 1) memcpy(job->hXs, r.Xstar, sizeof(float) * r.m * r.d);
+  job->req.X = job->req.y = job->req.Xstar = nullptr;
+  job->res.t_submit_s = t_submit;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    job->ticket = srv->next_ticket++;
+    srv->jobs[job->ticket] = job;
+    srv->queue.push_back(job);
+    ++srv->submitted;
+  }
+  srv->cv_work.notify_all();
+  *ticket = job->ticket;
+  return GP_OK;
+}
+
+gp_status gp_server_poll(gp_server* srv, uint64_t ticket, gp_result* res) {
+  if (srv == nullptr || res == nullptr) return fail(GP_ERR_ARG, "NULL argument");
+  std::shared_ptr<Job> job;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->jobs.find(ticket);
+    if (it == srv->jobs.end()) return fail(GP_ERR_ARG, "gp_server_poll: unknown ticket");
+    if (!it->second->done) return GP_ERR_TIMEOUT;
+    job = it->second;
+    srv->jobs.erase(it);
+  }
+  float* user_mu = res->mu;
+  *res = job->res;
+  res->mu = user_mu;
+  if (user_mu != nullptr && job->req.kind == 1 && job->hmu != nullptr)
+    memcpy(user_mu, job->hmu, sizeof(float) * job->req.m);
+  free_staging(*job);
+  return GP_OK;
+}
+
+gp_status gp_server_drain(gp_server* srv, double timeout_s) {
+  if (srv == nullptr) return fail(GP_ERR_ARG, "NULL server");
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const bool ok = srv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+    return srv->completed >= srv->submitted;
+  });
+  return ok ? GP_OK : GP_ERR_TIMEOUT;
+}
+
+gp_status gp_server_get_stats(gp_server* srv, gp_server_stats* out) {
+  if (srv == nullptr || out == nullptr) return fail(GP_ERR_ARG, "NULL argument");
+  std::lock_guard<std::mutex> lk(srv->mu);
+  out->submitted = srv->submitted;
+  out->completed = srv->completed;
+  out->refused = srv->refused;
+  out->peak_active = srv->peak_active;
+  out->peak_bytes = srv->peak_bytes;
+  out->budget_bytes = srv->budget;
+  return GP_OK;
+}
+
+gp_status gp_server_destroy(gp_server* srv) {
+  if (srv == nullptr) return fail(GP_ERR_ARG, "NULL server");
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->stop = true;
+  }
+  srv->cv_work.notify_all();
+  for (auto& t : srv->workers) t.join();
+  for (auto& kv : srv->jobs) free_staging(*kv.second);
+  srv->jobs.clear();
+  srv->queue.clear();
+  if (srv->pool) cudaFree(srv->pool);
+  delete srv;
+  return GP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,77 @@
+"""Mixed-precision iterative refinement: tensor-core inner CG, FP64 outer residual.
+
+Bound (mixed-precision path): after refinement the true residual
+||B - Kh X||_2 / ||B||_2 of the FP64 solution, recomputed here by the FP64
+oracle, is <= 1e-6.  The FP32-output form is additionally limited by the
+rounding of X to FP32 (about u ||Kh|| ||X|| / ||B||).
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+# Refinement converges when kappa * (relative product error) < 1: BF16 (~5e-3) at
+# kappa ~ 6e2 (s = 1), TF32 (~3e-4) and split BF16 (~1e-5) also at kappa ~ 6e3.
+@pytest.mark.parametrize("prec,s_noise", [(1, 1.0), (2, 1.0), (1, 0.1), (4, 0.1), (3, 0.1)])
+def test_refinement_reaches_1e6_true_residual(api, prec, s_noise):
+    prob = inputs.small_problem(seed=3)
+    theta = (s_noise, prob.theta[1], prob.theta[2])
+    Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 3, seed=4)]).astype(np.float32)
+    opts = api.solve_opts(cg_rtol=1e-2, prec=prec, refine_rtol=1e-7, refine_maxit=30)
+    Xs, iters, relres, st = api.gp_pcg_solve_refined(_dev(prob.X), _dev(Bm), prob.kind, theta, opts)
+    assert st == 0 and max(relres) <= 1e-7
+    Kh = O.khat_dense(prob.X, prob.kind, theta)
+    Xg = Xs.cpu().numpy()
+    true_res = np.linalg.norm(Bm - Kh @ Xg, axis=0) / np.linalg.norm(Bm, axis=0)
+    assert true_res.max() <= 1e-6, true_res
+    # The FP32-output form agrees up to the rounding of X.
+    X32, _, rel32, st32 = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, theta, opts)
+    assert st32 == 0
+    assert np.abs(X32.cpu().numpy() - Xg).max() <= 1e-6 * np.abs(Xg).max()
+    ref = sla.cho_solve(sla.cho_factor(Kh), Bm.astype(np.float64))
+    err = np.linalg.norm(Xg - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert err.max() <= np.linalg.cond(Kh) * 1e-6
+
+
+def test_refinement_reports_not_converged(api):
+    prob = inputs.small_problem(seed=4)
+    opts = api.solve_opts(cg_rtol=1e-1, prec=1, refine_rtol=1e-12, refine_maxit=1)
+    _, iters, relres, st = api.gp_pcg_solve(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts,
+                                            raise_not_converged=False)
+    assert st == 4 and relres[0] > 1e-12 and iters[0] > 0
+
+
+def test_refinement_beats_fp32_cg_true_residual(api):
+    # Plain FP32 CG plateaus near u * kappa; refinement reaches 1e-6.
+    prob = inputs.small_problem(seed=5)
+    X, y = _dev(prob.X), _dev(prob.y)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    x32, _, _, _ = api.gp_pcg_solve(X, y, prob.kind, prob.theta, api.solve_opts(cg_rtol=1e-10),
+                                   raise_not_converged=False)
+    xr, _, _, _ = api.gp_pcg_solve_refined(X, y, prob.kind, prob.theta,
+                                           api.solve_opts(cg_rtol=1e-2, prec=4, refine_rtol=1e-7,
+                                                          refine_maxit=30))
+    yy = prob.y.astype(np.float64)
+    r32 = np.linalg.norm(yy - Kh @ x32.cpu().numpy()[:, 0].astype(np.float64)) / np.linalg.norm(yy)
+    rr = np.linalg.norm(yy - Kh @ xr.cpu().numpy()[:, 0]) / np.linalg.norm(yy)
+    assert rr <= 1e-6 and rr < r32

@@ -1,0 +1,111 @@
+"""The continuous-batching server: each result is the same alone and in the mix,
+admission respects the device-memory budget, oversize requests are refused.
+
+Tolerance: results alone and in the mix are compared bit for bit (every kernel
+is deterministic and independent of what else runs); against the direct C calls
+likewise; predictions against the FP64 oracle at the FP32 product bound 1e-5
+when CG has converged.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import api, server
+    return torch, api, server
+
+
+def _requests():
+    rng = np.random.default_rng(0)
+    reqs = []
+    for i in range(8):
+        n = int(rng.integers(400, 3000))
+        d = [2, 3, 8][i % 3]
+        kind = i % 2
+        prob = inputs.uniform_problem(n, d, kind, (0.05 + 0.01 * i, 1.0 + 0.1 * i, 0.2 + 0.05 * i), seed=i)
+        is_pred = (i % 4 == 3)
+        Xs = inputs.points(300, d, seed=100 + i) if is_pred else None
+        reqs.append((1 if is_pred else 0, prob, Xs))
+    return reqs
+
+
+def _run(server_mod, reqs, slots, budget=8 << 30, **kw):
+    with server_mod.Server(budget, slots) as srv:
+        tickets = []
+        for kind, p, Xs in reqs:
+            r, keep = server_mod.Server.request(kind, p.X, p.y, p.kind, p.theta, nprobe=6, Xstar=Xs,
+                                                cg_maxit=400, nlanczos=15, cg_rtol=1e-6, seed=9, **kw)
+            tickets.append(srv.submit(r, keep))
+        srv.drain(300)
+        out = [srv.poll(t) for t in tickets]
+        return out, srv.stats()
+
+
+def test_results_same_alone_and_in_the_mix(env):
+    torch, api, server = env
+    reqs = _requests()
+    alone = [_run(server, [r], 1)[0][0] for r in reqs]
+    mixed, stats = _run(server, reqs, 4)
+    assert stats["completed"] == len(reqs)
+    assert stats["peak_active"] >= 2          # requests did share the device
+    for a, b in zip(alone, mixed):
+        assert a["status"] == b["status"]
+        if a["mu"] is None:
+            assert a["loss"] == b["loss"] and a["grad"] == b["grad"]
+        else:
+            assert np.array_equal(a["mu"], b["mu"])
+
+
+def test_server_matches_direct_calls(env):
+    torch, api, server = env
+    kind, p, _ = _requests()[0]
+    res, _ = _run(server, [(kind, p, None)], 2)
+    opts = api.solve_opts(nprobe=6, nlanczos=15, cg_rtol=1e-6, seed=9, cg_maxit=400)
+    loss, grad, _ = api.gp_loss_and_grad(torch.from_numpy(p.X).cuda(), torch.from_numpy(p.y).cuda(),
+                                         p.kind, p.theta, opts)
+    assert res[0]["loss"] == loss and res[0]["grad"] == grad
+
+
+def test_prediction_matches_oracle(env):
+    torch, api, server = env
+    p = inputs.uniform_problem(1200, 3, O.GAUSSIAN, (0.1, 1.0, 0.3), seed=21)
+    Xs = inputs.points(500, 3, seed=22)
+    res, _ = _run(server, [(1, p, Xs)], 1)
+    assert res[0]["status"] == 0
+    alpha = O.exact_nll(p.X, p.y, p.kind, p.theta)["alpha"]
+    ref = O.predict_mean(p.X, Xs, alpha, p.kind, p.theta)
+    # CG to 1e-6 on a system with kappa ~ 6e3 moves mu by ~kappa * 1e-6 relative at most.
+    assert np.linalg.norm(res[0]["mu"] - ref) / np.linalg.norm(ref) <= 1e-3
+
+
+def test_admission_respects_budget_and_refuses_oversize(env):
+    torch, api, server = env
+    reqs = _requests()
+    with server.Server(1 << 30, 8) as srv:
+        sizes = []
+        for kind, p, Xs in reqs:
+            r, keep = server.Server.request(kind, p.X, p.y, p.kind, p.theta, nprobe=6, Xstar=Xs,
+                                            cg_maxit=400, nlanczos=15, cg_rtol=1e-6)
+            sizes.append(srv.footprint(r))
+    budget = 2 * max(sizes) + (1 << 20)
+    res, stats = _run(server, reqs, 8, budget=budget)
+    assert stats["peak_bytes"] <= stats["budget_bytes"]
+    assert all(r["status"] in (0, 4) for r in res)
+    from paper_2503_02259_gb300._binding import GPError
+    big = inputs.uniform_problem(200000, 8, O.GAUSSIAN, (0.1, 1.0, 0.3), seed=1)
+    with server.Server(64 << 20, 1) as srv:
+        r, keep = server.Server.request(0, big.X, big.y, big.kind, big.theta, nprobe=16)
+        with pytest.raises(GPError) as ei:
+            srv.submit(r, keep)
+        assert ei.value.status == 3   # GP_ERR_OOM
+        assert srv.stats()["refused"] == 1
