@@ -206,6 +206,76 @@ def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
     return out
 
 
+def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
+    """L(Theta) and dL/dTheta on the differentiation problem (d = 8, 0.5 N(0,I), Gaussian
+    s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps, CG to 1e-6): accuracy of each
+    arithmetic against the FP64 oracle's same-probe estimator on the n = 4000 subsample,
+    and wall time per Theta at the full n."""
+    import oracle as O
+    from paper_2503_02259_gb300 import inputs
+    precs = {"fp32": 0, "bf16x3": 4, "tf32x3": 3}
+    sub = inputs.diff_problem(seed=0, n=4000)
+    est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
+    gref = np.asarray(est["grad"])
+    floor = 1e-3 * np.linalg.norm(gref)
+    out = {"workload": "differentiation problem, 32 probes x 40 Lanczos steps, CG rtol 1e-6; "
+                       "accuracy on the n=4000 subsample vs the FP64 same-probe oracle; time at "
+                       f"n={full_n}"}
+    Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
+    for name, prec in precs.items():
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=prec)
+        loss, grad, _ = api.gp_loss_and_grad(Xs, ys, sub.kind, sub.theta, opts)
+        rel_l = abs(loss - est["loss"]) / abs(est["loss"])
+        rel_g = max(abs(g - r) / max(abs(r), floor) for g, r in zip(grad, gref))
+        out[name] = {"relerr_loss_n4000": rel_l, "relerr_grad_n4000": rel_g}
+    full = inputs.diff_problem(seed=0, n=full_n)
+    Xf, yf = torch.from_numpy(full.X).cuda(), torch.from_numpy(full.y).cuda()
+    for name in ("fp32", "tf32x3", "bf16x3"):
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=precs[name])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, grad, info = api.gp_loss_and_grad(Xf, yf, full.kind, full.theta, opts)
+        torch.cuda.synchronize()
+        out[name].update({"ms_per_theta": (time.perf_counter() - t0) * 1e3, "loss": loss,
+                          "grad": grad, "cg_iters": info["cg_iters"]})
+    for name in ("tf32x3", "bf16x3"):
+        out[f"speedup_{name}_vs_fp32"] = out["fp32"]["ms_per_theta"] / out[name]["ms_per_theta"]
+    # The fastest arithmetic whose loss and gradient stay within 1e-4 of the oracle.
+    ok = [k for k in ("bf16x3", "tf32x3") if out[k]["relerr_loss_n4000"] <= 1e-4
+          and out[k]["relerr_grad_n4000"] <= 1e-4]
+    best = min(ok, key=lambda k: out[k]["ms_per_theta"]) if ok else None
+    out["mixed_at_1e-4"] = {"arithmetic": best,
+                            "ms_per_theta": out[best]["ms_per_theta"] if best else None,
+                            "speedup_vs_fp32": out[f"speedup_{best}_vs_fp32"] if best else None}
+    return out
+
+
+def serving(torch, count: int = 64, prec: int = 4, slots: int = 8, budget_gb: int = 96) -> dict:
+    """Replay a Poisson stream of mixed loss+grad and prediction requests through the server."""
+    from paper_2503_02259_gb300 import inputs, server
+    reqs = inputs.serving_stream(seed=0, count=count)
+    work = 0.0
+    for rq in reqs:   # entries x columns issued (CG budget 20 / 50, SLQ 20 steps, 1 gradient pass)
+        n = rq.problem.n
+        work += (n * n * (1 + rq.nprobe) * 41 if rq.kind == 0 else n * n * 50 + n * rq.Xstar.shape[0])
+    with server.Server(budget_gb << 30, slots) as srv:
+        t0 = time.perf_counter()
+        res = server.replay(srv, reqs, prec=prec, nlanczos=20, cg_rtol=1e-12)
+        wall = time.perf_counter() - t0
+        stats = srv.stats()
+    lat = np.array([r["latency_s"] for r in res])
+    ok = sum(r["status"] in (0, 4) for r in res)
+    return {"workload": f"{count} requests of the serving stream (Poisson 50/s, n log-uniform "
+                        "[1e3, 3e5], d in {2,3,8}, 70% loss+grad with 16 probes, 30% prediction at "
+                        "m=10000); fixed CG budget 20 (training) / 50 (prediction), SLQ 20 steps",
+            "arithmetic": {4: "bf16x3", 3: "tf32x3", 0: "fp32"}.get(prec, str(prec)),
+            "slots": slots, "requests_ok": ok, "wall_s": wall,
+            "requests_per_s": len(res) / wall, "entries_cols_per_s": work / wall,
+            "latency_p50_s": float(np.percentile(lat, 50)),
+            "latency_p99_s": float(np.percentile(lat, 99)),
+            "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"]}
+
+
 def loss_grad_small(api, torch, reps: int = 3) -> dict:
     """Loss + gradient per Theta on the small configuration (n=2000, d=3, Gaussian)."""
     from paper_2503_02259_gb300 import inputs
@@ -340,6 +410,8 @@ def main() -> int:
     if rank == 0 and not args.no_extras:
         extras["loss_grad"] = loss_grad_small(api, torch)
         extras["precision_modes"] = precision_modes(api, B, torch, prob, X, V, dev)
+        extras["loss_grad_mixed_vs_fp32"] = loss_grad_mixed_vs_fp32(api, torch)
+        extras["serving"] = serving(torch)
 
     if rank != 0:
         if dist:

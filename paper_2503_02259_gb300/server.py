@@ -82,9 +82,11 @@ class Server:
         return {k: getattr(s, k) for k, _ in B.gp_server_stats._fields_}
 
 
-def replay(server: Server, requests, time_scale: float = 1.0, **kw) -> list[dict]:
+def replay(server: Server, requests, time_scale: float = 1.0, cg_maxit_train: int = 20,
+           cg_maxit_pred: int = 50, **kw) -> list[dict]:
     """Submit requests at their arrival times (seconds x time_scale) and collect the
-    results; returns one dict per request with its latency (done - submit)."""
+    results; returns one dict per request with its latency (done - submit).  The CG
+    budgets default to a fixed 20 iterations for loss+grad and 50 for predictions."""
     t0 = time.perf_counter()
     tickets = []
     for rq in requests:
@@ -93,7 +95,8 @@ def replay(server: Server, requests, time_scale: float = 1.0, **kw) -> list[dict
             time.sleep(delay)
         p = rq.problem
         req, keep = Server.request(rq.kind, p.X, p.y, p.kind, p.theta, nprobe=rq.nprobe,
-                                   Xstar=rq.Xstar, **kw)
+                                   Xstar=rq.Xstar,
+                                   cg_maxit=cg_maxit_train if rq.kind == 0 else cg_maxit_pred, **kw)
         tickets.append(server.submit(req, keep))
     server.drain()
     out = []
