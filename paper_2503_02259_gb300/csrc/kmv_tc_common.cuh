@@ -15,9 +15,10 @@ constexpr int kTcM = 128;        // rows per CTA = MMA M
 constexpr int kTcBK = 32;        // points j per tile = MMA K extent per tile
 constexpr int kTcEvalThreads = 256;  // eval warps 0-7: two threads per row
 constexpr int kTcThreads = 288;      // + one control warp (copies and MMA issue)
-constexpr int kTcBStages = 3;
+constexpr int kTcBStages = 5;
 constexpr int kTcAStages = 2;
 constexpr int kTcNumBars = 2 * kTcBStages + 2 * kTcAStages + 1;
+static_assert(kTcNumBars * 8 + 8 <= 128, "barriers, tmem holder and abort flag share 128 bytes");
 constexpr int kTcFlush = 16;     // tiles per accumulation block
 
 // NSA / NSB: parts the A (kernel tile) and B (V tile) operands are split into
@@ -175,7 +176,7 @@ struct TcSmem {
 };
 
 template <int MODE, int DT>
-__host__ __device__ inline TcSmem tc_smem(int n, bool grad) {
+__host__ __device__ inline TcSmem tc_smem(int n, bool grad, int nbs) {
   using G = TcGeom<MODE>;
   constexpr int DP = DimTraits<DT>::DP;
   TcSmem s;
@@ -184,8 +185,8 @@ __host__ __device__ inline TcSmem tc_smem(int n, bool grad) {
   s.abytes = G::A_BYTES;
   s.bars = 0;                                 // kTcNumBars mbarriers, tmem holder, abort flag
   s.sx = 128;
-  s.sb = s.sx + ((kTcBStages * s.xbytes + 127) / 128) * 128;
-  s.sa = s.sb + kTcBStages * TcTraits<MODE>::NSB * s.bbytes;
+  s.sb = s.sx + ((nbs * s.xbytes + 127) / 128) * 128;
+  s.sa = s.sb + nbs * TcTraits<MODE>::NSB * s.bbytes;
   s.total = s.sa + kTcAStages * (grad ? 2 : 1) * TcTraits<MODE>::NSA * s.abytes;
   return s;
 }

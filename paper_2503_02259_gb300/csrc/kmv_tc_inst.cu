@@ -68,8 +68,12 @@ cudaError_t ensure_attr() {
 template <int KIND, bool GRAD, int DT>
 cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
   const int n = p.w_pad;
-  const TcSmem L = tc_smem<MODE, DT>(n, GRAD);
-  if (L.total > 227u * 1024u || n > 128 || n < 16 || (n & 15)) return cudaErrorNotSupported;
+  if (n > 128 || n < 16 || (n & 15)) return cudaErrorNotSupported;
+  // The deepest copy ring (<= kTcBStages stages) that fits in shared memory.
+  int nbs = kTcBStages;
+  while (nbs > 2 && tc_smem<MODE, DT>(n, GRAD, nbs).total > 227u * 1024u) --nbs;
+  const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs);
+  if (L.total > 227u * 1024u) return cudaErrorNotSupported;
   cudaError_t e = ensure_attr<KIND, GRAD, DT>();
   if (e != cudaSuccess) return e;
   const uint32_t cols = tc_tmem_cols(n, GRAD);
@@ -110,7 +114,7 @@ cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
   dim3 grid(p.row_tiles, p.split);
   auto fn = kernel_ptr<KIND, GRAD, DT>();
   profile_product_begin(st);
-  fn<<<grid, kTcThreads, smem, st>>>(a, n, p.nr_pad, p.jtiles, p.jt_per_split, idesc, cols);
+  fn<<<grid, kTcThreads, smem, st>>>(a, n, p.nr_pad, p.jtiles, p.jt_per_split, idesc, cols, nbs);
   profile_product_end(st);
   count_launch();
   return cudaGetLastError();

@@ -56,9 +56,20 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
 }  // namespace tc
 
 template <int KIND, bool GRAD, int DT, int MODE>
-__global__ void __launch_bounds__(kTcThreads)
+// Plain BF16 needs little shared memory, so it can keep three CTAs per SM if
+// the registers allow (<= 72 per thread at 288 threads); the other modes are
+// limited to one or two CTAs by shared memory and keep the compiler's own
+// register choice (each instantiation unit compiles one mode).
+#if defined(GP_TC_MODE) && GP_TC_MODE == 2
+#define GP_TC_BOUNDS __launch_bounds__(kTcThreads, 3)
+#else
+#define GP_TC_BOUNDS __launch_bounds__(kTcThreads)
+#endif
+__global__ void GP_TC_BOUNDS
     kmv_tc_kernel(TcArgs a, int n_cols, int64_t nr_pad, int jtiles, int jt_per_split,
-                  uint32_t idesc, uint32_t tmem_cols) {
+                  uint32_t idesc, uint32_t tmem_cols, int nbs) {
+  // nbs: stages of the point / B-operand ring, 2 <= nbs <= kTcBStages (host-chosen
+  // to fit shared memory).
   using G = TcGeom<MODE>;
   constexpr int DP = DimTraits<DT>::DP;
   constexpr int NSA = TcTraits<MODE>::NSA;
@@ -71,9 +82,9 @@ __global__ void __launch_bounds__(kTcThreads)
   if (a.active != nullptr && *a.active == 0) return;
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcSmem L = tc_smem<MODE, DT>(n_cols, GRAD);
-  uint64_t* fullX = reinterpret_cast<uint64_t*>(smem + L.bars);  // [3] points + B landed
-  uint64_t* emptyX = fullX + kTcBStages;                          // [3] MMA done with stage
+  const TcSmem L = tc_smem<MODE, DT>(n_cols, GRAD, nbs);
+  uint64_t* fullX = reinterpret_cast<uint64_t*>(smem + L.bars);  // [nbs] points + B landed
+  uint64_t* emptyX = fullX + kTcBStages;                          // [nbs] MMA done with stage
   uint64_t* fullA = emptyX + kTcBStages;                          // [2] A written (256 arrivals)
   uint64_t* emptyA = fullA + kTcAStages;                          // [2] MMA done with A
   uint64_t* folded = emptyA + kTcAStages;                         // [1] block sum folded
@@ -143,10 +154,11 @@ __global__ void __launch_bounds__(kTcThreads)
     const uint32_t rowoff =
         static_cast<uint32_t>(m >> 3) * G::SBO + static_cast<uint32_t>(m & 7) * 16;
     bool ok = true;
-    for (int t = 0; t < T && ok; ++t) {
-      const int bs = t % kTcBStages;
+    int bs = 0;          // ring slot of tile t and the parity of its phase,
+    uint32_t bph = 0;    // advanced without division
+    for (int t = 0; t < T && ok; ++t, bph ^= (++bs == nbs), bs = bs == nbs ? 0 : bs) {
       const int as = t % kTcAStages;
-      ok = tc::wait_or_abort(&fullX[bs], (t / kTcBStages) & 1, abort_s);
+      ok = tc::wait_or_abort(&fullX[bs], bph, abort_s);
       if (ok && t >= kTcAStages)
         ok = tc::wait_or_abort(&emptyA[as], ((t - kTcAStages) / kTcAStages) & 1, abort_s);
       if (!ok) break;
@@ -218,55 +230,74 @@ __global__ void __launch_bounds__(kTcThreads)
     // ---------------------------------------------------- control warp, lane 0
     int issued = 0;       // tiles whose copies were issued
     int committed = -1;   // last tile whose MMAs were committed
+    int ist = 0;         // ring slot of the next copy to issue
     auto issue_copy = [&](int t) {
-      const int st = t % kTcBStages;
+      const int st = ist;
+      ist = (ist + 1 == nbs) ? 0 : ist + 1;
       const int64_t jt = jt0 + t;
       dev::mbar_arrive_expect_tx(&fullX[st], L.xbytes + NSB * L.bbytes);
       dev::bulk_g2s(sX + st * (L.xbytes / 4), a.xc + jt * kTcBK * DP, L.xbytes, &fullX[st]);
       const unsigned char* vsrc = static_cast<const unsigned char*>(a.vt) + jt * NSB * L.bbytes;
       dev::bulk_g2s(sB + st * NSB * L.bbytes, vsrc, NSB * L.bbytes, &fullX[st]);
     };
-    for (int t = 0; t < 2 && t < T; ++t) issue_copy(t);
-    issued = T < 2 ? T : 2;
+    // Descriptor templates of stage 0 (addresses < 256 KiB keep the 14-bit
+    // start-address field free of carries when offsets are added).
+    const uint64_t desc_a0 = tc::smem_desc(dev::smem_addr(sA), G::LBO, G::SBO);
+    const uint64_t desc_b0 = tc::smem_desc(dev::smem_addr(sB), G::LBO, G::SBO);
+    const uint32_t a_stage = NMAT * NSA * L.abytes;   // bytes per A stage
+    const uint32_t b_stage = NSB * L.bbytes;          // bytes per B stage
+    // Prefetch distance: nbs - 1 tiles ahead of the tile being consumed.
+    const int kAhead = nbs - 1;
+    for (int t = 0; t < kAhead && t < T; ++t) issue_copy(t);
+    issued = T < kAhead ? T : kAhead;
     bool ok = true;
+    int bs = 0, pbs = 0;           // ring slot of tile t, and of tile t-1
+    uint32_t bph = 0, pbph = 0;    // their phase parities
     for (int t = 0; t < T; ++t) {
-      const int bs = t % kTcBStages;
+      if (t > 0) {
+        pbs = bs;
+        pbph = bph;
+        if (++bs == nbs) {
+          bs = 0;
+          bph ^= 1u;
+        }
+      }
       const int as = t % kTcAStages;
-      ok = tc::wait_or_abort(&fullX[bs], (t / kTcBStages) & 1, abort_s);
+      ok = tc::wait_or_abort(&fullX[bs], bph, abort_s);
       if (ok) ok = tc::wait_or_abort(&fullA[as], (t / kTcAStages) & 1, abort_s);
       if (ok && t > 0 && t % kTcFlush == 0)
         ok = tc::wait_or_abort(folded, ((t / kTcFlush) - 1) & 1, abort_s);
       if (!ok) break;
       tc::fence_after();
-      const uint32_t a0 = dev::smem_addr(sA + (as * NMAT * NSA) * L.abytes);
-      const uint32_t b0 = dev::smem_addr(sB + bs * NSB * L.bbytes);
+      // Descriptors: the stage-0 templates plus this tile's offsets, in the
+      // descriptor's start-address units (bytes >> 4, the low bits).
+      const uint64_t da = desc_a0 + ((static_cast<uint32_t>(as) * a_stage) >> 4);
+      const uint64_t db = desc_b0 + ((static_cast<uint32_t>(bs) * b_stage) >> 4);
       uint32_t acc = (t % kTcFlush == 0) ? 0u : 1u;   // a block starts from zero
 #pragma unroll
       for (int ks = 0; ks < G::KSTEPS; ++ks) {
         // One MMA consumes two K-adjacent core matrices (32 bytes of K).
-        const uint32_t ko = static_cast<uint32_t>(ks) * 2 * G::LBO;
+        const uint64_t ko = (static_cast<uint64_t>(ks) * 2 * G::LBO) >> 4;
         // Products (A part, B part): (hi, hi), then (hi, lo), then (lo, hi).
 #pragma unroll
         for (int pr = 0; pr < NPROD; ++pr) {
-          const uint32_t am = (pr == 2) ? 1u : 0u;
-          const uint32_t bm = (pr == 1) ? 1u : 0u;
-          const uint64_t bdesc = tc::smem_desc(b0 + bm * L.bbytes + ko, G::LBO, G::SBO);
-          const uint64_t adk = tc::smem_desc(a0 + am * L.abytes + ko, G::LBO, G::SBO);
-          tc::mma<MODE>(tmem, adk, bdesc, idesc, acc);
-          if constexpr (GRAD) {
-            const uint64_t add = tc::smem_desc(a0 + (NSA + am) * L.abytes + ko, G::LBO, G::SBO);
-            tc::mma<MODE>(tmem + static_cast<uint32_t>(n_cols), add, bdesc, idesc, acc);
-          }
+          const uint64_t am = (pr == 2) ? 1u : 0u;
+          const uint64_t bm = (pr == 1) ? 1u : 0u;
+          const uint64_t bdesc = db + ((bm * L.bbytes) >> 4) + ko;
+          tc::mma<MODE>(tmem, da + ((am * L.abytes) >> 4) + ko, bdesc, idesc, acc);
+          if constexpr (GRAD)
+            tc::mma<MODE>(tmem + static_cast<uint32_t>(n_cols),
+                          da + (((NSA + am) * L.abytes) >> 4) + ko, bdesc, idesc, acc);
           acc = 1u;
         }
       }
       tc::commit(&emptyA[as]);
       tc::commit(&emptyX[bs]);
       committed = t;
-      // Prefetch tile t+2 into the stage tile t-1 used, once its MMAs are done.
+      // Prefetch tile t + kAhead into the stage tile t-1 used, once its MMAs are done.
       if (issued < T) {
         if (t >= 1)
-          ok = tc::wait_or_abort(&emptyX[(t - 1) % kTcBStages], ((t - 1) / kTcBStages) & 1, abort_s);
+          ok = tc::wait_or_abort(&emptyX[pbs], pbph, abort_s);
         if (!ok) break;
         issue_copy(issued);
         ++issued;
@@ -278,7 +309,7 @@ __global__ void __launch_bounds__(kTcThreads)
       if (committed >= 0)
         dev::mbar_wait(&emptyA[committed % kTcAStages], (committed / kTcAStages) & 1);
       for (int t = committed + 1; t < issued; ++t)
-        dev::mbar_wait(&fullX[t % kTcBStages], (t / kTcBStages) & 1);
+        dev::mbar_wait(&fullX[t % nbs], (t / nbs) & 1);
     }
   }
   tc::fence_before();
