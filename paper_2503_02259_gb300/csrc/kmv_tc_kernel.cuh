@@ -5,9 +5,11 @@
 // j in tiles of kTcBK points.
 //   * Control warp (warp 8, lane 0): issues the bulk (TMA) copies of each
 //     tile's points and of its slice of V, already laid out as the MMA B
-//     operand, into a 3-stage shared ring, and issues the tile's tcgen05.mma
-//     instructions D_K += A_K B, D_D += A_D B (FP32 accumulation in tensor
-//     memory), then tcgen05.commit to the barriers that free the buffers.
+//     operand, into a shared ring of up to kTcBStages stages (as many as fit),
+//     and issues the tile's tcgen05.mma instructions D_K += A_K B,
+//     D_D += A_D B (FP32 accumulation in tensor memory) from descriptors
+//     precomputed for stage 0, then tcgen05.commit to the barriers that free
+//     the buffers.  (A second issuing warp for D was measured slower.)
 //   * Eval warps 0-7 (two threads per row, each half of the tile's columns):
 //     evaluate k(x_i, x_j) and dk/dl in registers and write them, rounded to
 //     the operand type, into a 2-stage A buffer in the K-major core-matrix
