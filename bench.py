@@ -206,42 +206,88 @@ def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
     return out
 
 
+def precision_config(api, B, torch, dev) -> dict:
+    """The precision problem (n = 1e6, d = 2 uniform, Gaussian f = 1, l = 0.05, s = 0.01,
+    V of width 64): one K-hat.V product per arithmetic, timed with the library's
+    product-kernel events, and its norm-wise error against the FP64 oracle on 1000
+    sampled rows (the same rows for every arithmetic)."""
+    import oracle as O
+    from paper_2503_02259_gb300 import inputs
+    prob = inputs.precision_problem(seed=0)
+    Vh = inputs.multivector(prob.y, 64, seed=0)
+    rows = np.sort(np.random.default_rng(3).choice(prob.n, 1000, replace=False))
+    t0 = time.perf_counter()
+    rY, _, _ = O.kmv_rows(prob.X, Vh, prob.kind, prob.theta, rows=rows, block=20)
+    t_oracle = time.perf_counter() - t0
+    X = torch.from_numpy(prob.X).to(dev)
+    V = torch.from_numpy(Vh).to(dev)
+    L = B.lib()
+    out = {"workload": "n=1000000 d=2 uniform[0,1]^2, Gaussian f=1 l=0.05 s=0.01, V=[y | 63 "
+                       "Rademacher] w=64, one Kh.V product; error on 1000 sampled rows vs FP64",
+           "oracle_rows_s": t_oracle}
+    for name, prec in PRECS.items():
+        pr, _ = api.problem(X, prob.kind, prob.theta)
+        ws = api.workspace(B.OP_MATMUL, pr, 64, api.solve_opts(prec=prec), dev)
+        Y = torch.empty_like(V)
+
+        def step():
+            B.check(L.gp_kernel_matmul(B.ctypes.byref(pr), api._ptr(V), 64, api._ptr(Y), prec,
+                                       api._ptr(ws), ws.numel(), api._stream(dev)), "matmul")
+        step()
+        torch.cuda.synchronize()
+        B.check(L.gp_profile_begin(), "profile")
+        step()
+        torch.cuda.synchronize()
+        ms, n1, n2 = B.c_double(), B.c_int64(), B.c_int64()
+        B.check(L.gp_profile_end(B.ctypes.byref(ms), B.ctypes.byref(n1), B.ctypes.byref(n2)), "profile")
+        yh = Y.cpu().numpy()[rows].astype(np.float64)
+        err = float(np.max(np.linalg.norm(yh - rY, axis=0) / np.linalg.norm(rY, axis=0)))
+        out[name] = {"kernel_ms": ms.value, "value": prob.n * prob.n * 64 / (ms.value * 1e-3),
+                     "unit": UNIT, "relerr_Y_1000_rows": err}
+        del ws, Y
+    return out
+
+
 def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     """L(Theta) and dL/dTheta on the differentiation problem (d = 8, 0.5 N(0,I), Gaussian
     s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps, CG to 1e-6): accuracy of each
-    arithmetic against the FP64 oracle's same-probe estimator on the n = 4000 subsample,
-    and wall time per Theta at the full n."""
+    arithmetic (CG products / SLQ products) against the FP64 oracle's same-probe estimator
+    on the n = 4000 subsample, and wall time per Theta at the full n."""
     import oracle as O
     from paper_2503_02259_gb300 import inputs
-    precs = {"fp32": 0, "bf16x3": 4, "tf32x3": 3}
+    same = -1
+    arms = {"fp32": (0, 0), "tf32x3": (3, same), "bf16x3": (4, same),
+            "bf16x3_slq_tf32x3": (4, 3)}
+    timed = ("fp32", "tf32x3", "bf16x3_slq_tf32x3")
     sub = inputs.diff_problem(seed=0, n=4000)
     est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
     gref = np.asarray(est["grad"])
     floor = 1e-3 * np.linalg.norm(gref)
     out = {"workload": "differentiation problem, 32 probes x 40 Lanczos steps, CG rtol 1e-6; "
                        "accuracy on the n=4000 subsample vs the FP64 same-probe oracle; time at "
-                       f"n={full_n}"}
+                       f"n={full_n}; arm = CG arithmetic[_slq_<SLQ arithmetic>], gradient pass FP32"}
     Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
-    for name, prec in precs.items():
-        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=prec)
+    for name, (prec, slq) in arms.items():
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=prec, slq_prec=slq)
         loss, grad, _ = api.gp_loss_and_grad(Xs, ys, sub.kind, sub.theta, opts)
         rel_l = abs(loss - est["loss"]) / abs(est["loss"])
         rel_g = max(abs(g - r) / max(abs(r), floor) for g, r in zip(grad, gref))
         out[name] = {"relerr_loss_n4000": rel_l, "relerr_grad_n4000": rel_g}
     full = inputs.diff_problem(seed=0, n=full_n)
     Xf, yf = torch.from_numpy(full.X).cuda(), torch.from_numpy(full.y).cuda()
-    for name in ("fp32", "tf32x3", "bf16x3"):
-        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=precs[name])
+    for name in timed:
+        prec, slq = arms[name]
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=prec, slq_prec=slq)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         loss, grad, info = api.gp_loss_and_grad(Xf, yf, full.kind, full.theta, opts)
         torch.cuda.synchronize()
         out[name].update({"ms_per_theta": (time.perf_counter() - t0) * 1e3, "loss": loss,
                           "grad": grad, "cg_iters": info["cg_iters"]})
-    for name in ("tf32x3", "bf16x3"):
+    for name in timed[1:]:
         out[f"speedup_{name}_vs_fp32"] = out["fp32"]["ms_per_theta"] / out[name]["ms_per_theta"]
-    # The fastest arithmetic whose loss and gradient stay within 1e-4 of the oracle.
-    ok = [k for k in ("bf16x3", "tf32x3") if out[k]["relerr_loss_n4000"] <= 1e-4
+    # The fastest timed mixed arithmetic whose loss and gradient stay within 1e-4.
+    ok = [k for k in timed[1:] if out[k]["relerr_loss_n4000"] <= 1e-4
           and out[k]["relerr_grad_n4000"] <= 1e-4]
     best = min(ok, key=lambda k: out[k]["ms_per_theta"]) if ok else None
     out["mixed_at_1e-4"] = {"arithmetic": best,
@@ -250,30 +296,70 @@ def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     return out
 
 
-def serving(torch, count: int = 64, prec: int = 4, slots: int = 8, budget_gb: int = 96) -> dict:
-    """Replay a Poisson stream of mixed loss+grad and prediction requests through the server."""
+def serving(torch, count: int = 64,
+            precs=(("fp32", 0, 0), ("bf16x3_slq_tf32x3", 4, 3), ("tf32x3", 3, 3)),
+            slots: int = 8, budget_gb: int = 96) -> dict:
+    """Replay one Poisson stream of mixed loss+grad and prediction requests through the
+    server once per arithmetic: throughput, p50/p99 latency, and how far each mixed
+    run's losses, gradients and predictions are from the FP32 run's (same probes, same
+    fixed CG budget, so the difference is the product arithmetic alone)."""
     from paper_2503_02259_gb300 import inputs, server
     reqs = inputs.serving_stream(seed=0, count=count)
     work = 0.0
     for rq in reqs:   # entries x columns issued (CG budget 20 / 50, SLQ 20 steps, 1 gradient pass)
         n = rq.problem.n
         work += (n * n * (1 + rq.nprobe) * 41 if rq.kind == 0 else n * n * 50 + n * rq.Xstar.shape[0])
-    with server.Server(budget_gb << 30, slots) as srv:
-        t0 = time.perf_counter()
-        res = server.replay(srv, reqs, prec=prec, nlanczos=20, cg_rtol=1e-12)
-        wall = time.perf_counter() - t0
-        stats = srv.stats()
-    lat = np.array([r["latency_s"] for r in res])
-    ok = sum(r["status"] in (0, 4) for r in res)
-    return {"workload": f"{count} requests of the serving stream (Poisson 50/s, n log-uniform "
-                        "[1e3, 3e5], d in {2,3,8}, 70% loss+grad with 16 probes, 30% prediction at "
-                        "m=10000); fixed CG budget 20 (training) / 50 (prediction), SLQ 20 steps",
-            "arithmetic": {4: "bf16x3", 3: "tf32x3", 0: "fp32"}.get(prec, str(prec)),
-            "slots": slots, "requests_ok": ok, "wall_s": wall,
-            "requests_per_s": len(res) / wall, "entries_cols_per_s": work / wall,
-            "latency_p50_s": float(np.percentile(lat, 50)),
-            "latency_p99_s": float(np.percentile(lat, 99)),
-            "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"]}
+    out = {"workload": f"{count} requests of the serving stream (Poisson 50/s, n log-uniform "
+                       "[1e3, 3e5], d in {2,3,8}, 70% loss+grad with 16 probes, 30% prediction at "
+                       "m=10000); fixed CG budget 20 (training) / 50 (prediction), SLQ 20 steps",
+           "slots": slots, "budget_gb": budget_gb}
+    results = {}
+    for name, prec, slq in precs:
+        with server.Server(budget_gb << 30, slots) as srv:
+            t0 = time.perf_counter()
+            res = server.replay(srv, reqs, prec=prec, slq_prec=slq, nlanczos=20, cg_rtol=1e-12)
+            wall = time.perf_counter() - t0
+            stats = srv.stats()
+        results[name] = res
+        lat = np.array([r["latency_s"] for r in res])
+        small = np.array([r["latency_s"] for r, rq in zip(res, reqs) if rq.problem.n <= 20000])
+        out[name] = {"requests_ok": sum(r["status"] in (0, 4) for r in res), "wall_s": wall,
+                     "requests_per_s": len(res) / wall, "entries_cols_per_s": work / wall,
+                     "latency_p50_s": float(np.percentile(lat, 50)),
+                     "latency_p99_s": float(np.percentile(lat, 99)),
+                     "latency_p99_s_n_le_2e4": float(np.percentile(small, 99)) if small.size else None,
+                     "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"]}
+    # Accuracy of a fixed-budget solve is its final CG residual (the budget, not the
+    # arithmetic, decides how far from K-hat^-1 y the iterate is): compare each mixed
+    # arm's residual with the FP32 arm's, request by request, and report how far the
+    # results themselves moved.
+    def q(v, p):
+        return float(np.percentile(v, p)) if v else None
+
+    ref = results.get("fp32")
+    if ref is not None:
+        for name, _, _ in precs:
+            if name == "fp32":
+                continue
+            ratio, dl, dg, dm = [], [], [], []
+            for a, b, rq in zip(results[name], ref, reqs):
+                if b["relres"] > 0:
+                    ratio.append(a["relres"] / b["relres"])
+                if rq.kind == 0:
+                    dl.append(abs(a["loss"] - b["loss"]) / abs(b["loss"]))
+                    g, gr = np.asarray(a["grad"]), np.asarray(b["grad"])
+                    floor = 1e-3 * np.linalg.norm(gr)
+                    dg.append(float(np.max(np.abs(g - gr) / np.maximum(np.abs(gr), floor))))
+                else:
+                    dm.append(float(np.linalg.norm(a["mu"] - b["mu"]) / np.linalg.norm(b["mu"])))
+            out[name].update({
+                "relres_ratio_vs_fp32_p50": q(ratio, 50), "relres_ratio_vs_fp32_p90": q(ratio, 90),
+                "reldiff_loss_vs_fp32_p50": q(dl, 50), "reldiff_loss_vs_fp32_p90": q(dl, 90),
+                "reldiff_grad_vs_fp32_p50": q(dg, 50), "reldiff_grad_vs_fp32_p90": q(dg, 90),
+                "reldiff_mu_vs_fp32_p50": q(dm, 50), "reldiff_mu_vs_fp32_p90": q(dm, 90),
+                "throughput_vs_fp32": out["fp32"]["wall_s"] / out[name]["wall_s"]})
+        out["fp32"]["relres_p50"] = q([r["relres"] for r in ref], 50)
+    return out
 
 
 def loss_grad_small(api, torch, reps: int = 3) -> dict:
@@ -305,6 +391,8 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=list(PRECS), help="arithmetic of the product")
+    ap.add_argument("--serving-requests", type=int, default=64,
+                    help="requests replayed by the serving leg (the full stream is 512)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -410,8 +498,9 @@ def main() -> int:
     if rank == 0 and not args.no_extras:
         extras["loss_grad"] = loss_grad_small(api, torch)
         extras["precision_modes"] = precision_modes(api, B, torch, prob, X, V, dev)
+        extras["precision_config"] = precision_config(api, B, torch, dev)
         extras["loss_grad_mixed_vs_fp32"] = loss_grad_mixed_vs_fp32(api, torch)
-        extras["serving"] = serving(torch)
+        extras["serving"] = serving(torch, count=args.serving_requests)
 
     if rank != 0:
         if dist:
@@ -445,12 +534,20 @@ def main() -> int:
         psrc = ("measured cuBLAS bf16 dense peak (MEASURED_PEAKS.json)"
                 + (" x 0.5, the nominal tf32:bf16 ratio" if ratio != 1.0 else ""))
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
+    # Measured pipe rates of this GPU (microbenchmarks, run after the timed region).
+    fma_t, mufu_g = B.c_double(), B.c_double()
+    B.check(B.lib().gp_measure_pipe_rates(B.ctypes.byref(fma_t), B.ctypes.byref(mufu_g),
+                                          api._stream(dev)), "gp_measure_pipe_rates")
     roofline = {"bound": bound, "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tr.get("bytes_per_launch") if tr else None,
                 "peak_source": psrc,
                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops_per_launch,
-                "kernel_share_of_step": kern_ms / per_step_ms}
+                "kernel_share_of_step": kern_ms / per_step_ms,
+                "pipe_rates_measured": {"fp32_ffma2_tflops": fma_t.value,
+                                        "mufu_ex2_gops": mufu_g.value,
+                                        "frac_of_measured_fp32": (achieved / fma_t.value
+                                                                  if prec == 0 else None)}}
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()

@@ -119,7 +119,13 @@ typedef struct {
  *  prec:       contraction precision of the inner products (gp_precision).
  *  probes:     optional device n x nprobe float32 probe block; NULL = generated
  *              from `seed` by the rule above.
- *  refine_maxit: cap on outer refinement steps (<= 0: 10). */
+ *  refine_maxit: cap on outer refinement steps (<= 0: 10).
+ *  slq_prec:   arithmetic of the SLQ Lanczos products (gp_slq_logdet,
+ *              gp_loss_and_grad, gp_nll_forward): a gp_precision, or
+ *              GP_PREC_SAME for `prec`.  Zero-initialised options run SLQ in
+ *              FP32.  The log-determinant of a smooth, ill-conditioned K-hat
+ *              needs kernel entries to about 24 bits (FP32 or TF32X3), while
+ *              the CG solves tolerate BF16X3, so the two may differ. */
 typedef struct {
   int32_t nprobe;
   int32_t nlanczos;
@@ -130,8 +136,11 @@ typedef struct {
   uint64_t seed;
   const float* probes;
   int32_t refine_maxit;
-  int32_t reserved;
+  int32_t slq_prec;
 } gp_solve_opts;
+
+/* slq_prec value meaning "the same arithmetic as prec". */
+#define GP_PREC_SAME (-1)
 
 /* Diagnostics of one loss/gradient evaluation (host struct, filled on GP_OK). */
 typedef struct {
@@ -290,12 +299,24 @@ gp_status gp_generate_probes(int64_t n, int32_t p, uint64_t seed, float* Z, int6
 gp_status gp_profile_begin(void);
 gp_status gp_profile_end(double* product_ms, int64_t* product_launches, int64_t* total_launches);
 
+/* Pipe-rate microbenchmarks of the current device (no counterpart in the
+ * paper): the FP32 FMA pipe driven by packed FP32x2 FMAs (TFLOP/s, an FMA = 2
+ * flops) and the MUFU ex2 rate (10^9 ex2 per second), each from one timed
+ * launch of about 20 ms on `stream` after one untimed launch.  These are the
+ * pipes that bound the on-the-fly product (the contraction and the kernel
+ * evaluation).  Allocates nothing; synchronises.  GP_ERR_ARG for NULL
+ * outputs, GP_ERR_CUDA if a launch fails. */
+gp_status gp_measure_pipe_rates(double* fp32_tflops, double* mufu_ex2_gops, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Serving: a continuous-batching request server on one device (the stateless
  * loss/gradient and prediction calls of §Design and Implementation, served as
  * a stream of requests; the paper has no server).
  *  - gp_server_create reserves one device pool of hbm_budget_bytes and starts
- *    max_slots worker threads, each with its own CUDA stream.
+ *    max_slots worker threads, each with one CUDA stream per stream-priority
+ *    level of the device; a request runs on the stream whose priority falls
+ *    with its work (entries x columns), so small requests are not queued
+ *    behind the tiles of large ones.
  *  - gp_server_submit copies the request's HOST arrays into pinned staging and
  *    queues it; a request whose footprint (inputs + outputs + solver
  *    workspace) exceeds the whole budget is refused with GP_ERR_OOM.
@@ -332,8 +353,8 @@ typedef struct {
   int32_t nlanczos;
   double cg_rtol;
   uint64_t seed;
-  int32_t prec;
-  int32_t reserved;
+  int32_t prec;            /* arithmetic of the CG products (gp_precision) */
+  int32_t slq_prec;        /* arithmetic of the SLQ products (gp_solve_opts.slq_prec) */
 } gp_request;
 
 typedef struct {

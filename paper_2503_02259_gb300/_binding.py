@@ -32,6 +32,7 @@ PREC_TF32 = 1
 PREC_BF16 = 2
 PREC_TF32X3 = 3
 PREC_BF16X3 = 4
+PREC_SAME = -1   # slq_prec: the same arithmetic as prec
 
 OP_MATMUL = 0
 OP_GRAD_MATMUL = 1
@@ -58,7 +59,7 @@ class gp_solve_opts(ctypes.Structure):
     _fields_ = [("nprobe", c_int32), ("nlanczos", c_int32), ("cg_maxit", c_int32),
                 ("prec", c_int32), ("cg_rtol", c_double), ("refine_rtol", c_double),
                 ("seed", c_uint64), ("probes", c_void_p), ("refine_maxit", c_int32),
-                ("reserved", c_int32)]
+                ("slq_prec", c_int32)]
 
 
 class gp_loss_info(ctypes.Structure):
@@ -79,7 +80,7 @@ class gp_request(ctypes.Structure):
     _fields_ = [("kind", c_int32), ("d", c_int32), ("n", c_int64), ("kernel", c_int32),
                 ("nprobe", c_int32), ("theta", gp_theta), ("X", c_void_p), ("y", c_void_p),
                 ("Xstar", c_void_p), ("m", c_int64), ("cg_maxit", c_int32), ("nlanczos", c_int32),
-                ("cg_rtol", c_double), ("seed", c_uint64), ("prec", c_int32), ("reserved", c_int32)]
+                ("cg_rtol", c_double), ("seed", c_uint64), ("prec", c_int32), ("slq_prec", c_int32)]
 
 
 class gp_server_stats(ctypes.Structure):
@@ -127,6 +128,7 @@ PROTOTYPES = {
     "gp_generate_probes": (c_int32, [c_int64, c_int32, c_uint64, c_void_p, c_int64, c_void_p]),
     "gp_profile_begin": (c_int32, []),
     "gp_profile_end": (c_int32, [POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
+    "gp_measure_pipe_rates": (c_int32, [POINTER(c_double), POINTER(c_double), c_void_p]),
     "gp_server_create": (c_int32, [c_size_t, c_int32, POINTER(c_void_p)]),
     "gp_server_submit": (c_int32, [c_void_p, POINTER(gp_request), POINTER(c_uint64)]),
     "gp_server_poll": (c_int32, [c_void_p, c_uint64, POINTER(gp_result)]),

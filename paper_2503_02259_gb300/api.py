@@ -43,10 +43,14 @@ def problem(X: torch.Tensor, kernel: int, theta) -> tuple[B.gp_problem, torch.Te
 
 def solve_opts(nprobe: int = 0, nlanczos: int = 30, cg_maxit: int = 0, cg_rtol: float = 1e-8,
                seed: int = 0, prec: int = B.PREC_FP32, refine_rtol: float = 0.0,
-               probes: torch.Tensor | None = None, refine_maxit: int = 0) -> B.gp_solve_opts:
+               probes: torch.Tensor | None = None, refine_maxit: int = 0,
+               slq_prec: int = B.PREC_FP32) -> B.gp_solve_opts:
+    """gp_solve_opts; slq_prec is the arithmetic of the SLQ Lanczos products
+    (B.PREC_SAME: the same as prec)."""
     return B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
                            float(refine_rtol), int(seed) & (2**64 - 1),
-                           0 if probes is None else probes.data_ptr(), int(refine_maxit), 0)
+                           0 if probes is None else probes.data_ptr(), int(refine_maxit),
+                           int(slq_prec))
 
 
 def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None, device) -> torch.Tensor:

@@ -35,6 +35,7 @@ UNITS = [
     ("vec_kernels", "vec_kernels.cu", []),
     ("server", "server.cu", []),
     ("static_scratch", "static_scratch.cu", []),
+    ("microbench", "microbench.cu", []),
     ("gp_api", "gp_api.cu", []),
 ]
 

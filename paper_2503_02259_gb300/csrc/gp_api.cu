@@ -248,8 +248,8 @@ struct SolveWs {
   size_t bytes;
 };
 
-static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, bool with_grad,
-                           int lz_k, int prec) {
+static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, const SimtPlan& pl,
+                           bool with_grad, int lz_k, int prec, int slq_prec) {
   Carve c(ws);
   SolveWs w;
   const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
@@ -259,16 +259,38 @@ static SolveWs carve_solve(void* ws, const SimtPlan& pc, const SimtPlan& pg, boo
   w.R = c.take<float>(plane);
   w.P = c.take<float>(plane);
   w.Q = c.take<float>(plane);
-  const size_t planes = std::max<size_t>(pc.split, with_grad ? 2 * static_cast<size_t>(pg.split) : 0);
+  size_t planes = std::max<size_t>(pc.split, with_grad ? 2 * static_cast<size_t>(pg.split) : 0);
+  if (lz_k > 0) planes = std::max<size_t>(planes, pl.split);
   w.part = c.take<float>(planes * plane);
   w.Lq = lz_k > 0 ? c.take<float>(static_cast<size_t>(lz_k) * plane) : nullptr;
-  const size_t vtb = tc_vt_bytes(pc, prec);
+  size_t vtb = tc_vt_bytes(pc, prec);
+  if (lz_k > 0) vtb = std::max(vtb, tc_vt_bytes(pl, slq_prec));
   w.vt = vtb ? static_cast<void*>(c.take<unsigned char>(vtb)) : nullptr;
   w.red = c.take<double>(red_doubles(pc.nr_pad, pc.w_pad));
   w.S = c.take<CgState>(1);
   w.S2 = c.take<CgState>(1);
   w.bytes = c.off + 256;
   return w;
+}
+
+// Plans of one solver call: the CG product (pc, arithmetic prec), the FP32
+// derivative product of the gradient pass (pg) and the SLQ Lanczos product
+// (pl, arithmetic slq_prec); they share the solver arrays, so all take the
+// widest padded width.
+struct SolvePlans {
+  SimtPlan pc, pg, pl;
+};
+
+static SolvePlans solve_plans(const gp_problem* prob, int w, int prec, int lz_k, int slq_prec) {
+  const int64_t n = prob->n;
+  SolvePlans P;
+  P.pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
+  P.pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
+  P.pl = lz_k > 0 ? plan_for(n, n, prob->d, w, false, prob->kernel, slq_prec) : P.pc;
+  unify_width(P.pc, P.pg);
+  unify_width(P.pc, P.pl);
+  unify_width(P.pg, P.pl);
+  return P;
 }
 
 }  // namespace gp
@@ -320,6 +342,8 @@ static gp_status check_opts(const gp_solve_opts* o, bool need_probes) {
     return fail(GP_ERR_ARG, "nlanczos must be in [1, 64]");
   if (!(o->cg_rtol >= 0)) return fail(GP_ERR_ARG, "cg_rtol must be >= 0");
   if (o->prec < GP_PREC_FP32 || o->prec > GP_PREC_BF16X3) return fail(GP_ERR_ARG, "unknown precision");
+  if (o->slq_prec != GP_PREC_SAME && (o->slq_prec < GP_PREC_FP32 || o->slq_prec > GP_PREC_BF16X3))
+    return fail(GP_ERR_ARG, "unknown slq_prec");
   return GP_OK;
 }
 
@@ -503,27 +527,36 @@ static gp_status read_cg(const CgState* S, HostCg& h, cudaStream_t st) {
 
 // Common set-up of the solver calls: stage points, build B = [y | Z] (or B = user).
 struct SolveSetup {
-  SimtPlan pc, pg;
+  SimtPlan pc, pg, pl;
+  int slq_prec;
   SolveWs W;
   KernelConsts kc;
 };
 
 static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, int lz_k,
-                             void* ws, size_t ws_bytes, cudaStream_t st, SolveSetup& out) {
+                             int slq_prec, void* ws, size_t ws_bytes, cudaStream_t st,
+                             SolveSetup& out) {
   gp_status s;
   const int64_t n = prob->n;
-  out.pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
-  out.pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
-  unify_width(out.pc, out.pg);
-  SolveWs L = carve_solve(nullptr, out.pc, out.pg, with_grad, lz_k, prec);
+  const SolvePlans P = solve_plans(prob, w, prec, lz_k, slq_prec);
+  out.pc = P.pc;
+  out.pg = P.pg;
+  out.pl = P.pl;
+  out.slq_prec = slq_prec;
+  SolveWs L = carve_solve(nullptr, P.pc, P.pg, P.pl, with_grad, lz_k, prec, slq_prec);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
-  out.W = carve_solve(ws, out.pc, out.pg, with_grad, lz_k, prec);
+  out.W = carve_solve(ws, P.pc, P.pg, P.pl, with_grad, lz_k, prec, slq_prec);
   out.kc = kernel_consts(prob->kernel, prob->theta.l);
   GP_CUDA(cudaMemsetAsync(out.W.S, 0, sizeof(CgState), st));
   GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.cs, out.pc.dp,
                               out.pc.nc_pad, out.W.xs, st));
   GP_CUDA(cudaMemsetAsync(out.W.B, 0, sizeof(float) * out.pc.nr_pad * out.pc.w_pad, st));
   return GP_OK;
+}
+
+// The arithmetic of the SLQ Lanczos products.
+static int slq_prec_of(const gp_solve_opts* o) {
+  return o->slq_prec == GP_PREC_SAME ? o->prec : o->slq_prec;
 }
 
 static gp_status fill_probes(const gp_problem* prob, const gp_solve_opts* o, float* B, int64_t n_pad,
@@ -551,14 +584,16 @@ static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_s
   const int p = o->nprobe;
   const int w = 1 + p;
   const int lz_k = p > 0 ? o->nlanczos : 0;
-  if ((s = setup_solve(prob, w, with_grad, o->prec, lz_k, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, with_grad, o->prec, lz_k, slq_prec_of(o), ws, ws_bytes, st, ss)) !=
+      GP_OK)
+    return s;
   SolveWs& W = ss.W;
   GP_CUDA(launch_pad_block(y, prob->n, 1, 1, W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   if ((s = fill_probes(prob, o, W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;
   s = run_cg(prob, ss.pc, o->prec, W, w, effective_maxit(prob, o), o->cg_rtol, st);
   if (s != GP_OK) return s;
   if (p > 0) {
-    if ((s = run_lanczos(prob, ss.pc, o->prec, W, 1, p, o->nlanczos, st)) != GP_OK) return s;
+    if ((s = run_lanczos(prob, ss.pl, ss.slq_prec, W, 1, p, o->nlanczos, st)) != GP_OK) return s;
     GP_CUDA(cudaMemcpyAsync(W.S->out, W.S2->out, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
   GP_CUDA(launch_yalpha(W.S, W.B, W.X, ss.pc.nr_pad, ss.pc.w_pad, W.red, st));
@@ -649,7 +684,8 @@ static gp_status check_conv(const CgState* S, int w, int maxit, double rtol, cud
 // the padded right-hand side (FP32).
 // ---------------------------------------------------------------------------
 static size_t refine_extra_offset(const SimtPlan& pc, int prec) {
-  return (carve_solve(nullptr, pc, pc, false, 0, prec).bytes + 255) & ~static_cast<size_t>(255);
+  return (carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes + 255) &
+         ~static_cast<size_t>(255);
 }
 
 static size_t refine_bytes(const SimtPlan& pc, int prec) {
@@ -668,7 +704,7 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   unify_width(pc, pg);   // the widths setup_solve uses
   if ((s = check_ws(ws, ws_bytes, refine_bytes(pc, prec))) != GP_OK) return s;
   SolveSetup ss;
-  if ((s = setup_solve(prob, w, false, prec, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, false, prec, 0, prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
   const size_t plane = static_cast<size_t>(ss.pc.nr_pad) * ss.pc.w_pad;
   char* extra = static_cast<char*>(ws) + refine_extra_offset(ss.pc, prec);
   double* x64 = reinterpret_cast<double*>(extra);
@@ -764,17 +800,16 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
       unify_width(pc, pg);
       if (opts != nullptr && opts->refine_rtol > 0)
         return refine_bytes(pc, prec);
-      return carve_solve(nullptr, pc, pc, false, 0, prec).bytes;
+      return carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes;
     }
     case GP_OP_SLQ:
     case GP_OP_LOSS_GRAD: {
       if (check_opts(opts, op == GP_OP_SLQ) != GP_OK) return 0;
       const int ww = op == GP_OP_SLQ ? opts->nprobe : 1 + opts->nprobe;
-      SimtPlan pc = plan_for(n, n, prob->d, ww, false, prob->kernel, prec);
-      SimtPlan pg = plan_for(n, n, prob->d, ww, true, prob->kernel, GP_PREC_FP32);
-      unify_width(pc, pg);
       const int lz_k = opts->nprobe > 0 ? opts->nlanczos : 0;
-      return carve_solve(nullptr, pc, pg, op == GP_OP_LOSS_GRAD, lz_k, prec).bytes;
+      const int sp = slq_prec_of(opts);
+      const SolvePlans P = solve_plans(prob, ww, prec, lz_k, sp);
+      return carve_solve(nullptr, P.pc, P.pg, P.pl, op == GP_OP_LOSS_GRAD, lz_k, prec, sp).bytes;
     }
   }
   set_error("unknown op");
@@ -804,7 +839,8 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
     return refine_solve(prob, B, w, Xsol, nullptr, opts, iters, relres, ws, ws_bytes, st);
   SolveSetup ss;
-  if ((s = setup_solve(prob, w, false, opts->prec, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, false, opts->prec, 0, opts->prec, ws, ws_bytes, st, ss)) != GP_OK)
+    return s;
   GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   const int maxit = effective_maxit(prob, opts);
   s = run_cg(prob, ss.pc, opts->prec, ss.W, w, maxit, opts->cg_rtol, st);
@@ -840,10 +876,11 @@ gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, doubl
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int p = opts->nprobe;
   SolveSetup ss;
-  if ((s = setup_solve(prob, p, false, opts->prec, opts->nlanczos, ws, ws_bytes, st, ss)) != GP_OK)
+  if ((s = setup_solve(prob, p, false, opts->prec, opts->nlanczos, slq_prec_of(opts), ws, ws_bytes,
+                       st, ss)) != GP_OK)
     return s;
   if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st)) != GP_OK) return s;
-  if ((s = run_lanczos(prob, ss.pc, opts->prec, ss.W, 0, p, opts->nlanczos, st)) != GP_OK) return s;
+  if ((s = run_lanczos(prob, ss.pl, ss.slq_prec, ss.W, 0, p, opts->nlanczos, st)) != GP_OK) return s;
   double out[16];
   GP_CUDA(cudaMemcpyAsync(out, ss.W.S2->out, sizeof(out), cudaMemcpyDeviceToHost, st));
   if ((s = device_status(&ss.W.S2->err, st)) != GP_OK) return s;
@@ -903,7 +940,8 @@ gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, con
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int w = 1 + opts->nprobe;
   SolveSetup ss;
-  if ((s = setup_solve(prob, w, true, GP_PREC_FP32, 0, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  if ((s = setup_solve(prob, w, true, GP_PREC_FP32, 0, GP_PREC_FP32, ws, ws_bytes, st, ss)) != GP_OK)
+    return s;
   // B = [alpha | Z] (alpha = column 0 of W), X = W.
   GP_CUDA(launch_pad_block(Wsol, prob->n, 1, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   if ((s = fill_probes(prob, opts, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;

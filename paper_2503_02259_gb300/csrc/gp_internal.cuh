@@ -91,6 +91,14 @@ void profile_product_end(cudaStream_t st);
 // ---------------------------------------------------------------------------
 #ifdef __CUDACC__
 namespace gp {
+
+// Staged point arrays hold tiles of 32 points, dimension-major within a tile:
+// coordinate t of point i (dp stored coordinates per point) is at
+// ((i / 32) * dp + t) * 32 + i % 32.  A tile of 32 points is contiguous.
+__host__ __device__ __forceinline__ int64_t pt_index(int64_t i, int t, int dp) {
+  return ((i >> 5) * dp + t) * 32 + (i & 31);
+}
+
 namespace dev {
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {

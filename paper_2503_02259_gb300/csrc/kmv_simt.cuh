@@ -14,7 +14,10 @@
 // rounding error at ~eps (sqrt(kBN) + sqrt(n / kBN)) instead of ~eps sqrt(n).
 //
 // Point and V tiles are staged by the bulk-copy (TMA) engine into a two-stage
-// shared-memory ring, each stage completed on its own mbarrier.
+// shared-memory ring, each stage completed on its own mbarrier.  Points are
+// stored in tiles of 32, dimension-major within a tile (pt_index), so one
+// 16-byte load brings one coordinate of four consecutive points and entries
+// are evaluated four at a time in packed FP32x2 arithmetic.
 #pragma once
 
 #include "gp_internal.cuh"
@@ -26,48 +29,56 @@ struct DimTraits {
   static constexpr int DP = DT <= 2 ? 2 : ((DT + 3) / 4) * 4;
 };
 
-// k and the scaled derivative D' from the scaled squared distance q.
+// k and the scaled derivative D' of two entries from their scaled squared
+// distances q, in packed FP32x2 arithmetic (MUFU operations per lane).  Every
+// operation is rounded explicitly, so every kernel evaluates bit-identical
+// entries.
 template <int KIND, bool GRAD>
-__device__ __forceinline__ void eval_entry(float q, float& kv, float& dv) {
+__device__ __forceinline__ void eval_pair(float2 q, float2& kv, float2& dv) {
   if constexpr (KIND == GP_KERNEL_GAUSSIAN) {
-    kv = dev::ex2_approx(-q);
-    if constexpr (GRAD) dv = __fmul_rn(kv, q);
+    kv = make_float2(dev::ex2_approx(-q.x), dev::ex2_approx(-q.y));
+    if constexpr (GRAD) dv = __fmul2_rn(kv, q);
   } else {
-    // Explicit roundings so that every variant evaluates bit-identical entries.
-    const float a = dev::sqrt_approx(q);
-    const float e = dev::ex2_approx(__fmul_rn(a, -1.4426950408889634f));
-    kv = __fmaf_rn(a, e, e);
-    if constexpr (GRAD) dv = __fmul_rn(a, __fmul_rn(a, e));
+    const float2 a = make_float2(dev::sqrt_approx(q.x), dev::sqrt_approx(q.y));
+    const float2 t = __fmul2_rn(a, make_float2(-1.4426950408889634f, -1.4426950408889634f));
+    const float2 e = make_float2(dev::ex2_approx(t.x), dev::ex2_approx(t.y));
+    kv = __ffma2_rn(a, e, e);
+    if constexpr (GRAD) dv = __fmul2_rn(a, __fmul2_rn(a, e));
   }
 }
 
+// Scaled squared distances from x_i (each coordinate duplicated into both
+// lanes) to the four points j, j+1, j+2, j+3 (j % 4 == 0) of a dimension-major
+// point tile xt [dp][32]: (q_j, q_j+1) and (q_j+2, q_j+3).  Difference form:
+// d = x_i - x_j as fma(x_j, -1, x_i), q = d0 d0 + d1 d1 + ... left to right.
 template <int DT>
-__device__ __forceinline__ float sqdist_tile(const float (&xi)[DT], const float* xj) {
-  constexpr int DP = DimTraits<DT>::DP;
-  float q = 0.f;
-  if constexpr (DP == 2) {
-    const float2 p = *reinterpret_cast<const float2*>(xj);
-    const float d0 = xi[0] - p.x;
-    q = d0 * d0;
-    if constexpr (DT > 1) {
-      const float d1 = xi[1] - p.y;
-      q = fmaf(d1, d1, q);
-    }
-  } else {
+__device__ __forceinline__ void sqdist_quad(const float2 (&xi2)[DT], const float* xt, int j,
+                                            float2& q01, float2& q23) {
+  const float2 m1 = make_float2(-1.f, -1.f);
 #pragma unroll
-    for (int t4 = 0; t4 < DP / 4; ++t4) {
-      const float4 p = *reinterpret_cast<const float4*>(xj + 4 * t4);
-      const float pv[4] = {p.x, p.y, p.z, p.w};
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        if (4 * t4 + u < DT) {
-          const float dd = xi[4 * t4 + u] - pv[u];
-          q = fmaf(dd, dd, q);
-        }
-      }
+  for (int t = 0; t < DT; ++t) {
+    const float4 p = *reinterpret_cast<const float4*>(xt + t * 32 + j);
+    const float2 d01 = __ffma2_rn(make_float2(p.x, p.y), m1, xi2[t]);
+    const float2 d23 = __ffma2_rn(make_float2(p.z, p.w), m1, xi2[t]);
+    if (t == 0) {
+      q01 = __fmul2_rn(d01, d01);
+      q23 = __fmul2_rn(d23, d23);
+    } else {
+      q01 = __ffma2_rn(d01, d01, q01);
+      q23 = __ffma2_rn(d23, d23, q23);
     }
   }
-  return q;
+}
+
+// Coordinates of the row point i, duplicated into both lanes.
+template <int DT>
+__device__ __forceinline__ void load_row_point(const float* xr, int64_t i, float2 (&xi2)[DT]) {
+  constexpr int DP = DimTraits<DT>::DP;
+#pragma unroll
+  for (int t = 0; t < DT; ++t) {
+    const float v = xr[pt_index(i, t, DP)];
+    xi2[t] = make_float2(v, v);
+  }
 }
 
 template <int KIND, bool GRAD, int DT, int TW>
@@ -97,9 +108,8 @@ __global__ void __launch_bounds__(kThreads)
   const uint32_t xbytes = kBN * DP * 4;
   const uint32_t vbytes = kBN * w_pad * 4;
 
-  float xi[DT];
-#pragma unroll
-  for (int t = 0; t < DT; ++t) xi[t] = a.xr[row * DP + t];
+  float2 xi2[DT];
+  load_row_point<DT>(a.xr, row, xi2);
 
   float2 accK[TW2], runK[TW2];
   float2 accD[GRAD ? TW2 : 1], runD[GRAD ? TW2 : 1];
@@ -144,24 +154,31 @@ __global__ void __launch_bounds__(kThreads)
     }
     const float* xs = sX + stage * kBN * DP;
     const float* vs = sV + stage * kBN * w_pad + g * TW;
-#pragma unroll 2
-    for (int jj = 0; jj < kBN; ++jj) {
-      const float q = sqdist_tile<DT>(xi, xs + jj * DP);
-      float kv, dv;
-      eval_entry<KIND, GRAD>(q, kv, dv);
-      const float2 kk = make_float2(kv, kv);
-      const float2 dd = make_float2(GRAD ? dv : 0.f, GRAD ? dv : 0.f);
-      const float4* v4 = reinterpret_cast<const float4*>(vs + jj * w_pad);
+#pragma unroll 1
+    for (int jj = 0; jj < kBN; jj += 4) {
+      float2 q01, q23;
+      sqdist_quad<DT>(xi2, xs + (jj >> 5) * (32 * DP), jj & 31, q01, q23);
+      float2 k01, d01 = make_float2(0.f, 0.f), k23, d23 = make_float2(0.f, 0.f);
+      eval_pair<KIND, GRAD>(q01, k01, d01);
+      eval_pair<KIND, GRAD>(q23, k23, d23);
+      const float kq[4] = {k01.x, k01.y, k23.x, k23.y};
+      const float dq[4] = {d01.x, d01.y, d23.x, d23.y};
 #pragma unroll
-      for (int c = 0; c < TW / 4; ++c) {
-        const float4 v = v4[c];
-        const float2 v01 = make_float2(v.x, v.y);
-        const float2 v23 = make_float2(v.z, v.w);
-        accK[2 * c] = __ffma2_rn(kk, v01, accK[2 * c]);
-        accK[2 * c + 1] = __ffma2_rn(kk, v23, accK[2 * c + 1]);
-        if constexpr (GRAD) {
-          accD[2 * c] = __ffma2_rn(dd, v01, accD[2 * c]);
-          accD[2 * c + 1] = __ffma2_rn(dd, v23, accD[2 * c + 1]);
+      for (int u = 0; u < 4; ++u) {
+        const float2 kk = make_float2(kq[u], kq[u]);
+        const float2 dd = make_float2(dq[u], dq[u]);
+        const float4* v4 = reinterpret_cast<const float4*>(vs + (jj + u) * w_pad);
+#pragma unroll
+        for (int c = 0; c < TW / 4; ++c) {
+          const float4 v = v4[c];
+          const float2 v01 = make_float2(v.x, v.y);
+          const float2 v23 = make_float2(v.z, v.w);
+          accK[2 * c] = __ffma2_rn(kk, v01, accK[2 * c]);
+          accK[2 * c + 1] = __ffma2_rn(kk, v23, accK[2 * c + 1]);
+          if constexpr (GRAD) {
+            accD[2 * c] = __ffma2_rn(dd, v01, accD[2 * c]);
+            accD[2 * c + 1] = __ffma2_rn(dd, v23, accD[2 * c + 1]);
+          }
         }
       }
     }

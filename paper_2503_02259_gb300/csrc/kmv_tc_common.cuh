@@ -134,21 +134,24 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
-// Store 16 bytes of one operand row (EPC entries) at `off` of the hi matrix and,
-// when SPLIT, the rounded remainder at `off` of the lo matrix (generic proxy).
+// Store 16 bytes of one operand row (EPC entries, as EPC / 2 pairs) at `off` of
+// the hi matrix and, when SPLIT, the rounded remainder at `off` of the lo matrix
+// (generic proxy).  The remainder v - hi is formed as fma(hi, -1, v) in packed
+// FP32x2, which rounds like the subtraction.
 template <int MODE, bool SPLIT>
 __device__ __forceinline__ void store_group(unsigned char* hi, unsigned char* lo, uint32_t off,
-                                            const float (&v)[16 / TcTraits<MODE>::ES]) {
+                                            const float2 (&v)[8 / TcTraits<MODE>::ES]) {
+  const float2 m1 = make_float2(-1.f, -1.f);
   if constexpr (TcTraits<MODE>::FMT == 1) {
     uint32_t h[4], l[4];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * u], v[2 * u + 1]);
+      const __nv_bfloat162 p = __floats2bfloat162_rn(v[u].x, v[u].y);
       h[u] = *reinterpret_cast<const uint32_t*>(&p);
       if constexpr (SPLIT) {
-        const float2 back = __bfloat1622float2(p);
-        const __nv_bfloat162 r = __floats2bfloat162_rn(v[2 * u] - back.x, v[2 * u + 1] - back.y);
-        l[u] = *reinterpret_cast<const uint32_t*>(&r);
+        const float2 r = __ffma2_rn(__bfloat1622float2(p), m1, v[u]);
+        const __nv_bfloat162 q = __floats2bfloat162_rn(r.x, r.y);
+        l[u] = *reinterpret_cast<const uint32_t*>(&q);
       }
     }
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
@@ -156,12 +159,20 @@ __device__ __forceinline__ void store_group(unsigned char* hi, unsigned char* lo
   } else {
     uint32_t h[4];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) h[u] = to_tf32(v[u]);
+    for (int u = 0; u < 2; ++u) {
+      h[2 * u] = to_tf32(v[u].x);
+      h[2 * u + 1] = to_tf32(v[u].y);
+    }
     *reinterpret_cast<uint4*>(hi + off) = make_uint4(h[0], h[1], h[2], h[3]);
     if constexpr (SPLIT) {
       uint32_t l[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) l[u] = to_tf32(v[u] - __uint_as_float(h[u]));
+      for (int u = 0; u < 2; ++u) {
+        const float2 hv = make_float2(__uint_as_float(h[2 * u]), __uint_as_float(h[2 * u + 1]));
+        const float2 r = __ffma2_rn(hv, m1, v[u]);
+        l[2 * u] = to_tf32(r.x);
+        l[2 * u + 1] = to_tf32(r.y);
+      }
       *reinterpret_cast<uint4*>(lo + off) = make_uint4(l[0], l[1], l[2], l[3]);
     }
   }

@@ -1,5 +1,5 @@
 // Instantiations of the tensor-core product for one operand mode, compiled once
-// per mode with -DGP_TC_MODE=<1|2|3> (TF32, BF16, split TF32).
+// per mode with -DGP_TC_MODE=<1|2|3|4> (TF32, BF16, split TF32, split BF16).
 #include <atomic>
 
 #include <cuda_bf16.h>
@@ -33,11 +33,11 @@ __global__ void tc_stage_v_kernel(const float* v, int n, int jtiles, unsigned ch
     const int kg = static_cast<int>(e % G::CK);
     const int c = static_cast<int>((e / G::CK) % n);
     const int64_t jt = e / (static_cast<int64_t>(G::CK) * n);
-    float vals[EPC];
+    float2 vals[EPC / 2];
 #pragma unroll
-    for (int u = 0; u < EPC; ++u) {
-      const int64_t j = jt * kTcBK + kg * EPC + u;
-      vals[u] = v[j * n + c];
+    for (int u = 0; u < EPC / 2; ++u) {
+      const int64_t j = jt * kTcBK + kg * EPC + 2 * u;
+      vals[u] = make_float2(v[j * n + c], v[(j + 1) * n + c]);
     }
     const uint32_t off = static_cast<uint32_t>(c >> 3) * G::SBO + static_cast<uint32_t>(kg) * G::LBO +
                          static_cast<uint32_t>(c & 7) * 16;

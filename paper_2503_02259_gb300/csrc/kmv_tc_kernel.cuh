@@ -141,9 +141,8 @@ __global__ void GP_TC_BOUNDS
 
   if (is_eval) {
     // ------------------------------------------------------------ eval warps
-    float xi[DT];
-#pragma unroll
-    for (int t = 0; t < DT; ++t) xi[t] = a.xr[row * DP + t];
+    float2 xi2[DT];
+    load_row_point<DT>(a.xr, row, xi2);
     {
       // Zero the running sums: warp (quad, half) clears chunks c % 2 == half.
       uint32_t z[16];
@@ -170,14 +169,14 @@ __global__ void GP_TC_BOUNDS
 #pragma unroll
       for (int kh = 0; kh < HALF_CK; ++kh) {
         const int kg = half * HALF_CK + kh;
-        float kv[EPC], dv[EPC];
+        float2 kv[EPC / 2], dv[EPC / 2];
 #pragma unroll
-        for (int u = 0; u < EPC; ++u) {
-          const float q = sqdist_tile<DT>(xi, xs + (kg * EPC + u) * DP);
-          float k1, d1 = 0.f;
-          eval_entry<KIND, GRAD>(q, k1, d1);
-          kv[u] = k1;
-          dv[u] = d1;
+        for (int u = 0; u < EPC / 4; ++u) {
+          float2 q01, q23;
+          sqdist_quad<DT>(xi2, xs, kg * EPC + 4 * u, q01, q23);
+          dv[2 * u] = dv[2 * u + 1] = make_float2(0.f, 0.f);
+          eval_pair<KIND, GRAD>(q01, kv[2 * u], dv[2 * u]);
+          eval_pair<KIND, GRAD>(q23, kv[2 * u + 1], dv[2 * u + 1]);
         }
         const uint32_t off = rowoff + static_cast<uint32_t>(kg) * G::LBO;
         tc::store_group<MODE, (NSA == 2)>(aK, aK + L.abytes, off, kv);

@@ -1,13 +1,17 @@
 // Continuous-batching request server (include/gp.h, "Serving").
 //
 // One device pool of the HBM budget is reserved at creation and sub-allocated
-// first-fit; max_slots worker threads each own a CUDA stream.  A worker takes
-// the queue head as soon as the head's footprint fits the pool's free space,
-// runs the request through the library's own calls on its stream and returns
-// the memory, so requests that arrive while others are running join them on
-// the device and their kernels overlap through the streams.  The paper serves
-// nothing; its stateless loss/gradient and prediction calls (§Design and
-// Implementation) are what each request runs.
+// first-fit; max_slots worker threads each own one CUDA stream per stream
+// priority level.  A worker takes the queue head as soon as the head's
+// footprint fits the pool's free space, runs the request through the library's
+// own calls and returns the memory, so requests that arrive while others are
+// running join them on the device: the CTAs of all running requests' kernels
+// are interleaved on the SMs by the hardware work distributor.  A request runs
+// on a stream whose priority falls with its work (entries x columns), so the
+// tiles of a small request are dispatched ahead of the queued tiles of a large
+// one instead of waiting for them.  The paper serves nothing; its stateless
+// loss/gradient and prediction calls (§Design and Implementation) are what
+// each request runs.
 #include <string.h>
 
 #include <algorithm>
@@ -85,6 +89,7 @@ gp_solve_opts opts_of(const gp_request& r, bool loss) {
   o.nlanczos = r.nlanczos > 0 ? r.nlanczos : 20;
   o.cg_maxit = r.cg_maxit;
   o.prec = r.prec;
+  o.slq_prec = r.slq_prec;
   o.cg_rtol = r.cg_rtol;
   o.seed = r.seed;
   return o;
@@ -219,10 +224,40 @@ void run_job(gp_server* srv, Job& j, char* base, cudaStream_t st) {
   (void)srv;
 }
 
+// Entries x columns of the products a request issues (its CG, Lanczos and
+// gradient passes, or its CG and the prediction product).
+double request_work(const gp_request& r) {
+  const double n = static_cast<double>(r.n);
+  const int maxit = r.cg_maxit > 0 ? r.cg_maxit : 1000;
+  if (r.kind == 0) {
+    const int k = r.nlanczos > 0 ? r.nlanczos : 20;
+    return n * n * (1.0 + r.nprobe) * (maxit + k + 1);
+  }
+  return n * n * maxit + n * static_cast<double>(r.m);
+}
+
+// Stream priority level (0 = highest) of a request: one level per decade of
+// work above 1e9 entries x columns, clamped to the levels the device offers.
+int priority_level(const gp_request& r, int levels) {
+  const double w = request_work(r);
+  int b = 0;
+  for (double t = 1e10; w >= t && b < levels - 1; t *= 10.0) ++b;
+  return b;
+}
+
 void worker_main(gp_server* srv) {
   cudaSetDevice(srv->device);
-  cudaStream_t st = nullptr;
-  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return;
+  int least = 0, greatest = 0;
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+  const int levels = std::max(1, std::min(8, least - greatest + 1));
+  std::vector<cudaStream_t> streams(levels, nullptr);
+  for (int i = 0; i < levels; ++i) {
+    // Level i has the i-th highest priority (numerically greatest + i).
+    if (cudaStreamCreateWithPriority(&streams[i], cudaStreamNonBlocking, greatest + i) != cudaSuccess) {
+      for (int k = 0; k < i; ++k) cudaStreamDestroy(streams[k]);
+      return;
+    }
+  }
   for (;;) {
     std::shared_ptr<Job> job;
     size_t off = 0;
@@ -239,7 +274,7 @@ void worker_main(gp_server* srv) {
       srv->peak_bytes = std::max(srv->peak_bytes, srv->alloc->in_use());
       job->res.t_start_s = seconds_since(srv->t0);
     }
-    run_job(srv, *job, srv->pool + off, st);
+    run_job(srv, *job, srv->pool + off, streams[priority_level(job->req, levels)]);
     {
       std::lock_guard<std::mutex> lk(srv->mu);
       srv->alloc->release(off, job->lay.total);
@@ -251,7 +286,7 @@ void worker_main(gp_server* srv) {
     srv->cv_work.notify_all();
     srv->cv_done.notify_all();
   }
-  cudaStreamDestroy(st);
+  for (cudaStream_t st : streams) cudaStreamDestroy(st);
 }
 
 gp_status fail(gp_status st, const char* msg) {

@@ -85,13 +85,17 @@ __device__ __forceinline__ double final_sum(const double* red, int q, int c, int
 
 // ------------------------------------------------------------------ staging --
 
+// Writes the staged layout of pt_index in order: element e is coordinate
+// t = (e / 32) % dp of point i = (e / (32 dp)) * 32 + e % 32.
 __global__ void stage_points_kernel(const float* X, int64_t n, int d, int64_t ld, const float* ref,
                                     float cs, int dp, int64_t n_pad, float* out) {
   const int64_t total = n_pad * dp;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = e / dp;
-    const int t = static_cast<int>(e - i * dp);
+    const int64_t tile = e / (32 * dp);
+    const int rem = static_cast<int>(e - tile * 32 * dp);
+    const int t = rem >> 5;
+    const int64_t i = tile * 32 + (rem & 31);
     float v = 0.f;
     if (i < n && t < d) v = (X[i * ld + t] - ref[t]) * cs;
     out[e] = v;

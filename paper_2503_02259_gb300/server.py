@@ -34,7 +34,8 @@ class Server:
     @staticmethod
     def request(kind: int, X: np.ndarray, y: np.ndarray, kernel: int, theta, nprobe: int = 16,
                 Xstar: np.ndarray | None = None, cg_maxit: int = 20, nlanczos: int = 20,
-                cg_rtol: float = 1e-8, seed: int = 0, prec: int = B.PREC_FP32):
+                cg_rtol: float = 1e-8, seed: int = 0, prec: int = B.PREC_FP32,
+                slq_prec: int = B.PREC_FP32):
         X = np.ascontiguousarray(X, dtype=np.float32)
         y = np.ascontiguousarray(y, dtype=np.float32).reshape(-1)
         Xs = None if Xstar is None else np.ascontiguousarray(Xstar, dtype=np.float32)
@@ -44,7 +45,7 @@ class Server:
                          y=y.ctypes.data, Xstar=0 if Xs is None else Xs.ctypes.data,
                          m=0 if Xs is None else Xs.shape[0], cg_maxit=int(cg_maxit),
                          nlanczos=int(nlanczos), cg_rtol=float(cg_rtol), seed=int(seed) & (2**64 - 1),
-                         prec=int(prec), reserved=0)
+                         prec=int(prec), slq_prec=int(slq_prec))
         return r, (X, y, Xs)
 
     def footprint(self, req) -> int:

@@ -158,3 +158,19 @@ def test_bad_arguments_raise(api):
         api.gp_kernel_matmul(X, V, 0, (0.1, 1.0, 0.3))
     with pytest.raises((GPError, ValueError)):
         api.gp_kernel_matmul(X, V[:, :4], 0, (0.1, 1.0, -0.3))
+
+
+def test_pipe_rate_microbenchmarks_are_plausible(api):
+    # The FP32 pipe of a GB300 (152 SMs x 128 lanes x 2 flops x up to 2.07 GHz
+    # = 80.5 TFLOP/s) and its MUFU unit: the measured rates must be positive,
+    # below the unit-count bound, and within a factor 4 of it (clocks vary).
+    from paper_2503_02259_gb300 import _binding as B
+    import torch
+    f, m = B.c_double(), B.c_double()
+    B.check(B.lib().gp_measure_pipe_rates(B.ctypes.byref(f), B.ctypes.byref(m),
+                                          torch.cuda.current_stream().cuda_stream),
+            "gp_measure_pipe_rates")
+    props = torch.cuda.get_device_properties(0)
+    bound = props.multi_processor_count * 128 * 2 * 2.1e9 / 1e12
+    assert bound / 4 < f.value <= bound * 1.02
+    assert m.value > 100.0

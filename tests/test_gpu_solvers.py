@@ -138,13 +138,22 @@ def test_autograd_function(api, small):
         assert rel(float(L.detach()), est["loss"]) <= 1e-4
 
 
-def test_differentiation_config_subsample(api):
+@pytest.fixture(scope="module")
+def diff_sub():
     # n = 4000 subsample of the d = 8, 0.5 N(0, I) differentiation problem;
     # Gaussian s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps.
     prob = inputs.diff_problem(seed=0, n=4000)
     Z = O.rademacher_probes(prob.n, 32, 77)
-    est = O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 40)
-    opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-8, seed=77)
+    return prob, O.est_nll(prob.X, prob.y, prob.kind, prob.theta, Z, 40)
+
+
+# (CG arithmetic, SLQ arithmetic): FP32; split TF32 for both; split BF16 for the
+# CG solves with split TF32 for the Lanczos products (the log-determinant needs
+# ~24-bit kernel entries; split BF16 keeps 16).
+@pytest.mark.parametrize("prec,slq", [(0, 0), (3, -1), (4, 3)])
+def test_differentiation_config_subsample(api, diff_sub, prec, slq):
+    prob, est = diff_sub
+    opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-8, seed=77, prec=prec, slq_prec=slq)
     loss, grad, info = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
     gfloor = 1e-3 * np.linalg.norm(est["grad"])
     assert rel(loss, est["loss"]) <= 1e-4, (loss, est["loss"])
