@@ -43,6 +43,10 @@ struct ProfileState {
 };
 thread_local ProfileState t_prof;
 constexpr size_t kMaxProfiled = 65536;
+// Stream capture in progress on this host thread: launches are recorded into a
+// graph, not executed, so they are counted separately and not timed.
+thread_local int t_capturing = 0;
+thread_local int64_t t_captured_launches = 0;
 std::mutex g_mu;
 std::map<std::tuple<int, int, int, int, int, int>, int> g_occ;
 std::map<int, int> g_nsm;
@@ -50,10 +54,15 @@ std::map<int, int> g_nsm;
 
 void set_error(const std::string& msg) { t_err = msg; }
 
-void count_launch() { ++t_prof.launches; }
+void count_launch() {
+  if (t_capturing)
+    ++t_captured_launches;
+  else
+    ++t_prof.launches;
+}
 
 void profile_product_begin(cudaStream_t st) {
-  if (!t_prof.on) return;
+  if (!t_prof.on || t_capturing) return;
   ++t_prof.product_launches;
   if (t_prof.used >= kMaxProfiled) return;
   if (t_prof.used == t_prof.ev.size()) {
@@ -69,7 +78,7 @@ void profile_product_begin(cudaStream_t st) {
 }
 
 void profile_product_end(cudaStream_t st) {
-  if (!t_prof.on || t_prof.used >= t_prof.ev.size()) return;
+  if (!t_prof.on || t_capturing || t_prof.used >= t_prof.ev.size()) return;
   cudaEventRecord(t_prof.ev[t_prof.used].second, st);
   ++t_prof.used;
 }
@@ -451,10 +460,85 @@ static gp_status product_call(const gp_problem* prob, const float* V, int32_t w,
 // ---------------------------------------------------------------------------
 namespace gp {
 
-gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W, int w, int maxit,
-                 double rtol, cudaStream_t st) {
+// One block-CG iteration: the product K P, then alpha, the x / r update and the
+// p update (vec_kernels.cu).
+static gp_status cg_iteration(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W,
+                              cudaStream_t st) {
   const int64_t n = prob->n;
   const double f2 = prob->theta.f * prob->theta.f;
+  gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.vt, W.part, nullptr,
+                            &W.S->n_active, &W.S->err, st);
+  if (s != GP_OK) return s;
+  GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
+                              prob->theta.s, W.red, st));
+  GP_CUDA(launch_cg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
+  GP_CUDA(launch_cg_pupdate(W.S, W.R, W.P, p.nr_pad, p.w_pad, st));
+  return GP_OK;
+}
+
+// A private non-blocking stream of this host thread on the current device,
+// used only to capture graphs (the caller's stream may be the legacy default
+// stream, which cannot be captured).  Lives as long as the thread.
+static cudaStream_t capture_stream() {
+  thread_local std::map<int, cudaStream_t> streams;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  cudaStream_t cs = nullptr;
+  if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+  streams[dev] = cs;
+  return cs;
+}
+
+// The launches of one solver iteration captured once as a CUDA graph and then
+// replayed on the caller's stream: one graph launch instead of one launch per
+// kernel (the small-n iterations are launch-bound).
+class IterationGraph {
+ public:
+  IterationGraph() = default;
+  IterationGraph(const IterationGraph&) = delete;
+  IterationGraph& operator=(const IterationGraph&) = delete;
+  ~IterationGraph() {
+    if (exec_ != nullptr) cudaGraphExecDestroy(exec_);
+  }
+  // Records body(stream) into the graph; false (and no graph) if anything fails.
+  template <class Body>
+  bool capture(Body&& body) {
+    cudaStream_t cs = capture_stream();
+    if (cs == nullptr || cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ++t_capturing;
+    t_captured_launches = 0;
+    const gp_status s = body(cs);
+    --t_capturing;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(cs, &g);
+    bool ok = s == GP_OK && e == cudaSuccess && g != nullptr &&
+              cudaGraphInstantiate(&exec_, g, 0) == cudaSuccess;
+    if (g != nullptr) cudaGraphDestroy(g);
+    if (!ok) {
+      exec_ = nullptr;
+      cudaGetLastError();
+      return false;
+    }
+    kernels_ = t_captured_launches;
+    return true;
+  }
+  cudaError_t launch(cudaStream_t st) {
+    for (int64_t k = 0; k < kernels_; ++k) count_launch();
+    return cudaGraphLaunch(exec_, st);
+  }
+
+ private:
+  cudaGraphExec_t exec_ = nullptr;
+  int64_t kernels_ = 0;
+};
+
+gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W, int w, int maxit,
+                 double rtol, cudaStream_t st) {
   GP_CUDA(launch_cg_init(W.S, W.B, W.X, W.R, W.P, p.nr_pad, p.w_pad, w, maxit, rtol, W.red, st));
   int chunk = 4;
   int issued = 0;
@@ -462,16 +546,24 @@ gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W
     int n_active;
     int err;
   } h{1, 0};
+  // The first iteration runs eagerly (it also performs the one-time kernel
+  // set-up); the rest replay a graph of one iteration, or run eagerly if the
+  // graph could not be built.
+  IterationGraph graph;
+  bool tried = false, use_graph = false;
   while (issued < maxit) {
     const int todo = std::min(chunk, maxit - issued);
     for (int k = 0; k < todo; ++k) {
-      gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.vt, W.part, nullptr,
-                                &W.S->n_active, &W.S->err, st);
-      if (s != GP_OK) return s;
-      GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
-                                  prob->theta.s, W.red, st));
-      GP_CUDA(launch_cg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
-      GP_CUDA(launch_cg_pupdate(W.S, W.R, W.P, p.nr_pad, p.w_pad, st));
+      if (issued + k > 0 && !tried) {
+        tried = true;
+        use_graph = graph.capture([&](cudaStream_t cs) { return cg_iteration(prob, p, prec, W, cs); });
+      }
+      if (use_graph) {
+        GP_CUDA(graph.launch(st));
+      } else {
+        gp_status s = cg_iteration(prob, p, prec, W, st);
+        if (s != GP_OK) return s;
+      }
     }
     issued += todo;
     GP_CUDA(cudaMemcpyAsync(&h, W.S, sizeof(h), cudaMemcpyDeviceToHost, st));
