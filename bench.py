@@ -56,6 +56,23 @@ def _traffic():
         return {}
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest of the ranks' values (the slowest replica sets the job's time);
+    `value` itself without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(world: int, work_per_rank: float, slowest_ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas: all ranks' work over
+    the slowest rank's time."""
+    return world * work_per_rank / (slowest_ms * 1e-3)
+
+
 class ClockSampler:
     """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -459,12 +476,9 @@ def main() -> int:
     launches = B.c_int64()
     B.check(L.gp_profile_end(B.ctypes.byref(prod_ms), B.ctypes.byref(prod_n),
                              B.ctypes.byref(launches)), "gp_profile_end")
-    step_ms = sum(a.elapsed_time(b) for a, b in zip(starts, stops))
+    step_ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, stops)), dist, dev)
     if dist:
-        t = torch.tensor([step_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
         dist.barrier()
-        step_ms = float(t.item())
     clocks = sampler.stop() if sampler else None
 
     # End to end through the public call with host buffers: pinned H2D of X and V,
@@ -490,7 +504,7 @@ def main() -> int:
             o.copy_(src, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e2e_steps, dist, dev)
     h2d = Xp.numel() * 4 + Vp.numel() * 4
     d2h = 3 * N_PTS * W * 4
 
@@ -509,7 +523,7 @@ def main() -> int:
 
     per_step_ms = step_ms / args.steps
     work = N_PTS * N_PTS * W
-    value = world * work / (per_step_ms * 1e-3)
+    value = replica_rate(world, work, per_step_ms)
     peaks = _peaks()
     sm_mhz = (clocks or {}).get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median") or 2070.0
     kern_ms = prod_ms.value / max(1, prod_n.value)
@@ -560,7 +574,7 @@ def main() -> int:
                                                    "the timed bracket)",
                        "parallelism": f"replicas x{world}" if world > 1 else "single GPU"},
             "roofline": roofline, "cpu_baseline": cpu,
-            "e2e": {"value": world * work / (e2e_ms * 1e-3), "unit": UNIT,
+            "e2e": {"value": replica_rate(world, work, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms},
             "gpu_launches": int(launches.value), "clocks": clocks}
     line.update(extras)

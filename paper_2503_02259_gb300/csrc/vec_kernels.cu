@@ -234,6 +234,7 @@ __global__ void cg_epi_alpha_kernel(CgState* S, const float* part_k, int split, 
       float q = 0.f;
       if (r < n) {
         double sk = 0.0;
+#pragma unroll 4
         for (int s = 0; s < split; ++s) sk += part_k[s * plane + idx];
         const double pv = P[idx];
         const double qd = f2 * sk + snoise * pv;
@@ -397,6 +398,7 @@ __global__ void lz_epi_alpha_kernel(CgState* S, const float* part_k, int split, 
       float wv = 0.f;
       if (r < n) {
         double sk = 0.0;
+#pragma unroll 4
         for (int s = 0; s < split; ++s) sk += part_k[s * plane + idx];
         const double qv = Qj[idx];
         wv = static_cast<float>(f2 * sk + snoise * qv);
@@ -518,13 +520,12 @@ __global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_
 
 // ---------------------------------------------------------------------- SLQ --
 
+// One block per probe (thread 0 works: the QR sweeps of different probes take
+// different paths, so they run in separate warps); the last block to finish
+// forms the mean and standard error over the probes in probe order.
 __global__ void slq_kernel(CgState* S, int col0, int p, int k) {
-  __shared__ double vals[kMaxW];
-  __shared__ int bad;
-  if (threadIdx.x == 0) bad = 0;
-  __syncthreads();
-  const int i = threadIdx.x;
-  if (i < p) {
+  const int i = blockIdx.x;
+  if (threadIdx.x == 0) {
     const int c = col0 + i;
     int m = S->iters[c];
     if (m > k) m = k;
@@ -532,21 +533,19 @@ __global__ void slq_kernel(CgState* S, int col0, int p, int k) {
     bool ok = true;
     const double v = lanczos_logquad(&S->ahist[0][c], &S->bhist[0][c], kMaxW, m, S->bn2[c], a, b,
                                      q, &ok);
-    vals[i] = v;
     S->slq_val[i] = v;
-    if (!ok) atomicExch(&bad, 1);
+    if (!ok) atomicExch(&S->err, kDevNumeric);
   }
-  __syncthreads();
+  if (!last_block(&S->ticket)) return;
   if (threadIdx.x == 0) {
     double mean = 0.0;
-    for (int j = 0; j < p; ++j) mean += vals[j];
+    for (int j = 0; j < p; ++j) mean += S->slq_val[j];
     mean = p > 0 ? mean / p : 0.0;
     double var = 0.0;
-    for (int j = 0; j < p; ++j) var += (vals[j] - mean) * (vals[j] - mean);
+    for (int j = 0; j < p; ++j) var += (S->slq_val[j] - mean) * (S->slq_val[j] - mean);
     const double se = p > 1 ? sqrt(var / (p - 1) / p) : 0.0;
     S->out[0] = mean;
     S->out[1] = se;
-    if (bad) S->err = kDevNumeric;
   }
 }
 
@@ -740,8 +739,10 @@ __global__ void refine_out_kernel(const double* x64, float* Xsol, int64_t n, int
 
 }  // namespace
 
+// Blocks of the reducing O(n w) kernels: about 32 rows per block (each thread a
+// row or two: these kernels are latency-bound at small n), at most 4 per SM.
 int red_blocks(int64_t n_pad) {
-  int64_t b = n_pad / 256;
+  int64_t b = n_pad / 32;
   if (b > 608) b = 608;
   if (b < 1) b = 1;
   return static_cast<int>(b);
@@ -870,7 +871,8 @@ size_t red_doubles(int64_t n_pad, int w_pad) {
 }
 
 cudaError_t launch_slq(CgState* S, int col0, int p, int k, cudaStream_t st) {
-  slq_kernel<<<1, kMaxW, 0, st>>>(S, col0, p, k);
+  if (p < 1) return cudaSuccess;
+  slq_kernel<<<p, 32, 0, st>>>(S, col0, p, k);
   count_launch();
   return cudaGetLastError();
 }

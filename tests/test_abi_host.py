@@ -74,6 +74,13 @@ def test_argument_errors_need_no_gpu(L):
     assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) == 0
     opts.nlanczos = 30
     assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) > 0
+    # slq_prec: a precision or GP_PREC_SAME (-1); anything else is refused.
+    for bad in (-2, 5, 99):
+        opts.slq_prec = bad
+        assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) == 0
+        assert b"slq_prec" in L.gp_last_error()
+    opts.slq_prec = B.PREC_SAME
+    assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) > 0
     # A workspace that is too small is refused before any launch.
     prob.theta.l = 0.3
     st = L.gp_kernel_matmul(ctypes.byref(prob), 256, 4, 512, 0, 1024, 16, None)

@@ -172,3 +172,25 @@ def test_loss_matern_and_user_probes(api):
     assert rel(loss, est["loss"]) <= 1e-4
     for t in range(3):
         assert rel(grad[t], est["grad"][t], gfloor) <= 1e-4
+
+
+def test_slq_arithmetic_is_chosen_separately(api, small):
+    # slq_prec selects the arithmetic of the Lanczos products alone: SLQ in FP32
+    # under a tensor-core CG equals the all-FP32 log-determinant (up to the order
+    # of the FP64 dot-product sums, which follows the padded width the two
+    # products share), and GP_PREC_SAME equals naming the CG arithmetic.  A
+    # tensor-core Lanczos product would move the result by ~1e-6.
+    prob, est, ex = small
+    X = _dev(prob.X)
+    ld32, _ = api.gp_slq_logdet(X, prob.kind, prob.theta,
+                                api.solve_opts(nprobe=10, nlanczos=30, seed=1234))
+    ld_a, _ = api.gp_slq_logdet(X, prob.kind, prob.theta,
+                                api.solve_opts(nprobe=10, nlanczos=30, seed=1234, prec=4, slq_prec=0))
+    assert rel(ld_a, ld32) <= 1e-12
+    ld_same, _ = api.gp_slq_logdet(X, prob.kind, prob.theta,
+                                   api.solve_opts(nprobe=10, nlanczos=30, seed=1234, prec=3,
+                                                  slq_prec=-1))
+    ld_tf, _ = api.gp_slq_logdet(X, prob.kind, prob.theta,
+                                 api.solve_opts(nprobe=10, nlanczos=30, seed=1234, prec=0, slq_prec=3))
+    assert rel(ld_same, ld_tf) <= 1e-12
+    assert rel(ld_tf, est["logdet"]) <= 1e-4
