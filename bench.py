@@ -399,6 +399,27 @@ def loss_grad_small(api, torch, reps: int = 3) -> dict:
             "cg_iters": info["cg_iters"]}
 
 
+def run_leg(args) -> int:
+    """One extra leg alone (the same code the full run calls), for profiling it."""
+    import torch
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import _binding as B
+    from paper_2503_02259_gb300 import api
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    if args.leg == "loss_grad":
+        out = loss_grad_small(api, torch)
+    elif args.leg == "precision_config":
+        out = precision_config(api, B, torch, dev)
+    elif args.leg == "loss_grad_mixed_vs_fp32":
+        out = loss_grad_mixed_vs_fp32(api, torch)
+    else:
+        out = serving(torch, count=args.serving_requests)
+    print(json.dumps({"leg": args.leg, **out}), flush=True)
+    return 0
+
+
 def main() -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -410,9 +431,14 @@ def main() -> int:
     ap.add_argument("--prec", default="fp32", choices=list(PRECS), help="arithmetic of the product")
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests replayed by the serving leg (the full stream is 512)")
+    ap.add_argument("--leg", default=None,
+                    choices=["loss_grad", "precision_config", "loss_grad_mixed_vs_fp32", "serving"],
+                    help="run one extra leg alone on cuda:0 and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.leg is not None:
+        return run_leg(args)
 
     import torch
     from paper_2503_02259_gb300 import build

@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     const float* xs = sX + stage * kBN * DP;
     const float* vs = sV + stage * kBN * w_pad + g * TW;
-#pragma unroll 2
+#pragma unroll 8
     for (int jj = 0; jj < kBN; jj += 4) {
       float2 q01, q23;
       sqdist_quad<DT>(xi2, xs + (jj >> 5) * (32 * DP), jj & 31, q01, q23);
