@@ -146,27 +146,61 @@ __global__ void probes_kernel(int64_t n, int p, uint64_t seed, float* Z, int64_t
 
 // ----------------------------------------------------------------- epilogue --
 
+// Fixed-order compensated sum of the split partials of four adjacent columns:
+// Knuth's two-sum carries each addition's rounding error in c, so the result is
+// the exactly rounded sum up to a few units of FP32 rounding for any split count.
+__device__ __forceinline__ float4 split_sum4(const float* part, int split, int64_t plane,
+                                             int64_t idx) {
+  float4 s = *reinterpret_cast<const float4*>(part + idx);
+  float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+  auto two_sum = [](float& sv, float& cv, float p) {
+    const float t = sv + p;
+    const float bp = t - sv;
+    cv += (sv - (t - bp)) + (p - bp);
+    sv = t;
+  };
+  for (int k = 1; k < split; ++k) {
+    const float4 p = *reinterpret_cast<const float4*>(part + k * plane + idx);
+    two_sum(s.x, c.x, p.x);
+    two_sum(s.y, c.y, p.y);
+    two_sum(s.z, c.z, p.z);
+    two_sum(s.w, c.w, p.w);
+  }
+  return make_float4(s.x + c.x, s.y + c.y, s.z + c.z, s.w + c.w);
+}
+
+// One thread per (row, four columns); w_pad is a multiple of 4, so the partial
+// planes and V are read as float4 rows.
 __global__ void epilogue_kernel(EpiArgs a) {
   const bool bad = (a.err != nullptr) && (*a.err != 0);
-  const int64_t total = a.n * a.w;
+  const int nq = a.w_pad >> 2;
+  const int64_t total = a.n * nq;
   const float qnan = __int_as_float(0x7fc00000);
+  const int64_t plane = a.nr_pad * a.w_pad;
+  const float cK = static_cast<float>(a.cK), cV = static_cast<float>(a.cV);
+  const float cF = static_cast<float>(a.cF), cL = static_cast<float>(a.cL);
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-    const int64_t i = e / a.w;
-    const int c = static_cast<int>(e - i * a.w);
-    const int64_t idx = i * a.w_pad + c;
-    const int64_t plane = a.nr_pad * a.w_pad;
-    double sk = 0.0, sd = 0.0;
-    for (int s = 0; s < a.split; ++s) sk += a.part_k[s * plane + idx];
-    if (a.dyl != nullptr)
-      for (int s = 0; s < a.split; ++s) sd += a.part_d[s * plane + idx];
-    if (a.y != nullptr) {
-      double yv = a.cK * sk;
-      if (a.cV != 0.0) yv += a.cV * static_cast<double>(a.v[idx]);
-      a.y[i * a.ldy + c] = bad ? qnan : static_cast<float>(yv);
+    const int64_t i = e / nq;
+    const int c0 = static_cast<int>(e - i * nq) * 4;
+    if (c0 >= a.w) continue;
+    const int64_t idx = i * a.w_pad + c0;
+    const float4 sk = split_sum4(a.part_k, a.split, plane, idx);
+    float4 sd = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.dyl != nullptr) sd = split_sum4(a.part_d, a.split, plane, idx);
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (a.y != nullptr && a.cV != 0.0) v = *reinterpret_cast<const float4*>(a.v + idx);
+    const float skv[4] = {sk.x, sk.y, sk.z, sk.w};
+    const float sdv[4] = {sd.x, sd.y, sd.z, sd.w};
+    const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int c = c0 + u;
+      if (c >= a.w) break;
+      if (a.y != nullptr) a.y[i * a.ldy + c] = bad ? qnan : fmaf(cK, skv[u], cV * vv[u]);
+      if (a.dyf != nullptr) a.dyf[i * a.ldf + c] = bad ? qnan : cF * skv[u];
+      if (a.dyl != nullptr) a.dyl[i * a.ldl + c] = bad ? qnan : cL * sdv[u];
     }
-    if (a.dyf != nullptr) a.dyf[i * a.ldf + c] = bad ? qnan : static_cast<float>(a.cF * sk);
-    if (a.dyl != nullptr) a.dyl[i * a.ldl + c] = bad ? qnan : static_cast<float>(a.cL * sd);
   }
 }
 
@@ -780,7 +814,7 @@ cudaError_t launch_probes(int64_t n, int p, uint64_t seed, float* Z, int64_t ldz
 }
 
 cudaError_t launch_epilogue(const EpiArgs& a, cudaStream_t st) {
-  epilogue_kernel<<<elt_blocks(a.n * a.w), kEltThreads, 0, st>>>(a);
+  epilogue_kernel<<<elt_blocks(a.n * (a.w_pad / 4)), kEltThreads, 0, st>>>(a);
   count_launch();
   return cudaGetLastError();
 }
