@@ -6,7 +6,9 @@ of §Gaussian Processes).  Here the forward runs the block CG on [y | Z] and SLQ
 (gp_nll_forward) and keeps only W = Kh^-1 [y | Z]; the backward regenerates the
 same probes Z from the seed instead of storing them and runs one fused
 derivative product (gp_nll_backward).  With ``recompute=True`` the forward
-keeps nothing n-sized and the backward re-solves for W first.
+keeps nothing n-sized and the backward re-solves for W first.  ``prec`` and
+``slq_prec`` choose the arithmetic of the CG and of the Lanczos products (the
+derivative product of the backward is FP32).
 """
 from __future__ import annotations
 
@@ -18,12 +20,13 @@ from ._binding import PREC_FP32
 
 class GPNegLogLik(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute):
+    def forward(ctx, theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute,
+                prec, slq_prec):
         th = [float(v) for v in theta.detach().cpu().tolist()]
         opts = api.solve_opts(nprobe=nprobe, nlanczos=nlanczos, cg_rtol=cg_rtol, seed=seed,
-                              cg_maxit=cg_maxit, prec=PREC_FP32)
+                              cg_maxit=cg_maxit, prec=prec, slq_prec=slq_prec)
         loss, W, info = api.gp_nll_forward(X, y, kernel, th, opts)
-        ctx.cfg = (kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute)
+        ctx.cfg = (kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec, slq_prec)
         ctx.info = info
         ctx.theta_dtype = theta.dtype
         ctx.theta_device = theta.device
@@ -33,19 +36,21 @@ class GPNegLogLik(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         X, y, W = ctx.saved_tensors
-        kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute = ctx.cfg
+        kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec, slq_prec = ctx.cfg
         opts = api.solve_opts(nprobe=nprobe, nlanczos=nlanczos, cg_rtol=cg_rtol, seed=seed,
-                              cg_maxit=cg_maxit, prec=PREC_FP32)
+                              cg_maxit=cg_maxit, prec=prec, slq_prec=slq_prec)
         if W is None:
             _, W, _ = api.gp_nll_forward(X, y, kernel, th, opts)
         grad, _ = api.gp_nll_backward(X, W, kernel, th, opts)
         g = torch.tensor(grad, dtype=ctx.theta_dtype, device=ctx.theta_device) * grad_out.to(
             device=ctx.theta_device, dtype=ctx.theta_dtype)
-        return (g, None, None, None, None, None, None, None, None, None)
+        return (g, None, None, None, None, None, None, None, None, None, None, None)
 
 
 def neg_log_likelihood(theta: torch.Tensor, X: torch.Tensor, y: torch.Tensor, kernel: int,
                        nprobe: int = 16, nlanczos: int = 30, cg_rtol: float = 1e-6, seed: int = 0,
-                       cg_maxit: int = 0, recompute: bool = False) -> torch.Tensor:
+                       cg_maxit: int = 0, recompute: bool = False, prec: int = PREC_FP32,
+                       slq_prec: int = PREC_FP32) -> torch.Tensor:
     """L(theta) with theta = (s, f, l) a 3-element tensor; differentiable in theta."""
-    return GPNegLogLik.apply(theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute)
+    return GPNegLogLik.apply(theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute,
+                             prec, slq_prec)

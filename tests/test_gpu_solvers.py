@@ -121,7 +121,9 @@ def test_forward_backward_split_equals_fused(api, small):
     np.testing.assert_allclose(grad2, grad, rtol=1e-12, atol=0)
 
 
-def test_autograd_function(api, small):
+# (CG arithmetic, SLQ arithmetic) of the forward: FP32, and the mixed pair.
+@pytest.mark.parametrize("prec,slq", [(0, 0), (4, 3)])
+def test_autograd_function(api, small, prec, slq):
     import torch
     from paper_2503_02259_gb300.autograd import neg_log_likelihood
     prob, est, _ = small
@@ -129,7 +131,7 @@ def test_autograd_function(api, small):
     for recompute in (False, True):
         theta = torch.tensor(prob.theta, dtype=torch.float64, requires_grad=True)
         L = neg_log_likelihood(theta, X, y, prob.kind, nprobe=10, nlanczos=30, cg_rtol=1e-8,
-                               seed=1234, recompute=recompute)
+                               seed=1234, recompute=recompute, prec=prec, slq_prec=slq)
         (2.0 * L).backward()
         g = theta.grad.numpy() / 2.0
         gfloor = 1e-3 * np.linalg.norm(est["grad"])
