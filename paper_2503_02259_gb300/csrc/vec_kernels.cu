@@ -83,6 +83,40 @@ __device__ __forceinline__ double final_sum(const double* red, int q, int c, int
   return s;
 }
 
+// Called by every thread of the last block: the sums over the grid's blocks of
+// red[q][b][c] for q < nq (<= 3), c < w_pad, into shared memory (index
+// q * w_pad + c).  With np = nq * w_pad pairs, lane l of the blockDim / np lanes
+// of a pair adds blocks l, l + lanes, ...; the lanes are then added in lane
+// order, so the result depends only on the launch shape, and the serial chain
+// per thread is about gridDim / lanes loads instead of gridDim.
+__device__ const double* final_sums(const double* red, int nq, int w_pad) {
+  __shared__ double tot[3 * kMaxW];
+  __shared__ double part[kRedThreads];
+  const int np = nq * w_pad;
+  const int t = threadIdx.x;
+  const int nb = static_cast<int>(gridDim.x);
+  const int nl = static_cast<int>(blockDim.x) / np;
+  if (nl >= 1) {
+    const int pr = t % np, l = t / np;
+    double s = 0.0;
+    if (l < nl) {
+      const int q = pr / w_pad, c = pr - q * w_pad;
+      for (int b = l; b < nb; b += nl) s += red[(static_cast<int64_t>(q) * nb + b) * w_pad + c];
+    }
+    part[t] = s;
+    __syncthreads();
+    if (t < np) {
+      double a = 0.0;
+      for (int k = 0; k < nl; ++k) a += part[k * np + t];
+      tot[t] = a;
+    }
+  } else {
+    for (int pr = t; pr < np; pr += blockDim.x) tot[pr] = final_sum(red, pr / w_pad, pr % w_pad, w_pad);
+  }
+  __syncthreads();
+  return tot;
+}
+
 // ------------------------------------------------------------------ staging --
 
 // Writes the staged layout of pt_index in order: element e is coordinate
@@ -225,13 +259,14 @@ __global__ void cg_init_kernel(CgState* S, const float* B, float* X, float* R, f
   }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   if (threadIdx.x < kMaxW) {
     const int c = threadIdx.x;
     double bn2 = 0.0;
-    if (c < w_pad) bn2 = final_sum(red, 0, c, w_pad);
+    if (c < w_pad) bn2 = tot[c];
     const bool act = (c < w) && (bn2 > 0.0);
     S->bn2[c] = bn2;
     S->rr[c] = bn2;
@@ -280,9 +315,10 @@ __global__ void cg_epi_alpha_kernel(CgState* S, const float* part_k, int split, 
   }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
-    const double pap = final_sum(red, 0, c, w_pad);
+    const double pap = tot[c];
     double al = 0.0;
     if (S->active[c]) {
       if (!(pap > 0.0) || !isfinite(pap)) {
@@ -320,13 +356,14 @@ __global__ void cg_update_kernel(CgState* S, float* X, float* R, const float* P,
   }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
     if (S->active[c]) {
-      const double rr_new = final_sum(red, 0, c, w_pad);
+      const double rr_new = tot[c];
       const double be = rr_new / S->rr[c];
       const int it = S->iters[c];
       if (it < kMaxK) S->bhist[it][c] = be;
@@ -377,12 +414,13 @@ __global__ void lz_init_kernel(CgState* S, const float* B, int64_t n_pad, int w_
     }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   if (threadIdx.x < kMaxW) {
     const int c = threadIdx.x;
-    const double bn2 = c < w_pad ? final_sum(red, 0, c, w_pad) : 0.0;
+    const double bn2 = c < w_pad ? tot[c] : 0.0;
     const bool act = c >= col0 && c < col0 + p && bn2 > 0.0;
     S->bn2[c] = bn2;
     S->active[c] = act ? 1 : 0;
@@ -443,9 +481,10 @@ __global__ void lz_epi_alpha_kernel(CgState* S, const float* part_k, int split, 
   }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
-    const double al = final_sum(red, 0, c, w_pad);
+    const double al = tot[c];
     if (S->active[c]) S->ahist[j][c] = al;
   }
 }
@@ -529,13 +568,14 @@ __global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_
     }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
   __shared__ int cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
     if (S->active[c]) {
-      const double be = sqrt(final_sum(red, 0, c, w_pad));
+      const double be = sqrt(tot[c]);
       const double bprev = j > 0 ? S->bhist[j - 1][c] : 0.0;
       const double tn = fmax(S->tnorm[c], fabs(S->ahist[j][c]) + be + bprev);
       S->tnorm[c] = tn;
@@ -610,9 +650,10 @@ __global__ void grad_dots_kernel(CgState* S, const float* part_k, const float* p
   }
   block_store<3>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 3, w_pad);
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
-    for (int q = 0; q < 3; ++q) S->dots[q][c] = final_sum(red, q, c, w_pad);
+    for (int q = 0; q < 3; ++q) S->dots[q][c] = tot[q * w_pad + c];
   }
 }
 
@@ -630,7 +671,8 @@ __global__ void yalpha_kernel(CgState* S, const float* B, const float* X, int64_
   L.live = true;
   block_store<1>(acc, L, 1, red);
   if (!last_block(&S->ticket)) return;
-  if (threadIdx.x == 0) S->yalpha = final_sum(red, 0, 0, 1);
+  const double* tot = final_sums(red, 1, 1);
+  if (threadIdx.x == 0) S->yalpha = tot[0];
 }
 
 // out: [0] logdet [1] logdet_stderr [2] loss [3..5] grad [6..8] quad [9..11] trace
@@ -744,10 +786,11 @@ __global__ void refine_norms_kernel(CgState* S, const double* r64, const float* 
   }
   block_store<2>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 2, w_pad);
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
-    const double rr = final_sum(red, 0, c, w_pad);
-    const double bb = final_sum(red, 1, c, w_pad);
+    const double rr = tot[c];
+    const double bb = tot[w_pad + c];
     S->rr[c] = rr;
     S->bn2[c] = bb;
     S->relres[c] = bb > 0.0 ? sqrt(rr / bb) : 0.0;
