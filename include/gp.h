@@ -277,6 +277,8 @@ gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, con
 /* Posterior mean mu = f^2 K(Xstar, X) alpha at m test points (noise-free test
  * outputs, §Gaussian Processes; the prediction call of §Design and
  * Implementation).  alpha: device n; Xstar: device m x d; mu: device m.
+ * prec must be a valid gp_precision, but the product always runs in FP32 on
+ * the CUDA cores: one column (w = 1) is far too narrow for a tensor-core tile.
  * Workspace: gp_workspace_bytes(GP_OP_PREDICT, prob, m, NULL).  Asynchronous. */
 gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const float* Xstar,
                           int64_t m, float* mu, int32_t prec, void* ws, size_t ws_bytes,
