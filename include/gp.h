@@ -34,8 +34,9 @@
  *    1 <= w <= GP_MAX_COLS, s > 0, f > 0, l > 0, non-NULL device pointers,
  *    kernel in {GAUSSIAN, MATERN32}.
  *  - Statelessness (§Design and Implementation: the interfaces are stateless):
- *    no call keeps state between calls except the thread-local error string
- *    and per-device launch-configuration caches.
+ *    no call keeps state between calls except the thread-local error string,
+ *    per-device launch-configuration caches, and one private stream per host
+ *    thread and device on which the solvers capture their CG-iteration graphs.
  */
 #ifndef GP_H
 #define GP_H
