@@ -22,11 +22,13 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", 
          "-I", INCLUDE, "-I", CSRC]
 
 # (object name, source, extra flags)
-UNITS = [
-    ("kmv_simt_k0_g0", "kmv_simt_inst.cu", ["-DGP_KIND=0", "-DGP_GRAD=0"]),
-    ("kmv_simt_k0_g1", "kmv_simt_inst.cu", ["-DGP_KIND=0", "-DGP_GRAD=1"]),
-    ("kmv_simt_k1_g0", "kmv_simt_inst.cu", ["-DGP_KIND=1", "-DGP_GRAD=0"]),
-    ("kmv_simt_k1_g1", "kmv_simt_inst.cu", ["-DGP_KIND=1", "-DGP_GRAD=1"]),
+# The SIMT product is instantiated per (kernel family, grad, dimension template)
+# in 24 units, so that a multi-core host compiles them in parallel.
+SIMT_UNITS = [(f"kmv_simt_k{k}_g{g}_d{dt}", "kmv_simt_inst.cu",
+               [f"-DGP_KIND={k}", f"-DGP_GRAD={g}", f"-DGP_DT={dt}"])
+              for k in (0, 1) for g in (0, 1) for dt in (1, 2, 3, 4, 8, 16)]
+
+UNITS = SIMT_UNITS + [
     ("kmv_tc", "kmv_tc.cu", []),
     ("kmv_tc_m1", "kmv_tc_inst.cu", ["-DGP_TC_MODE=1"]),
     ("kmv_tc_m2", "kmv_tc_inst.cu", ["-DGP_TC_MODE=2"]),

@@ -20,15 +20,56 @@
 
 namespace gp {
 
-// Per-(kernel, grad) instantiation units (kmv_simt_inst.cu).
-cudaError_t launch_simt_k0_g0(const SimtPlan&, const SimtArgs&, cudaStream_t);
-cudaError_t launch_simt_k0_g1(const SimtPlan&, const SimtArgs&, cudaStream_t);
-cudaError_t launch_simt_k1_g0(const SimtPlan&, const SimtArgs&, cudaStream_t);
-cudaError_t launch_simt_k1_g1(const SimtPlan&, const SimtArgs&, cudaStream_t);
-int occupancy_simt_k0_g0(int, int, int);
-int occupancy_simt_k0_g1(int, int, int);
-int occupancy_simt_k1_g0(int, int, int);
-int occupancy_simt_k1_g1(int, int, int);
+// Per-(kernel, grad, dimension) instantiation units (kmv_simt_inst.cu).
+#define GP_SIMT_DECL(K, G, D)                                                                \
+  cudaError_t launch_simt_k##K##_g##G##_d##D(const SimtPlan&, const SimtArgs&, cudaStream_t); \
+  int occupancy_simt_k##K##_g##G##_d##D(int, int);
+#define GP_SIMT_DECL_DT(K, G) \
+  GP_SIMT_DECL(K, G, 1)       \
+  GP_SIMT_DECL(K, G, 2)       \
+  GP_SIMT_DECL(K, G, 3)       \
+  GP_SIMT_DECL(K, G, 4)       \
+  GP_SIMT_DECL(K, G, 8)       \
+  GP_SIMT_DECL(K, G, 16)
+GP_SIMT_DECL_DT(0, 0)
+GP_SIMT_DECL_DT(0, 1)
+GP_SIMT_DECL_DT(1, 0)
+GP_SIMT_DECL_DT(1, 1)
+
+#define GP_SIMT_DT_SWITCH(K, G, CALL) \
+  switch (dt) {                       \
+    case 1: return CALL(K, G, 1);     \
+    case 2: return CALL(K, G, 2);     \
+    case 3: return CALL(K, G, 3);     \
+    case 4: return CALL(K, G, 4);     \
+    case 8: return CALL(K, G, 8);     \
+    case 16: return CALL(K, G, 16);   \
+    default: break;                   \
+  }
+
+static cudaError_t launch_simt_dt(int kernel, bool grad, const SimtPlan& p, const SimtArgs& a,
+                                  cudaStream_t st) {
+  const int dt = p.dt;
+#define GP_L(K, G, D) launch_simt_k##K##_g##G##_d##D(p, a, st)
+  if (kernel == 0) {
+    if (grad) { GP_SIMT_DT_SWITCH(0, 1, GP_L) } else { GP_SIMT_DT_SWITCH(0, 0, GP_L) }
+  } else {
+    if (grad) { GP_SIMT_DT_SWITCH(1, 1, GP_L) } else { GP_SIMT_DT_SWITCH(1, 0, GP_L) }
+  }
+#undef GP_L
+  return cudaErrorInvalidValue;
+}
+
+static int occupancy_simt_dt(int kernel, bool grad, int dt, int tw, int w_pad) {
+#define GP_O(K, G, D) occupancy_simt_k##K##_g##G##_d##D(tw, w_pad)
+  if (kernel == 0) {
+    if (grad) { GP_SIMT_DT_SWITCH(0, 1, GP_O) } else { GP_SIMT_DT_SWITCH(0, 0, GP_O) }
+  } else {
+    if (grad) { GP_SIMT_DT_SWITCH(1, 1, GP_O) } else { GP_SIMT_DT_SWITCH(1, 0, GP_O) }
+  }
+#undef GP_O
+  return 1;
+}
 
 namespace {
 thread_local std::string t_err;
@@ -128,10 +169,7 @@ int simt_occupancy(int kernel, bool grad, int dt, int tw, int w_pad, int) {
     if (it != g_occ.end()) return it->second;
   }
   int occ = 1;
-  if (kernel == 0)
-    occ = grad ? occupancy_simt_k0_g1(dt, tw, w_pad) : occupancy_simt_k0_g0(dt, tw, w_pad);
-  else
-    occ = grad ? occupancy_simt_k1_g1(dt, tw, w_pad) : occupancy_simt_k1_g0(dt, tw, w_pad);
+  occ = occupancy_simt_dt(kernel, grad, dt, tw, w_pad);
   std::lock_guard<std::mutex> lk(g_mu);
   g_occ[key] = occ;
   return occ;
@@ -143,7 +181,9 @@ SimtPlan plan_simt(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel) 
   SimtPlan p;
   p.dt = dim_template(d);
   p.dp = dim_padded(p.dt);
-  p.ng = w <= 32 ? 1 : (w <= 64 ? 2 : 4);
+  // One column group up to 40 columns (a 1 + 32-probe block stays in one group,
+  // so each entry is evaluated once), else two or four groups of <= 32.
+  p.ng = w <= 40 ? 1 : (w <= 64 ? 2 : 4);
   const int per = (w + p.ng - 1) / p.ng;
   p.tw = static_cast<int>(round_up(per, 4));
   p.w_pad = p.ng * p.tw;
@@ -185,8 +225,7 @@ SimtPlan plan_for(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel, i
 
 cudaError_t launch_simt(const SimtPlan& p, int kernel, bool grad, const SimtArgs& a,
                         cudaStream_t st) {
-  if (kernel == 0) return grad ? launch_simt_k0_g1(p, a, st) : launch_simt_k0_g0(p, a, st);
-  return grad ? launch_simt_k1_g1(p, a, st) : launch_simt_k1_g0(p, a, st);
+  return launch_simt_dt(kernel, grad, p, a, st);
 }
 
 // ---------------------------------------------------------------------------

@@ -86,6 +86,10 @@ __global__ void __launch_bounds__(kThreads)
     kmv_simt_kernel(SimtArgs a, int w_pad, int ng, int64_t nr_pad, int jtiles, int jt_per_split) {
   constexpr int DP = DimTraits<DT>::DP;
   constexpr int TW2 = TW / 2;
+  // Quads of entries per loop iteration: eight let the scheduler overlap one
+  // quad's evaluation with another's contraction; fewer for the long distance
+  // loops of d > 4, which already give that overlap (and build faster).
+  constexpr int kQuadUnroll = DT >= 16 ? 2 : (DT >= 8 ? 4 : 8);
   static_assert(TW % 4 == 0, "TW must be a multiple of 4");
 
   if (a.active != nullptr && *a.active == 0) return;
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(kThreads)
     }
     const float* xs = sX + stage * kBN * DP;
     const float* vs = sV + stage * kBN * w_pad + g * TW;
-#pragma unroll 8
+#pragma unroll kQuadUnroll
     for (int jj = 0; jj < kBN; jj += 4) {
       float2 q01, q23;
       sqdist_quad<DT>(xi2, xs + (jj >> 5) * (32 * DP), jj & 31, q01, q23);

@@ -1,21 +1,19 @@
-// Instantiations of the SIMT product for one (kernel family, grad) pair.
-// Compiled once per pair with -DGP_KIND=<0|1> -DGP_GRAD=<0|1> so that the
-// instantiations build in parallel translation units.
+// Instantiations of the SIMT product for one (kernel family, grad, dimension)
+// triple.  Compiled once per triple with -DGP_KIND=<0|1> -DGP_GRAD=<0|1>
+// -DGP_DT=<1|2|3|4|8|16> so that the instantiations build in parallel
+// translation units.
 #include <atomic>
 
 #include "kmv_simt.cuh"
 
-#ifndef GP_KIND
-#error "GP_KIND must be defined"
-#endif
-#ifndef GP_GRAD
-#error "GP_GRAD must be defined"
+#if !defined(GP_KIND) || !defined(GP_GRAD) || !defined(GP_DT)
+#error "GP_KIND, GP_GRAD and GP_DT must be defined"
 #endif
 
-#define GP_CAT4(a, b, c, d) a##b##c##d
-#define GP_FN(prefix, k, g) GP_CAT4(prefix, k, _g, g)
-#define GP_LAUNCH GP_FN(launch_simt_k, GP_KIND, GP_GRAD)
-#define GP_OCC GP_FN(occupancy_simt_k, GP_KIND, GP_GRAD)
+#define GP_CAT6(a, b, c, d, e, f) a##b##c##d##e##f
+#define GP_FN(prefix, k, g, dt) GP_CAT6(prefix, k, _g, g, _d, dt)
+#define GP_LAUNCH GP_FN(launch_simt_k, GP_KIND, GP_GRAD, GP_DT)
+#define GP_OCC GP_FN(occupancy_simt_k, GP_KIND, GP_GRAD, GP_DT)
 
 namespace gp {
 
@@ -76,33 +74,24 @@ int occ_one(int w_pad) {
     case 24: return CALL(DT, 24);              \
     case 28: return CALL(DT, 28);              \
     case 32: return CALL(DT, 32);              \
+    case 36: return CALL(DT, 36);              \
+    case 40: return CALL(DT, 40);              \
     default: break;                            \
-  }
-
-#define GP_DT_SWITCH(CALL)                      \
-  switch (dt) {                                 \
-    case 1: GP_TW_SWITCH(1, CALL) break;        \
-    case 2: GP_TW_SWITCH(2, CALL) break;        \
-    case 3: GP_TW_SWITCH(3, CALL) break;        \
-    case 4: GP_TW_SWITCH(4, CALL) break;        \
-    case 8: GP_TW_SWITCH(8, CALL) break;        \
-    case 16: GP_TW_SWITCH(16, CALL) break;      \
-    default: break;                             \
   }
 
 }  // namespace
 
 cudaError_t GP_LAUNCH(const SimtPlan& p, const SimtArgs& a, cudaStream_t st) {
-  const int dt = p.dt, tw = p.tw;
+  const int tw = p.tw;
 #define GP_CALL_LAUNCH(D, W) launch_one<D, W>(p, a, st)
-  GP_DT_SWITCH(GP_CALL_LAUNCH)
+  GP_TW_SWITCH(GP_DT, GP_CALL_LAUNCH)
 #undef GP_CALL_LAUNCH
   return cudaErrorInvalidValue;
 }
 
-int GP_OCC(int dt, int tw, int w_pad) {
+int GP_OCC(int tw, int w_pad) {
 #define GP_CALL_OCC(D, W) occ_one<D, W>(w_pad)
-  GP_DT_SWITCH(GP_CALL_OCC)
+  GP_TW_SWITCH(GP_DT, GP_CALL_OCC)
 #undef GP_CALL_OCC
   return 1;
 }
