@@ -514,23 +514,35 @@ __global__ void lz_dots_kernel(CgState* S, const float* W, const float* Q, int64
   block_rows(n_pad, r0, r1);
   const int64_t plane = n_pad * w_pad;
   __shared__ double sm[kRedThreads];
-  for (int i = 0; i < nq; ++i) {
-    double acc = 0.0;
+  // Eight basis vectors per pass: their loads are independent, so they are in
+  // flight together instead of one round trip per basis vector.
+  constexpr int kChunk = 8;
+  for (int i0 = 0; i0 < nq; i0 += kChunk) {
+    double acc[kChunk];
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) acc[k] = 0.0;
     if (L.live) {
-      const float* Qi = Q + static_cast<int64_t>(i) * plane;
       for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
         const int64_t idx = r * w_pad + L.c;
-        acc += static_cast<double>(Qi[idx]) * static_cast<double>(W[idx]);
+        const double wv = static_cast<double>(W[idx]);
+#pragma unroll
+        for (int k = 0; k < kChunk; ++k)
+          if (i0 + k < nq)
+            acc[k] += static_cast<double>(Q[static_cast<int64_t>(i0 + k) * plane + idx]) * wv;
       }
     }
-    sm[threadIdx.x] = L.live ? acc : 0.0;
-    __syncthreads();
-    if (threadIdx.x < w_pad) {
-      double s = 0.0;
-      for (int q = 0; q < L.nrl; ++q) s += sm[q * w_pad + threadIdx.x];
-      red[(static_cast<int64_t>(i) * gridDim.x + blockIdx.x) * w_pad + threadIdx.x] = s;
+#pragma unroll
+    for (int k = 0; k < kChunk; ++k) {
+      if (i0 + k >= nq) break;
+      sm[threadIdx.x] = L.live ? acc[k] : 0.0;
+      __syncthreads();
+      if (threadIdx.x < w_pad) {
+        double sum = 0.0;
+        for (int q = 0; q < L.nrl; ++q) sum += sm[q * w_pad + threadIdx.x];
+        red[(static_cast<int64_t>(i0 + k) * gridDim.x + blockIdx.x) * w_pad + threadIdx.x] = sum;
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   if (!last_block(&S->ticket)) return;
   for (int t = threadIdx.x; t < nq * w_pad; t += blockDim.x) {
