@@ -48,6 +48,13 @@ def _peaks():
         return {}
 
 
+def _refs():
+    """FP64 reference values written by tests/golden/make_bench_refs.py (which
+    calls only the oracle); the accuracy columns of the extra legs compare
+    against them."""
+    return np.load(os.path.join(ROOT, "tests", "golden", "bench_refs.npz"))
+
+
 def _traffic():
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
@@ -185,10 +192,10 @@ PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
 
 def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
     """Each tensor-core mode on the bench workload: product-kernel throughput and the
-    norm-wise error of K.V and dK/dl.V against the FP64 oracle on 100 sampled rows."""
-    import oracle as O
-    rows = np.sort(np.random.default_rng(11).choice(prob.n, 100, replace=False))
-    rY, _, rL = O.kmv_rows(prob.X, V.cpu().numpy(), prob.kind, prob.theta, rows=rows, block=50)
+    norm-wise error of K.V and dK/dl.V against FP64 oracle values on 100 sampled rows
+    (tests/golden/bench_refs.npz)."""
+    refs = _refs()
+    rows, rY, rL = refs["matvec_rows"], refs["matvec_Y"], refs["matvec_L"]
     L = B.lib()
     out = {}
     for name, prec in PRECS.items():
@@ -226,22 +233,18 @@ def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
 def precision_config(api, B, torch, dev) -> dict:
     """The precision problem (n = 1e6, d = 2 uniform, Gaussian f = 1, l = 0.05, s = 0.01,
     V of width 64): one K-hat.V product per arithmetic, timed with the library's
-    product-kernel events, and its norm-wise error against the FP64 oracle on 1000
-    sampled rows (the same rows for every arithmetic)."""
-    import oracle as O
+    product-kernel events, and its norm-wise error against FP64 oracle values on 200
+    sampled rows (tests/golden/bench_refs.npz; the same rows for every arithmetic)."""
     from paper_2503_02259_gb300 import inputs
     prob = inputs.precision_problem(seed=0)
     Vh = inputs.multivector(prob.y, 64, seed=0)
-    rows = np.sort(np.random.default_rng(3).choice(prob.n, 1000, replace=False))
-    t0 = time.perf_counter()
-    rY, _, _ = O.kmv_rows(prob.X, Vh, prob.kind, prob.theta, rows=rows, block=20)
-    t_oracle = time.perf_counter() - t0
+    refs = _refs()
+    rows, rY = refs["precision_rows"], refs["precision_Y"]
     X = torch.from_numpy(prob.X).to(dev)
     V = torch.from_numpy(Vh).to(dev)
     L = B.lib()
     out = {"workload": "n=1000000 d=2 uniform[0,1]^2, Gaussian f=1 l=0.05 s=0.01, V=[y | 63 "
-                       "Rademacher] w=64, one Kh.V product; error on 1000 sampled rows vs FP64",
-           "oracle_rows_s": t_oracle}
+                       "Rademacher] w=64, one Kh.V product; error on 200 sampled rows vs FP64"}
     for name, prec in PRECS.items():
         pr, _ = api.problem(X, prob.kind, prob.theta)
         ws = api.workspace(B.OP_MATMUL, pr, 64, api.solve_opts(prec=prec), dev)
@@ -260,7 +263,7 @@ def precision_config(api, B, torch, dev) -> dict:
         yh = Y.cpu().numpy()[rows].astype(np.float64)
         err = float(np.max(np.linalg.norm(yh - rY, axis=0) / np.linalg.norm(rY, axis=0)))
         out[name] = {"kernel_ms": ms.value, "value": prob.n * prob.n * 64 / (ms.value * 1e-3),
-                     "unit": UNIT, "relerr_Y_1000_rows": err}
+                     "unit": UNIT, "relerr_Y_200_rows": err}
         del ws, Y
     return out
 
@@ -270,14 +273,14 @@ def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps, CG to 1e-6): accuracy of each
     arithmetic (CG products / SLQ products) against the FP64 oracle's same-probe estimator
     on the n = 4000 subsample, and wall time per Theta at the full n."""
-    import oracle as O
     from paper_2503_02259_gb300 import inputs
     same = -1
     arms = {"fp32": (0, 0), "tf32x3": (3, same), "bf16x3": (4, same),
             "bf16x3_slq_tf32x3": (4, 3)}
     timed = ("fp32", "tf32x3", "bf16x3_slq_tf32x3")
     sub = inputs.diff_problem(seed=0, n=4000)
-    est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
+    refs = _refs()
+    est = {"loss": float(refs["diff_loss"]), "grad": refs["diff_grad"]}
     gref = np.asarray(est["grad"])
     floor = 1e-3 * np.linalg.norm(gref)
     out = {"workload": "differentiation problem, 32 probes x 40 Lanczos steps, CG rtol 1e-6; "

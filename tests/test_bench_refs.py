@@ -1,0 +1,40 @@
+"""The FP64 reference values bench.py compares against (tests/golden/bench_refs.npz,
+written by tests/golden/make_bench_refs.py) are the oracle's: recompute a few of
+them here and compare."""
+import os
+
+import numpy as np
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+REFS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "bench_refs.npz")
+
+
+def test_matvec_rows_are_the_oracles():
+    refs = np.load(REFS)
+    prob = inputs.matvec_problem(seed=0)
+    V = inputs.multivector(prob.y, 32, seed=0)
+    rows = np.sort(np.random.default_rng(11).choice(prob.n, 100, replace=False))
+    assert np.array_equal(rows, refs["matvec_rows"])
+    Y, _, Lr = O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows[:3], block=3)
+    np.testing.assert_allclose(Y, refs["matvec_Y"][:3], rtol=1e-12, atol=0)
+    np.testing.assert_allclose(Lr, refs["matvec_L"][:3], rtol=1e-12, atol=0)
+
+
+def test_precision_rows_are_the_oracles():
+    refs = np.load(REFS)
+    prob = inputs.precision_problem(seed=0)
+    V = inputs.multivector(prob.y, 64, seed=0)
+    rows = np.sort(np.random.default_rng(3).choice(prob.n, 200, replace=False))
+    assert np.array_equal(rows, refs["precision_rows"])
+    Y, _, _ = O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows[-2:], block=2)
+    np.testing.assert_allclose(Y, refs["precision_Y"][-2:], rtol=1e-12, atol=0)
+
+
+def test_differentiation_subsample_estimate_is_the_oracles():
+    refs = np.load(REFS)
+    sub = inputs.diff_problem(seed=0, n=4000)
+    est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
+    assert abs(est["loss"] - float(refs["diff_loss"])) <= 1e-9 * abs(est["loss"])
+    np.testing.assert_allclose(est["grad"], refs["diff_grad"], rtol=1e-9, atol=0)
