@@ -268,6 +268,40 @@ def precision_config(api, B, torch, dev) -> dict:
     return out
 
 
+def refinement(api, torch, n: int = 20_000) -> dict:
+    """Time to a true residual of 1e-6 on the precision problem's kernel at n = 2e4
+    (d = 2, Gaussian f = 1, l = 0.05, s = 0.01; kappa ~ 3e4): plain FP32 CG against
+    mixed-precision iterative refinement (split-BF16 inner CG to 1e-2, FP64 outer
+    residual).  True residuals are the library's FP64 gp_true_residual."""
+    from paper_2503_02259_gb300 import inputs
+    prob = inputs.precision_problem(seed=0, n=n)
+    X = torch.from_numpy(prob.X).cuda()
+    y = torch.from_numpy(prob.y).cuda()
+    out = {"workload": f"n={n} d=2 uniform, Gaussian f=1 l=0.05 s=0.01, B = y (w = 1); "
+                       "target true residual 1e-6"}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    x32, it32, rr32, _ = api.gp_pcg_solve(X, y, prob.kind, prob.theta,
+                                          api.solve_opts(cg_rtol=1e-10, cg_maxit=4000),
+                                          raise_not_converged=False)
+    torch.cuda.synchronize()
+    t32 = time.perf_counter() - t0
+    true32 = api.gp_true_residual(X, y, x32, prob.kind, prob.theta)[0]
+    out["fp32_cg"] = {"s": t32, "iterations": it32[0], "recurrence_relres": rr32[0],
+                      "true_relres": true32}
+    for name, prec in (("bf16x3", 4), ("tf32x3", 3)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, it, rr, st = api.gp_pcg_solve_refined(
+            X, y, prob.kind, prob.theta,
+            api.solve_opts(cg_rtol=1e-2, prec=prec, refine_rtol=1e-7, refine_maxit=40),
+            raise_not_converged=False)
+        torch.cuda.synchronize()
+        out[f"refined_{name}"] = {"s": time.perf_counter() - t0, "inner_iterations": it[0],
+                                  "true_relres": rr[0], "status": st}
+    return out
+
+
 def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     """L(Theta) and dL/dTheta on the differentiation problem (d = 8, 0.5 N(0,I), Gaussian
     s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps, CG to 1e-6): accuracy of each
@@ -415,6 +449,8 @@ def run_leg(args) -> int:
         out = loss_grad_small(api, torch)
     elif args.leg == "precision_config":
         out = precision_config(api, B, torch, dev)
+    elif args.leg == "refinement":
+        out = refinement(api, torch)
     elif args.leg == "loss_grad_mixed_vs_fp32":
         out = loss_grad_mixed_vs_fp32(api, torch)
     else:
@@ -435,7 +471,8 @@ def main() -> int:
     ap.add_argument("--serving-requests", type=int, default=64,
                     help="requests replayed by the serving leg (the full stream is 512)")
     ap.add_argument("--leg", default=None,
-                    choices=["loss_grad", "precision_config", "loss_grad_mixed_vs_fp32", "serving"],
+                    choices=["loss_grad", "precision_config", "refinement", "loss_grad_mixed_vs_fp32",
+                             "serving"],
                     help="run one extra leg alone on cuda:0 and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -542,6 +579,7 @@ def main() -> int:
         extras["loss_grad"] = loss_grad_small(api, torch)
         extras["precision_modes"] = precision_modes(api, B, torch, prob, X, V, dev)
         extras["precision_config"] = precision_config(api, B, torch, dev)
+        extras["refinement"] = refinement(api, torch)
         extras["loss_grad_mixed_vs_fp32"] = loss_grad_mixed_vs_fp32(api, torch)
         extras["serving"] = serving(torch, count=args.serving_requests)
 

@@ -90,7 +90,8 @@ typedef enum {
   GP_OP_PCG = 2,          /* gp_pcg_solve */
   GP_OP_SLQ = 3,          /* gp_slq_logdet */
   GP_OP_LOSS_GRAD = 4,    /* gp_loss_and_grad, gp_nll_forward, gp_nll_backward */
-  GP_OP_PREDICT = 5       /* gp_predict_mean */
+  GP_OP_PREDICT = 5,      /* gp_predict_mean */
+  GP_OP_RESIDUAL = 6      /* gp_true_residual */
 } gp_op;
 
 /* Theta = (s, f, l): noise s, scale f, length-scale l (§Gaussian Processes). */
@@ -239,6 +240,15 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
  * relres[w]: final outer relative residual (FP64).  Workspace:
  * gp_workspace_bytes(GP_OP_PCG, prob, w, opts) with opts->refine_rtol > 0.
  * The FP64 residual is O(n^2 w) FP64 work per outer step.  Synchronises. */
+/* True relative residual of a solution: relres[c] = ||B_c - Kh X_c||_2 / ||B_c||_2
+ * for each column c < w, with FP64 kernel entries and FP64 sums (the outer
+ * residual of gp_pcg_solve_refined), e.g. to check the FP32 solution of
+ * gp_pcg_solve.  B, X: device n x w float32; relres[w]: host.  Workspace:
+ * gp_workspace_bytes(GP_OP_RESIDUAL, prob, w, NULL).  O(n^2 w) FP64 work.
+ * Synchronises. */
+gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* X, int32_t w,
+                           double* relres, void* ws, size_t ws_bytes, void* stream);
+
 gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w, double* X64,
                                const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                                size_t ws_bytes, void* stream);

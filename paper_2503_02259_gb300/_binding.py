@@ -40,6 +40,7 @@ OP_PCG = 2
 OP_SLQ = 3
 OP_LOSS_GRAD = 4
 OP_PREDICT = 5
+OP_RESIDUAL = 6
 
 MAX_DIM = 16
 MAX_COLS = 128
@@ -112,6 +113,8 @@ PROTOTYPES = {
     "gp_pcg_solve_refined": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,
                                        POINTER(gp_solve_opts), POINTER(c_int32), POINTER(c_double),
                                        c_void_p, c_size_t, c_void_p]),
+    "gp_true_residual": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int32,
+                                   POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "gp_slq_logdet": (c_int32, [POINTER(gp_problem), POINTER(gp_solve_opts), POINTER(c_double),
                                 POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "gp_loss_and_grad": (c_int32, [POINTER(gp_problem), c_void_p, POINTER(gp_solve_opts),

@@ -824,6 +824,34 @@ static size_t refine_bytes(const SimtPlan& pc, int prec) {
   return refine_extra_offset(pc, prec) + 2 * plane * sizeof(double) + plane * sizeof(float) + 1024;
 }
 
+// Workspace of gp_true_residual: x (FP64), r (FP64), padded B, padded X and the
+// FP32 residual (all [n_pad][w_pad]), reduction scratch and one CgState.
+struct ResidualWs {
+  double* x64;
+  double* r64;
+  float* Bp;
+  float* Xp;
+  float* rf;
+  double* red;
+  CgState* S;
+  size_t bytes;
+};
+
+static ResidualWs carve_residual(void* ws, int64_t n_pad, int w_pad) {
+  Carve c(ws);
+  ResidualWs r;
+  const size_t plane = static_cast<size_t>(n_pad) * w_pad;
+  r.x64 = c.take<double>(plane);
+  r.r64 = c.take<double>(plane);
+  r.Bp = c.take<float>(plane);
+  r.Xp = c.take<float>(plane);
+  r.rf = c.take<float>(plane);
+  r.red = c.take<double>(red_doubles(n_pad, w_pad));
+  r.S = c.take<CgState>(1);
+  r.bytes = c.off + 256;
+  return r;
+}
+
 gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol, double* X64,
                        const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                        size_t ws_bytes, cudaStream_t st) {
@@ -924,6 +952,10 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
                            false, true, GP_PREC_FP32)
           .bytes;
     }
+    case GP_OP_RESIDUAL: {
+      if (check_width(w) != GP_OK) return 0;
+      return carve_residual(nullptr, round_up(n, kPad), static_cast<int>(round_up(w, 4))).bytes;
+    }
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
       SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
@@ -997,6 +1029,37 @@ gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w
   if (!(opts->refine_rtol > 0)) return fail(GP_ERR_ARG, "refine_rtol must be > 0");
   return refine_solve(prob, B, w, nullptr, X64, opts, iters, relres, ws, ws_bytes,
                       static_cast<cudaStream_t>(stream));
+}
+
+gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* X, int32_t w,
+                           double* relres, void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if (B == nullptr || X == nullptr || relres == nullptr)
+    return fail(GP_ERR_ARG, "B, X and relres must be non-NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  const int64_t n_pad = round_up(n, kPad);
+  const int w_pad = static_cast<int>(round_up(w, 4));
+  if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n_pad, w_pad).bytes)) != GP_OK) return s;
+  const ResidualWs R = carve_residual(ws, n_pad, w_pad);
+  const size_t plane = static_cast<size_t>(n_pad) * w_pad;
+  GP_CUDA(cudaMemsetAsync(R.x64, 0, plane * sizeof(double), st));
+  GP_CUDA(cudaMemsetAsync(R.Bp, 0, plane * sizeof(float), st));
+  GP_CUDA(cudaMemsetAsync(R.Xp, 0, plane * sizeof(float), st));
+  GP_CUDA(cudaMemsetAsync(R.S, 0, sizeof(CgState), st));
+  GP_CUDA(launch_pad_block(B, n, w, w, R.Bp, n_pad, w_pad, 0, st));
+  GP_CUDA(launch_pad_block(X, n, w, w, R.Xp, n_pad, w_pad, 0, st));
+  GP_CUDA(launch_refine_update(R.x64, R.Xp, n_pad, w_pad, w, st));   // x64 = X
+  const double f2 = prob->theta.f * prob->theta.f;
+  GP_CUDA(launch_refine_residual(prob->X, n, prob->d, prob->kernel, prob->theta.l, f2,
+                                 prob->theta.s, R.x64, R.Bp, R.r64, n_pad, w_pad, w, st));
+  GP_CUDA(launch_refine_norms(R.S, R.r64, R.Bp, R.rf, n_pad, w_pad, w, R.red, st));
+  HostCg h;
+  if ((s = read_cg(R.S, h, st)) != GP_OK) return s;
+  for (int c = 0; c < w; ++c) relres[c] = h.relres[c];
+  return GP_OK;
 }
 
 gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, double* logdet,

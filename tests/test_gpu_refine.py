@@ -75,3 +75,17 @@ def test_refinement_beats_fp32_cg_true_residual(api):
     r32 = np.linalg.norm(yy - Kh @ x32.cpu().numpy()[:, 0].astype(np.float64)) / np.linalg.norm(yy)
     rr = np.linalg.norm(yy - Kh @ xr.cpu().numpy()[:, 0]) / np.linalg.norm(yy)
     assert rr <= 1e-6 and rr < r32
+
+
+def test_true_residual_matches_oracle(api):
+    # gp_true_residual (FP64 entries and sums) against the dense FP64 oracle on
+    # the FP32 CG solution of three columns.
+    prob = inputs.small_problem(seed=6)
+    Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 2, seed=8)]).astype(np.float32)
+    Xs, _, _, _ = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, prob.theta,
+                                   api.solve_opts(cg_rtol=1e-6), raise_not_converged=False)
+    rel = api.gp_true_residual(_dev(prob.X), _dev(Bm), Xs, prob.kind, prob.theta)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    Xh = Xs.cpu().numpy().astype(np.float64)
+    ref = np.linalg.norm(Bm - Kh @ Xh, axis=0) / np.linalg.norm(Bm, axis=0)
+    np.testing.assert_allclose(rel, ref, rtol=1e-6, atol=0)
