@@ -135,7 +135,7 @@ def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_
     return X64, list(iters), list(relres), st
 
 
-def gp_true_residual(X, Bm, Xsol, kernel, theta) -> list:
+def gp_true_residual(X, Bm, Xsol, kernel, theta, ws=None) -> list:
     """||B_c - Kh X_c|| / ||B_c|| per column, FP64 entries and sums."""
     prob, X = problem(X, kernel, theta)
     Bm = _f32(Bm, "B")
@@ -148,7 +148,8 @@ def gp_true_residual(X, Bm, Xsol, kernel, theta) -> list:
     if Xsol.shape != (n, w):
         raise ValueError("B and Xsol must have the same shape")
     relres = (c_double * w)()
-    ws = workspace(B.OP_RESIDUAL, prob, w, None, X.device)
+    if ws is None:
+        ws = workspace(B.OP_RESIDUAL, prob, w, None, X.device)
     check(lib().gp_true_residual(byref(prob), _ptr(Bm), _ptr(Xsol), w, relres, _ptr(ws), ws.numel(),
                                  _stream(X.device)), "gp_true_residual")
     return list(relres)

@@ -1045,7 +1045,10 @@ gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* 
   if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n_pad, w_pad).bytes)) != GP_OK) return s;
   const ResidualWs R = carve_residual(ws, n_pad, w_pad);
   const size_t plane = static_cast<size_t>(n_pad) * w_pad;
+  // The residual kernel writes rows < n and columns < w only; the norms read
+  // the whole padded plane, so the padding must be zero.
   GP_CUDA(cudaMemsetAsync(R.x64, 0, plane * sizeof(double), st));
+  GP_CUDA(cudaMemsetAsync(R.r64, 0, plane * sizeof(double), st));
   GP_CUDA(cudaMemsetAsync(R.Bp, 0, plane * sizeof(float), st));
   GP_CUDA(cudaMemsetAsync(R.Xp, 0, plane * sizeof(float), st));
   GP_CUDA(cudaMemsetAsync(R.S, 0, sizeof(CgState), st));

@@ -89,3 +89,38 @@ def test_true_residual_matches_oracle(api):
     Xh = Xs.cpu().numpy().astype(np.float64)
     ref = np.linalg.norm(Bm - Kh @ Xh, axis=0) / np.linalg.norm(Bm, axis=0)
     np.testing.assert_allclose(rel, ref, rtol=1e-6, atol=0)
+
+
+def test_workspace_contents_are_ignored(api):
+    # Every call treats its workspace as scratch: a workspace full of NaN bytes
+    # gives the same results as a fresh one.
+    import torch
+    from paper_2503_02259_gb300 import _binding as B
+    prob = inputs.small_problem(seed=7)
+    X, y = _dev(prob.X), _dev(prob.y)
+    V = _dev(inputs.multivector(prob.y, 11, seed=1))
+    pr, _ = api.problem(X, prob.kind, prob.theta)
+
+    def poisoned(op, w, opts=None):
+        ws = api.workspace(op, pr, w, opts, X.device)
+        ws.fill_(0xFF)
+        return ws
+
+    Y0 = api.gp_kernel_matmul(X, V, prob.kind, prob.theta)
+    Y1 = api.gp_kernel_matmul(X, V, prob.kind, prob.theta, ws=poisoned(B.OP_MATMUL, 11))
+    assert torch.equal(Y0, Y1)
+    for prec in (3, 4):
+        o = api.solve_opts(prec=prec)
+        Y0 = api.gp_kernel_matmul(X, V, prob.kind, prob.theta, prec=prec)
+        Y1 = api.gp_kernel_matmul(X, V, prob.kind, prob.theta, prec=prec,
+                                  ws=poisoned(B.OP_MATMUL, 11, o))
+        assert torch.equal(Y0, Y1)
+    G0 = api.gp_kernel_grad_matmul(X, V, prob.kind, prob.theta)
+    G1 = api.gp_kernel_grad_matmul(X, V, prob.kind, prob.theta, ws=poisoned(B.OP_GRAD_MATMUL, 11))
+    for a, b in zip(G0, G1):
+        assert torch.equal(a, b)
+    xs, _, _, _ = api.gp_pcg_solve(X, y, prob.kind, prob.theta, api.solve_opts(cg_rtol=1e-6),
+                                   raise_not_converged=False)
+    r0 = api.gp_true_residual(X, y, xs, prob.kind, prob.theta)
+    r1 = api.gp_true_residual(X, y, xs, prob.kind, prob.theta, ws=poisoned(B.OP_RESIDUAL, 1))
+    assert r0 == r1 and r0[0] < 1e-3
