@@ -98,7 +98,7 @@ def gp_kernel_grad_matmul(X, V, kernel, theta, ws=None):
     return Y, dYf, dYl
 
 
-def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True):
+def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True, ws=None):
     """Column-wise CG: returns (Xsol, iters (w,), relres (w,), status)."""
     prob, X = problem(X, kernel, theta)
     Bm = _f32(Bm, "B")
@@ -108,7 +108,8 @@ def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converge
     Xsol = torch.empty_like(Bm)
     iters = (c_int32 * w)()
     relres = (c_double * w)()
-    ws = workspace(B.OP_PCG, prob, w, opts, X.device)
+    if ws is None:
+        ws = workspace(B.OP_PCG, prob, w, opts, X.device)
     st = lib().gp_pcg_solve(byref(prob), _ptr(Bm), w, _ptr(Xsol), byref(opts), iters, relres,
                             _ptr(ws), ws.numel(), _stream(X.device))
     if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
@@ -116,7 +117,8 @@ def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converge
     return Xsol, list(iters), list(relres), st
 
 
-def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True):
+def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True,
+                         ws=None):
     """Mixed-precision iterative refinement with an FP64 solution:
     returns (X64 (n, w) float64, total inner iterations (w,), final relres (w,), status)."""
     prob, X = problem(X, kernel, theta)
@@ -127,7 +129,8 @@ def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_
     X64 = torch.empty((n, w), dtype=torch.float64, device=X.device)
     iters = (c_int32 * w)()
     relres = (c_double * w)()
-    ws = workspace(B.OP_PCG, prob, w, opts, X.device)
+    if ws is None:
+        ws = workspace(B.OP_PCG, prob, w, opts, X.device)
     st = lib().gp_pcg_solve_refined(byref(prob), _ptr(Bm), w, _ptr(X64), byref(opts), iters, relres,
                                     _ptr(ws), ws.numel(), _stream(X.device))
     if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
@@ -155,11 +158,12 @@ def gp_true_residual(X, Bm, Xsol, kernel, theta, ws=None) -> list:
     return list(relres)
 
 
-def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts):
+def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts, ws=None):
     prob, X = problem(X, kernel, theta)
     ld = c_double()
     se = c_double()
-    ws = workspace(B.OP_SLQ, prob, 0, opts, X.device)
+    if ws is None:
+        ws = workspace(B.OP_SLQ, prob, 0, opts, X.device)
     check(lib().gp_slq_logdet(byref(prob), byref(opts), byref(ld), byref(se), _ptr(ws), ws.numel(),
                               _stream(X.device)), "gp_slq_logdet")
     return ld.value, se.value
@@ -204,14 +208,15 @@ def gp_nll_backward(X, W, kernel, theta, opts: B.gp_solve_opts):
     return list(grad), info.as_dict()
 
 
-def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32):
+def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32, ws=None):
     """mu = f^2 K(X*, X) alpha."""
     prob, X = problem(X, kernel, theta)
     alpha = _f32(alpha, "alpha").reshape(-1)
     Xstar = _f32(Xstar, "Xstar")
     m = Xstar.shape[0]
     mu = torch.empty(m, dtype=torch.float32, device=X.device)
-    ws = workspace(B.OP_PREDICT, prob, m, None, X.device)
+    if ws is None:
+        ws = workspace(B.OP_PREDICT, prob, m, None, X.device)
     check(lib().gp_predict_mean(byref(prob), _ptr(alpha), _ptr(Xstar), m, _ptr(mu), int(prec),
                                 _ptr(ws), ws.numel(), _stream(X.device)), "gp_predict_mean")
     return mu

@@ -124,3 +124,24 @@ def test_workspace_contents_are_ignored(api):
     r0 = api.gp_true_residual(X, y, xs, prob.kind, prob.theta)
     r1 = api.gp_true_residual(X, y, xs, prob.kind, prob.theta, ws=poisoned(B.OP_RESIDUAL, 1))
     assert r0 == r1 and r0[0] < 1e-3
+    # Solvers: CG (FP32 and a refined tensor-core solve), SLQ, loss + gradient, prediction.
+    o = api.solve_opts(cg_rtol=1e-6)
+    a0 = api.gp_pcg_solve(X, y, prob.kind, prob.theta, o)
+    a1 = api.gp_pcg_solve(X, y, prob.kind, prob.theta, o, ws=poisoned(B.OP_PCG, 1, o))
+    assert torch.equal(a0[0], a1[0]) and a0[1:] == a1[1:]
+    o = api.solve_opts(cg_rtol=1e-2, prec=4, refine_rtol=1e-7, refine_maxit=30)
+    b0 = api.gp_pcg_solve_refined(X, y, prob.kind, prob.theta, o)
+    b1 = api.gp_pcg_solve_refined(X, y, prob.kind, prob.theta, o, ws=poisoned(B.OP_PCG, 1, o))
+    assert torch.equal(b0[0], b1[0]) and b0[1:] == b1[1:]
+    o = api.solve_opts(nprobe=6, nlanczos=20, seed=3, prec=4, slq_prec=3)
+    assert (api.gp_slq_logdet(X, prob.kind, prob.theta, o) ==
+            api.gp_slq_logdet(X, prob.kind, prob.theta, o, ws=poisoned(B.OP_SLQ, 0, o)))
+    o = api.solve_opts(nprobe=6, nlanczos=20, seed=3, cg_rtol=1e-6)
+    l0 = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, o)
+    l1 = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, o, ws=poisoned(B.OP_LOSS_GRAD, 0, o))
+    assert l0[0] == l1[0] and l0[1] == l1[1]
+    Xs = _dev(inputs.points(300, 3, seed=9))
+    m0 = api.gp_predict_mean(X, a0[0][:, 0].contiguous(), Xs, prob.kind, prob.theta)
+    m1 = api.gp_predict_mean(X, a0[0][:, 0].contiguous(), Xs, prob.kind, prob.theta,
+                             ws=poisoned(B.OP_PREDICT, 300))
+    assert torch.equal(m0, m1)
