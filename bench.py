@@ -375,12 +375,14 @@ def serving(torch, count: int = 64,
             wall = time.perf_counter() - t0
             stats = srv.stats()
         results[name] = res
-        lat = np.array([r["latency_s"] for r in res])
-        small = np.array([r["latency_s"] for r, rq in zip(res, reqs) if rq.problem.n <= 20000])
+        lat = np.array([r["latency_from_arrival_s"] for r in res])
+        small = np.array([r["latency_from_arrival_s"] for r, rq in zip(res, reqs)
+                          if rq.problem.n <= 20000])
         out[name] = {"requests_ok": sum(r["status"] in (0, 4) for r in res), "wall_s": wall,
                      "requests_per_s": len(res) / wall, "entries_cols_per_s": work / wall,
                      "latency_p50_s": float(np.percentile(lat, 50)),
                      "latency_p99_s": float(np.percentile(lat, 99)),
+                     "latency_from": "scheduled arrival (Poisson stream time) to completion",
                      "latency_p99_s_n_le_2e4": float(np.percentile(small, 99)) if small.size else None,
                      "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"]}
     # Accuracy of a fixed-budget solve is its final CG residual (the budget, not the

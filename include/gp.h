@@ -333,10 +333,13 @@ gp_status gp_measure_pipe_rates(double* fp32_tflops, double* mufu_ex2_gops, void
  *  - gp_server_submit copies the request's HOST arrays into pinned staging and
  *    queues it; a request whose footprint (inputs + outputs + solver
  *    workspace) exceeds the whole budget is refused with GP_ERR_OOM.
- *  - Admission is first come, first served: the queue head starts as soon as a
- *    worker is free and its footprint fits the pool's free space, so requests
- *    that arrive while others run join them on the device; their kernels
- *    overlap through the workers' streams.
+ *  - Admission: when a worker is free, the queued request with the least work
+ *    (entries x columns) among those whose footprint fits the pool's free
+ *    space starts; a request that has waited 2 s or more starts before any
+ *    younger one, in arrival order (it waits for room if it does not fit), so
+ *    large requests are not starved.  Requests that arrive while others run
+ *    join them on the device; their kernels overlap through the workers'
+ *    streams.
  *  - Kind 0 runs gp_loss_and_grad; kind 1 solves alpha = Kh^-1 y by block CG and
  *    returns the posterior mean at Xstar.  With a fixed CG budget (cg_maxit) a
  *    result may carry GP_ERR_NOT_CONVERGED with its estimates filled in.

@@ -2,11 +2,14 @@
 //
 // One device pool of the HBM budget is reserved at creation and sub-allocated
 // first-fit; max_slots worker threads each own one CUDA stream per stream
-// priority level.  A worker takes the queue head as soon as the head's
-// footprint fits the pool's free space, runs the request through the library's
-// own calls and returns the memory, so requests that arrive while others are
-// running join them on the device: the CTAs of all running requests' kernels
-// are interleaved on the SMs by the hardware work distributor.  A request runs
+// priority level.  A free worker admits the queued request with the least work
+// (entries x columns) among those whose footprint fits the pool's free space;
+// a request that has waited kAgeSeconds or more is admitted first, in arrival
+// order, so large requests are not starved.  It runs the request through the
+// library's own calls and returns the memory, so requests that arrive while
+// others are running join them on the device: the CTAs of all running
+// requests' kernels are interleaved on the SMs by the hardware work
+// distributor.  A request runs
 // on a stream whose priority falls with its work (entries x columns), so the
 // tiles of a small request are dispatched ahead of the queued tiles of a large
 // one instead of waiting for them.  The paper serves nothing; its stateless
@@ -21,6 +24,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -132,10 +136,13 @@ struct Job {
   uint64_t ticket = 0;
   gp_request req{};
   JobLayout lay{};
-  float* hX = nullptr;   // pinned staging (inputs) and results
-  float* hy = nullptr;
-  float* hXs = nullptr;
+  double work = 0.0;     // entries x columns of its products (admission order)
+  float* hX = nullptr;   // host staging (inputs) and results: a block of the
+  float* hy = nullptr;   // pinned staging pool, or pageable memory when the
+  float* hXs = nullptr;  // pool is full
   float* hmu = nullptr;
+  size_t hoff = 0, hbytes = 0;        // pinned block (hbytes > 0)
+  std::unique_ptr<float[]> pageable;  // fallback staging
   gp_result res{};
   bool done = false;
 };
@@ -151,6 +158,11 @@ struct gp_server {
   char* pool = nullptr;
   size_t budget = 0;
   std::unique_ptr<PoolAllocator> alloc;
+  // Pinned host staging, reserved once (a per-request cudaMallocHost /
+  // cudaFreeHost could stall the device); guarded by mu.
+  char* hpool = nullptr;
+  size_t hbudget = 0;
+  std::unique_ptr<PoolAllocator> halloc;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<std::shared_ptr<Job>> queue;
@@ -165,11 +177,14 @@ struct gp_server {
 
 namespace {
 
-void free_staging(Job& j) {
-  if (j.hX) cudaFreeHost(j.hX);
-  if (j.hy) cudaFreeHost(j.hy);
-  if (j.hXs) cudaFreeHost(j.hXs);
-  if (j.hmu) cudaFreeHost(j.hmu);
+// Returns a job's staging (its pinned block, or its pageable buffer).
+void free_staging(gp_server* srv, Job& j) {
+  if (j.hbytes > 0) {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    srv->halloc->release(j.hoff, j.hbytes);
+  }
+  j.hbytes = 0;
+  j.pageable.reset();
   j.hX = j.hy = j.hXs = j.hmu = nullptr;
 }
 
@@ -245,6 +260,37 @@ int priority_level(const gp_request& r, int levels) {
   return b;
 }
 
+// Waiting time after which a queued request is admitted before any younger one.
+constexpr double kAgeSeconds = 2.0;
+
+// Called with srv->mu held: picks the next request to admit and reserves its
+// pool block (returns false if none can start now).  The oldest request goes
+// first once it has waited kAgeSeconds (it waits for room if it does not fit);
+// otherwise the request with the least work that fits.
+bool admit_next(gp_server* srv, std::shared_ptr<Job>* job, size_t* off) {
+  auto& q = srv->queue;
+  if (q.empty()) return false;
+  const double now = seconds_since(srv->t0);
+  if (now - q.front()->res.t_submit_s >= kAgeSeconds) {
+    if (!srv->alloc->alloc(q.front()->lay.total, off)) return false;
+    *job = q.front();
+    q.pop_front();
+    return true;
+  }
+  std::vector<size_t> order(q.size());
+  for (size_t i = 0; i < q.size(); ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](size_t a, size_t b) { return q[a]->work < q[b]->work; });
+  for (size_t i : order) {
+    if (srv->alloc->alloc(q[i]->lay.total, off)) {
+      *job = q[i];
+      q.erase(q.begin() + static_cast<std::ptrdiff_t>(i));
+      return true;
+    }
+  }
+  return false;
+}
+
 void worker_main(gp_server* srv) {
   cudaSetDevice(srv->device);
   int least = 0, greatest = 0;
@@ -263,12 +309,11 @@ void worker_main(gp_server* srv) {
     size_t off = 0;
     {
       std::unique_lock<std::mutex> lk(srv->mu);
-      srv->cv_work.wait(lk, [&] {
-        return srv->stop || (!srv->queue.empty() && srv->alloc->alloc(srv->queue.front()->lay.total, &off));
-      });
+      // Re-check at least every 100 ms, so that a request reaching kAgeSeconds
+      // is noticed without another event.
+      while (!srv->stop && !admit_next(srv, &job, &off))
+        srv->cv_work.wait_for(lk, std::chrono::milliseconds(100));
       if (srv->stop) break;
-      job = srv->queue.front();
-      srv->queue.pop_front();
       ++srv->active;
       srv->peak_active = std::max(srv->peak_active, srv->active);
       srv->peak_bytes = std::max(srv->peak_bytes, srv->alloc->in_use());
@@ -321,6 +366,17 @@ gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server
   }
   srv->pool = static_cast<char*>(p);
   srv->alloc = std::make_unique<PoolAllocator>(srv->budget);
+  // Pinned staging: 1/8 of the device budget, between 64 MiB and 2 GiB.
+  srv->hbudget = std::min<size_t>(std::max<size_t>(srv->budget / 8, size_t(64) << 20),
+                                  size_t(2) << 30);
+  void* hp = nullptr;
+  if (cudaMallocHost(&hp, srv->hbudget) != cudaSuccess) {
+    cudaGetLastError();
+    srv->hbudget = 0;   // every request uses pageable staging
+  }
+  srv->hpool = static_cast<char*>(hp);
+  srv->halloc = std::make_unique<PoolAllocator>(srv->hbudget);
+  srv->t0 = std::chrono::steady_clock::now();   // the clock of t_submit_s / t_done_s
   for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back(worker_main, srv);
   *out = srv;
   return GP_OK;
@@ -334,20 +390,38 @@ gp_status gp_server_submit(gp_server* srv, const gp_request* req, uint64_t* tick
   auto job = std::make_shared<Job>();
   if (!layout_of(r, &job->lay)) return fail(GP_ERR_ARG, "gp_server_submit: invalid request");
   job->req = r;
+  job->work = request_work(r);
   const double t_submit = seconds_since(srv->t0);
   if (job->lay.total > srv->budget) {
     std::lock_guard<std::mutex> lk(srv->mu);
     ++srv->refused;
     return fail(GP_ERR_OOM, "gp_server_submit: request footprint exceeds the server's budget");
   }
-  bool ok = cudaMallocHost(reinterpret_cast<void**>(&job->hX), sizeof(float) * r.n * r.d) == cudaSuccess &&
-            cudaMallocHost(reinterpret_cast<void**>(&job->hy), sizeof(float) * r.n) == cudaSuccess;
-  if (ok && r.kind == 1)
-    ok = cudaMallocHost(reinterpret_cast<void**>(&job->hXs), sizeof(float) * r.m * r.d) == cudaSuccess &&
-         cudaMallocHost(reinterpret_cast<void**>(&job->hmu), sizeof(float) * r.m) == cudaSuccess;
-  if (!ok) {
-    free_staging(*job);
-    return fail(GP_ERR_OOM, "gp_server_submit: cannot allocate pinned staging");
+  // Staging block: X, y, and for predictions X* and mu, each 256-byte aligned.
+  const size_t bx = align_up(sizeof(float) * r.n * r.d), by = align_up(sizeof(float) * r.n);
+  const size_t bxs = r.kind == 1 ? align_up(sizeof(float) * r.m * r.d) : 0;
+  const size_t bmu = r.kind == 1 ? align_up(sizeof(float) * r.m) : 0;
+  const size_t hb = bx + by + bxs + bmu;
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    size_t off = 0;
+    if (srv->hbudget > 0 && srv->halloc->alloc(hb, &off)) {
+      job->hoff = off;
+      job->hbytes = hb;
+      base = srv->hpool + off;
+    }
+  }
+  if (base == nullptr) {
+    job->pageable.reset(new (std::nothrow) float[hb / sizeof(float)]);
+    if (!job->pageable) return fail(GP_ERR_OOM, "gp_server_submit: cannot allocate host staging");
+    base = reinterpret_cast<char*>(job->pageable.get());
+  }
+  job->hX = reinterpret_cast<float*>(base);
+  job->hy = reinterpret_cast<float*>(base + bx);
+  if (r.kind == 1) {
+    job->hXs = reinterpret_cast<float*>(base + bx + by);
+    job->hmu = reinterpret_cast<float*>(base + bx + by + bxs);
   }
   memcpy(job->hX, r.X, sizeof(float) * r.n * r.d);
   memcpy(job->hy, r.y, sizeof(float) * r.n);
@@ -382,7 +456,7 @@ gp_status gp_server_poll(gp_server* srv, uint64_t ticket, gp_result* res) {
   res->mu = user_mu;
   if (user_mu != nullptr && job->req.kind == 1 && job->hmu != nullptr)
     memcpy(user_mu, job->hmu, sizeof(float) * job->req.m);
-  free_staging(*job);
+  free_staging(srv, *job);
   return GP_OK;
 }
 
@@ -415,10 +489,11 @@ gp_status gp_server_destroy(gp_server* srv) {
   }
   srv->cv_work.notify_all();
   for (auto& t : srv->workers) t.join();
-  for (auto& kv : srv->jobs) free_staging(*kv.second);
+  for (auto& kv : srv->jobs) free_staging(srv, *kv.second);
   srv->jobs.clear();
   srv->queue.clear();
   if (srv->pool) cudaFree(srv->pool);
+  if (srv->hpool) cudaFreeHost(srv->hpool);
   delete srv;
   return GP_OK;
 }

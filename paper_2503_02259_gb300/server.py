@@ -17,6 +17,7 @@ class Server:
         h = ctypes.c_void_p()
         check(lib().gp_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
               "gp_server_create")
+        self.t0 = time.perf_counter()   # the server clock's origin (its times are relative to it)
         self._h = h
         self._keep = {}   # host arrays of queued requests stay alive until polled
 
@@ -86,9 +87,12 @@ class Server:
 def replay(server: Server, requests, time_scale: float = 1.0, cg_maxit_train: int = 20,
            cg_maxit_pred: int = 50, **kw) -> list[dict]:
     """Submit requests at their arrival times (seconds x time_scale) and collect the
-    results; returns one dict per request with its latency (done - submit).  The CG
-    budgets default to a fixed 20 iterations for loss+grad and 50 for predictions."""
+    results; returns one dict per request with its latency from submission
+    (done - submit, server clock) and from its scheduled arrival time (which also
+    counts any delay in submitting it).  The CG budgets default to a fixed 20
+    iterations for loss+grad and 50 for predictions."""
     t0 = time.perf_counter()
+    shift = t0 - server.t0   # server-clock time of the stream's start
     tickets = []
     for rq in requests:
         delay = rq.t_arrive * time_scale - (time.perf_counter() - t0)
@@ -101,8 +105,9 @@ def replay(server: Server, requests, time_scale: float = 1.0, cg_maxit_train: in
         tickets.append(server.submit(req, keep))
     server.drain()
     out = []
-    for t in tickets:
+    for t, rq in zip(tickets, requests):
         r = server.poll(t)
         r["latency_s"] = r["t_done"] - r["t_submit"]
+        r["latency_from_arrival_s"] = r["t_done"] - (shift + rq.t_arrive * time_scale)
         out.append(r)
     return out
