@@ -335,7 +335,7 @@ gp_status gp_measure_pipe_rates(double* fp32_tflops, double* mufu_ex2_gops, void
  *    workspace) exceeds the whole budget is refused with GP_ERR_OOM.
  *  - Admission: when a worker is free, the queued request with the least work
  *    (entries x columns) among those whose footprint fits the pool's free
- *    space starts; a request that has waited 2 s or more starts before any
+ *    space starts; a request that has waited 30 s or more starts before any
  *    younger one, in arrival order (it waits for room if it does not fit), so
  *    large requests are not starved.  Requests that arrive while others run
  *    join them on the device; their kernels overlap through the workers'

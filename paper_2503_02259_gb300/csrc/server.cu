@@ -260,8 +260,9 @@ int priority_level(const gp_request& r, int levels) {
   return b;
 }
 
-// Waiting time after which a queued request is admitted before any younger one.
-constexpr double kAgeSeconds = 2.0;
+// Waiting time after which a queued request is admitted before any younger one
+// (bounds how long the least-work-first order can hold a large request back).
+constexpr double kAgeSeconds = 30.0;
 
 // Called with srv->mu held: picks the next request to admit and reserves its
 // pool block (returns false if none can start now).  The oldest request goes
