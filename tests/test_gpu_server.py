@@ -109,3 +109,21 @@ def test_admission_respects_budget_and_refuses_oversize(env):
             srv.submit(r, keep)
         assert ei.value.status == 3   # GP_ERR_OOM
         assert srv.stats()["refused"] == 1
+
+
+def test_least_work_first_admission(env):
+    # One slot: A runs while B (larger) and C (smaller) queue; when A finishes,
+    # the request with less work (C) starts before B.
+    torch, api, server = env
+    sizes = {"A": 20000, "B": 8000, "C": 1000}
+    with server.Server(8 << 30, 1) as srv:
+        tickets = {}
+        for name in ("A", "B", "C"):
+            p = inputs.uniform_problem(sizes[name], 3, O.GAUSSIAN, (0.1, 1.0, 0.3), seed=3)
+            r, keep = server.Server.request(0, p.X, p.y, p.kind, p.theta, nprobe=4, cg_maxit=30,
+                                            nlanczos=10, cg_rtol=1e-12)
+            tickets[name] = srv.submit(r, keep)
+        srv.drain(300)
+        res = {k: srv.poll(t) for k, t in tickets.items()}
+    assert all(r["status"] in (0, 4) for r in res.values())
+    assert res["A"]["t_start"] <= res["C"]["t_start"] <= res["B"]["t_start"]
