@@ -330,9 +330,11 @@ gp_status gp_measure_pipe_rates(double* fp32_tflops, double* mufu_ex2_gops, void
  *    level of the device; a request runs on the stream whose priority falls
  *    with its work (entries x columns), so small requests are not queued
  *    behind the tiles of large ones.
- *  - gp_server_submit copies the request's HOST arrays into pinned staging and
- *    queues it; a request whose footprint (inputs + outputs + solver
- *    workspace) exceeds the whole budget is refused with GP_ERR_OOM.
+ *  - gp_server_submit copies the request's HOST arrays into staging (a pinned
+ *    host pool reserved at creation, 1/8 of the budget between 64 MiB and
+ *    2 GiB; pageable memory when it is full) and queues it; a request whose
+ *    footprint (inputs + outputs + solver workspace) exceeds the whole budget
+ *    is refused with GP_ERR_OOM.
  *  - Admission: when a worker is free, the queued request with the least work
  *    (entries x columns) among those whose footprint fits the pool's free
  *    space starts; a request that has waited 30 s or more starts before any
@@ -386,7 +388,9 @@ typedef struct {
 } gp_result;
 
 /* Create a server on the current device with a device-memory budget and a
- * maximum number of concurrently resident requests. */
+ * maximum number of concurrently resident requests (1..256; budget >= 1 MiB).
+ * GP_ERR_OOM if the device pool cannot be reserved.  The server clock of
+ * gp_result starts when this call returns. */
 gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server** out);
 /* Queue a request (host arrays copied at submit); returns a ticket.
  * GP_ERR_OOM if the request can never fit the budget. */
@@ -402,7 +406,7 @@ gp_status gp_server_get_stats(gp_server* srv, gp_server_stats* out);
 /* Footprint in bytes the server charges a request (0 on invalid arguments). */
 size_t gp_server_footprint(const gp_request* req);
 /* Stop the workers after the running requests finish; queued requests are
- * dropped.  Frees the pool. */
+ * dropped.  Frees the device pool and the pinned staging pool. */
 gp_status gp_server_destroy(gp_server* srv);
 
 #ifdef __cplusplus
