@@ -23,7 +23,7 @@ int tc_mode_for(int prec) {
 
 static int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-SimtPlan plan_tc(int64_t nr, int64_t nc, int d, int w, int, int) {
+SimtPlan plan_tc(int64_t nr, int64_t nc, int d, int w, int, int prec) {
   SimtPlan p{};
   p.dt = dim_template(d);
   p.dp = dim_padded(p.dt);
@@ -34,7 +34,7 @@ SimtPlan plan_tc(int64_t nr, int64_t nc, int d, int w, int, int) {
   p.nr_pad = round_up(nr, kPad);
   p.nc_pad = round_up(nc, kPad);
   p.row_tiles = static_cast<int>(p.nr_pad / kTcM);
-  p.jtiles = static_cast<int>(p.nc_pad / kTcBK);
+  p.jtiles = static_cast<int>(p.nc_pad / tc_tile_cols(tc_mode_for(prec)));
   // Same balance rule as the SIMT plan: spread CTAs evenly over the SMs.
   const int nsm = num_sms();
   int best_s = 1;

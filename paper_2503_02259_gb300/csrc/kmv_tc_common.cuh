@@ -12,14 +12,14 @@
 namespace gp {
 
 constexpr int kTcM = 128;        // rows per CTA = MMA M
-constexpr int kTcBK = 32;        // points j per tile = MMA K extent per tile
+constexpr int kTcBK = 32;        // points per staged point tile; the widest MMA tile
 constexpr int kTcEvalThreads = 256;  // eval warps 0-7: two threads per row
 constexpr int kTcThreads = 288;      // + one control warp (copies and MMA issue)
 constexpr int kTcBStages = 5;
 constexpr int kTcAStages = 2;
 constexpr int kTcNumBars = 2 * kTcBStages + 2 * kTcAStages + 1;
 static_assert(kTcNumBars * 8 + 8 <= 128, "barriers, tmem holder and abort flag share 128 bytes");
-constexpr int kTcFlush = 16;     // tiles per accumulation block
+constexpr int kTcFlushCols = 512;  // columns j per accumulation block
 
 // NSA / NSB: parts the A (kernel tile) and B (V tile) operands are split into
 // (hi, or hi + rounded remainder lo); NPROD: MMAs per K-step and accumulator.
@@ -50,12 +50,19 @@ struct TcTraits<kTcBF16x3> {
   static constexpr uint32_t FMT = 1;
 };
 
+// Columns j per tile (the MMA K extent of a tile): 32, or 16 for split TF32,
+// whose 4-byte hi and lo A operands would otherwise fill 128 KB of shared
+// memory per CTA and allow only one CTA per SM.
+constexpr int tc_tile_cols(int mode) { return mode == kTcTF32x3 ? 16 : 32; }
+
 // Geometry shared by host and device.
 template <int MODE>
 struct TcGeom {
   static constexpr int ES = TcTraits<MODE>::ES;
+  static constexpr int BK = tc_tile_cols(MODE);       // columns j per tile
+  static constexpr int FLUSH = kTcFlushCols / BK;     // tiles per accumulation block
   static constexpr int EPC = 16 / ES;                 // elements per 16-byte core-matrix row
-  static constexpr int CK = kTcBK / EPC;              // core matrices along K per tile
+  static constexpr int CK = BK / EPC;                 // core matrices along K per tile
   static constexpr uint32_t SBO = CK * 128;           // bytes between 8-row groups
   static constexpr uint32_t LBO = 128;                // bytes between K-adjacent core matrices
   static constexpr int KSTEPS = CK / 2;               // MMAs (32 bytes of K each) per tile
@@ -191,7 +198,7 @@ __host__ __device__ inline TcSmem tc_smem(int n, bool grad, int nbs) {
   using G = TcGeom<MODE>;
   constexpr int DP = DimTraits<DT>::DP;
   TcSmem s;
-  s.xbytes = kTcBK * DP * 4;
+  s.xbytes = kTcBK * DP * 4;   // the 32-point tile holding the tile's points
   s.bbytes = static_cast<uint32_t>(n / 8) * G::SBO;
   s.abytes = G::A_BYTES;
   s.bars = 0;                                 // kTcNumBars mbarriers, tmem holder, abort flag

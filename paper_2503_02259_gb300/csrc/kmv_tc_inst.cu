@@ -36,7 +36,7 @@ __global__ void tc_stage_v_kernel(const float* v, int n, int jtiles, unsigned ch
     float2 vals[EPC / 2];
 #pragma unroll
     for (int u = 0; u < EPC / 2; ++u) {
-      const int64_t j = jt * kTcBK + kg * EPC + 2 * u;
+      const int64_t j = jt * G::BK + kg * EPC + 2 * u;
       vals[u] = make_float2(v[j * n + c], v[(j + 1) * n + c]);
     }
     const uint32_t off = static_cast<uint32_t>(c >> 3) * G::SBO + static_cast<uint32_t>(kg) * G::LBO +

@@ -2,7 +2,7 @@
 // generation tensor cores (tcgen05, sm_103a), warp-specialised.
 //
 // One CTA owns 128 rows (points x_i, the MMA M dimension) and walks the columns
-// j in tiles of kTcBK points.
+// j in tiles of G::BK points (32, or 16 for split TF32).
 //   * Control warp (warp 8, lane 0): issues the bulk (TMA) copies of each
 //     tile's points and of its slice of V, already laid out as the MMA B
 //     operand, into a shared ring of up to kTcBStages stages (as many as fit),
@@ -19,9 +19,9 @@
 // SM (the on-the-fly MatVec of §Statement of Need; the derivative shares the
 // distance evaluation).
 //
-// Blocked accumulation: the accumulator restarts every kTcFlush tiles after the
+// Blocked accumulation: the accumulator restarts every G::FLUSH tiles after the
 // eval warps have added its block sum (FP32) into a running sum kept in tensor
-// memory, so accumulation chains stay kTcFlush * kTcBK long.
+// memory, so accumulation chains stay kTcFlushCols = 512 columns long.
 //
 // Every mbarrier wait is bounded (and polls a shared abort flag); on a timeout
 // the CTA records kDevTimeout, waits (bounded) for its own copies and MMAs in
@@ -164,6 +164,7 @@ __global__ void GP_TC_BOUNDS
         ok = tc::wait_or_abort(&emptyA[as], ((t - kTcAStages) / kTcAStages) & 1, abort_s);
       if (!ok) break;
       const float* xs = sX + bs * (L.xbytes / 4);
+      const int jo = ((jt0 + t) * G::BK) & (kTcBK - 1);   // the tile's offset in its point tile
       unsigned char* aK = sA + (as * NMAT * NSA) * L.abytes;
       unsigned char* aD = aK + NSA * L.abytes;
 #pragma unroll
@@ -173,7 +174,7 @@ __global__ void GP_TC_BOUNDS
 #pragma unroll
         for (int u = 0; u < EPC / 4; ++u) {
           float2 q01, q23;
-          sqdist_quad<DT>(xi2, xs, kg * EPC + 4 * u, q01, q23);
+          sqdist_quad<DT>(xi2, xs, jo + kg * EPC + 4 * u, q01, q23);
           dv[2 * u] = dv[2 * u + 1] = make_float2(0.f, 0.f);
           eval_pair<KIND, GRAD>(q01, kv[2 * u], dv[2 * u]);
           eval_pair<KIND, GRAD>(q23, kv[2 * u + 1], dv[2 * u + 1]);
@@ -184,7 +185,7 @@ __global__ void GP_TC_BOUNDS
       }
       tc::fence_proxy_async();
       tc::arrive(&fullA[as]);
-      if (t > 0 && t % kTcFlush == 0) {
+      if (t > 0 && t % G::FLUSH == 0) {
         // Fold the block that ended at tile t-1 once its MMAs are complete.
         ok = tc::wait_or_abort(&emptyA[(t - 1) % kTcAStages], ((t - 1) / kTcAStages) & 1, abort_s);
         if (!ok) break;
@@ -237,7 +238,8 @@ __global__ void GP_TC_BOUNDS
       ist = (ist + 1 == nbs) ? 0 : ist + 1;
       const int64_t jt = jt0 + t;
       dev::mbar_arrive_expect_tx(&fullX[st], L.xbytes + NSB * L.bbytes);
-      dev::bulk_g2s(sX + st * (L.xbytes / 4), a.xc + jt * kTcBK * DP, L.xbytes, &fullX[st]);
+      dev::bulk_g2s(sX + st * (L.xbytes / 4), a.xc + ((jt * G::BK) / kTcBK) * kTcBK * DP, L.xbytes,
+                    &fullX[st]);
       const unsigned char* vsrc = static_cast<const unsigned char*>(a.vt) + jt * NSB * L.bbytes;
       dev::bulk_g2s(sB + st * NSB * L.bbytes, vsrc, NSB * L.bbytes, &fullX[st]);
     };
@@ -266,15 +268,15 @@ __global__ void GP_TC_BOUNDS
       const int as = t % kTcAStages;
       ok = tc::wait_or_abort(&fullX[bs], bph, abort_s);
       if (ok) ok = tc::wait_or_abort(&fullA[as], (t / kTcAStages) & 1, abort_s);
-      if (ok && t > 0 && t % kTcFlush == 0)
-        ok = tc::wait_or_abort(folded, ((t / kTcFlush) - 1) & 1, abort_s);
+      if (ok && t > 0 && t % G::FLUSH == 0)
+        ok = tc::wait_or_abort(folded, ((t / G::FLUSH) - 1) & 1, abort_s);
       if (!ok) break;
       tc::fence_after();
       // Descriptors: the stage-0 templates plus this tile's offsets, in the
       // descriptor's start-address units (bytes >> 4, the low bits).
       const uint64_t da = desc_a0 + ((static_cast<uint32_t>(as) * a_stage) >> 4);
       const uint64_t db = desc_b0 + ((static_cast<uint32_t>(bs) * b_stage) >> 4);
-      uint32_t acc = (t % kTcFlush == 0) ? 0u : 1u;   // a block starts from zero
+      uint32_t acc = (t % G::FLUSH == 0) ? 0u : 1u;   // a block starts from zero
 #pragma unroll
       for (int ks = 0; ks < G::KSTEPS; ++ks) {
         // One MMA consumes two K-adjacent core matrices (32 bytes of K).
