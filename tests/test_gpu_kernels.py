@@ -46,6 +46,8 @@ CASES = [
     (128, 3, 17, O.MATERN32),
     (129, 5, 32, O.GAUSSIAN),
     (300, 8, 33, O.MATERN32),
+    (513, 3, 37, O.GAUSSIAN),      # one 40-column group (TW = 40)
+    (640, 8, 40, O.MATERN32),
     (777, 16, 64, O.GAUSSIAN),
     (2000, 3, 11, O.GAUSSIAN),
     (2000, 3, 32, O.MATERN32),
