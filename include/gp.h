@@ -37,6 +37,12 @@
  *    no call keeps state between calls except the thread-local error string,
  *    per-device launch-configuration caches, and one private stream per host
  *    thread and device on which the solvers capture their CG-iteration graphs.
+ *  - CG step: after each product the O(n w) part of a CG iteration (alpha,
+ *    the x / r update, beta and the stopping test, the p update) runs as one
+ *    cooperative launch with two grid barriers (bounded: a barrier that waits
+ *    more than 4 s returns GP_ERR_TIMEOUT).  The environment variable
+ *    GP_CG_FUSED=0 selects three separate launches instead; both give the same
+ *    bits.  The request server's workers always use the separate launches.
  */
 #ifndef GP_H
 #define GP_H

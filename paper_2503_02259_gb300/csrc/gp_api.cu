@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cstdlib>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <string>
@@ -87,6 +89,7 @@ constexpr size_t kMaxProfiled = 65536;
 // Stream capture in progress on this host thread: launches are recorded into a
 // graph, not executed, so they are counted separately and not timed.
 thread_local int t_capturing = 0;
+thread_local bool t_cooperative = true;
 thread_local int64_t t_captured_launches = 0;
 std::mutex g_mu;
 std::map<std::tuple<int, int, int, int, int, int>, int> g_occ;
@@ -94,6 +97,9 @@ std::map<int, int> g_nsm;
 }  // namespace
 
 void set_error(const std::string& msg) { t_err = msg; }
+
+void set_thread_cooperative(bool allowed) { t_cooperative = allowed; }
+bool thread_cooperative() { return t_cooperative; }
 
 void count_launch() {
   if (t_capturing)
@@ -500,19 +506,32 @@ static gp_status product_call(const gp_problem* prob, const float* V, int32_t w,
 namespace gp {
 
 // One block-CG iteration: the product K P, then alpha, the x / r update and the
-// p update (vec_kernels.cu).
+// p update (vec_kernels.cu), as one cooperative launch when `fused`, else as
+// three launches with the same arithmetic.
 static gp_status cg_iteration(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W,
-                              cudaStream_t st) {
+                              bool fused, cudaStream_t st) {
   const int64_t n = prob->n;
   const double f2 = prob->theta.f * prob->theta.f;
   gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.vt, W.part, nullptr,
                             &W.S->n_active, &W.S->err, st);
   if (s != GP_OK) return s;
+  if (fused) {
+    GP_CUDA(launch_cg_step(W.S, W.part, p.split, W.X, W.R, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
+                           prob->theta.s, W.red, st));
+    return GP_OK;
+  }
   GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
                               prob->theta.s, W.red, st));
   GP_CUDA(launch_cg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
   GP_CUDA(launch_cg_pupdate(W.S, W.R, W.P, p.nr_pad, p.w_pad, st));
   return GP_OK;
+}
+
+// The fused CG step is used unless the environment sets GP_CG_FUSED=0 (the
+// separate kernels give the same bits; the switch exists to compare them).
+static bool cg_fused_wanted() {
+  const char* v = std::getenv("GP_CG_FUSED");
+  return v == nullptr || std::strcmp(v, "0") != 0;
 }
 
 // A private non-blocking stream of this host thread on the current device,
@@ -590,17 +609,19 @@ gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W
   // graph could not be built.
   IterationGraph graph;
   bool tried = false, use_graph = false;
+  const bool fused = thread_cooperative() && cg_fused_wanted() && cg_step_fits(p.nr_pad);
   while (issued < maxit) {
     const int todo = std::min(chunk, maxit - issued);
     for (int k = 0; k < todo; ++k) {
       if (issued + k > 0 && !tried) {
         tried = true;
-        use_graph = graph.capture([&](cudaStream_t cs) { return cg_iteration(prob, p, prec, W, cs); });
+        use_graph = graph.capture(
+            [&](cudaStream_t cs) { return cg_iteration(prob, p, prec, W, fused, cs); });
       }
       if (use_graph) {
         GP_CUDA(graph.launch(st));
       } else {
-        gp_status s = cg_iteration(prob, p, prec, W, st);
+        gp_status s = cg_iteration(prob, p, prec, W, fused, st);
         if (s != GP_OK) return s;
       }
     }

@@ -78,6 +78,12 @@ int simt_occupancy(int kernel, bool grad, int dt, int tw, int w_pad, int dp);
 // Thread-local error message.
 void set_error(const std::string& msg);
 
+// Cooperative launches (the fused CG step) are allowed on this host thread
+// unless switched off; the request server switches them off in its workers, so
+// that grids on concurrent streams never wait for one another's residency.
+void set_thread_cooperative(bool allowed);
+bool thread_cooperative();
+
 // Measurement hooks: every launcher calls count_launch(); the product launch is
 // bracketed by profile_product_begin/end (no-ops unless a window is open).
 void count_launch();

@@ -294,6 +294,7 @@ bool admit_next(gp_server* srv, std::shared_ptr<Job>* job, size_t* off) {
 
 void worker_main(gp_server* srv) {
   cudaSetDevice(srv->device);
+  gp::set_thread_cooperative(false);
   int least = 0, greatest = 0;
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
   const int levels = std::max(1, std::min(8, least - greatest + 1));

@@ -282,6 +282,7 @@ __global__ void cg_init_kernel(CgState* S, const float* B, float* X, float* R, f
     S->n_active = cnt;
     S->err = 0;
     S->iter = 0;
+    S->bar_count = 0u;
     S->maxit = maxit;
     S->w = w;
     S->rtol = rtol;
@@ -393,6 +394,178 @@ __global__ void cg_pupdate_kernel(CgState* S, const float* R, float* P, int64_t 
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     const int c = static_cast<int>(e % w_pad);
     if (S->active[c]) P[e] = fmaf(static_cast<float>(S->beta[c]), P[e], R[e]);
+  }
+}
+
+// Grid-wide barrier for a cooperative launch.  Writes of the block before the
+// call are visible to every block after it (fence before the arrival, fence
+// after the release).  The wait is bounded by time and by iterations: on
+// timeout the block records kDevTimeout and the caller returns.
+constexpr unsigned long long kBarrierNs = 4000000000ull;
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_barrier(CgState* S) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &S->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    int good = 1;
+    if (atomicAdd(&S->bar_count, 1u) == gridDim.x - 1) {
+      atomicExch(&S->bar_count, 0u);
+      __threadfence();
+      atomicAdd(&S->bar_gen, 1u);
+    } else {
+      const unsigned long long t0 = global_ns();
+      for (long long it = 0; *gen == g; ++it) {
+        if (it >= 16 * kSpinLimit || global_ns() - t0 > kBarrierNs) {
+          atomicExch(&S->err, static_cast<int>(kDevTimeout));
+          good = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// One CG iteration after the product: phase A is cg_epi_alpha (Q and p^T q,
+// reduced in plane 0 of red), phase B cg_update (x, r and r^T r in plane 1),
+// phase C cg_pupdate.  Every block reads the column state once before the
+// first barrier and then derives alpha, beta and the stopping decisions from
+// the same sums in the same order as the separate kernels' last block; block 0
+// alone writes them back.  A thread touches only the rows of its own block, so
+// the vectors need no barrier, only the sums do.
+__global__ void __launch_bounds__(kRedThreads, 4)
+    cg_step_kernel(CgState* S, const float* part_k, int split, float* X, float* R, float* P,
+                   float* Q, int64_t n_pad, int64_t n, int w_pad, double f2, double snoise,
+                   double* red) {
+  if (S->n_active == 0 || S->err == kDevTimeout) return;
+  __shared__ int act_s[kMaxW];
+  __shared__ int it_s[kMaxW];
+  __shared__ double rr_s[kMaxW];
+  __shared__ double coef_s[kMaxW];
+  __shared__ int cnt;
+  const bool writer = blockIdx.x == 0;
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    act_s[c] = S->active[c];
+    it_s[c] = S->iters[c];
+    rr_s[c] = S->rr[c];
+  }
+  if (threadIdx.x == 0) cnt = 0;
+  const double rtol = S->rtol;
+  const int maxit = S->maxit;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  const int64_t plane = n_pad * w_pad;
+  double* red_b = red + static_cast<int64_t>(gridDim.x) * w_pad;
+
+  // A: Q = f^2 sum_s partK + s P on live rows (0 on padding rows); p^T q.
+  double acc[1] = {0.0};
+  if (L.live) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      float q = 0.f;
+      if (r < n) {
+        double sk = 0.0;
+#pragma unroll 4
+        for (int s = 0; s < split; ++s) sk += part_k[s * plane + idx];
+        const double pv = P[idx];
+        const double qd = f2 * sk + snoise * pv;
+        q = static_cast<float>(qd);
+        acc[0] += pv * static_cast<double>(q);
+      }
+      Q[idx] = q;
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!grid_barrier(S)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    const double pap = tot[c];
+    double al = 0.0;
+    if (act_s[c]) {
+      if (!(pap > 0.0) || !isfinite(pap)) {
+        act_s[c] = 0;
+        if (writer) {
+          S->err = kDevBreakdown;
+          S->active[c] = 0;
+        }
+      } else {
+        al = rr_s[c] / pap;
+        if (writer && it_s[c] < kMaxK) S->ahist[it_s[c]][c] = al;
+      }
+    }
+    coef_s[c] = al;
+    if (writer) S->alpha[c] = al;
+  }
+  __syncthreads();
+
+  // B: x += alpha p; r -= alpha q; r^T r.
+  acc[0] = 0.0;
+  if (L.live && act_s[L.c]) {
+    const float al = static_cast<float>(coef_s[L.c]);
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      X[idx] = fmaf(al, P[idx], X[idx]);
+      const float rn = fmaf(-al, Q[idx], R[idx]);
+      R[idx] = rn;
+      acc[0] += static_cast<double>(rn) * rn;
+    }
+  }
+  block_store<1>(acc, L, w_pad, red_b);
+  if (!grid_barrier(S)) return;
+  tot = final_sums(red_b, 1, w_pad);
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    double be = 0.0;
+    if (act_s[c]) {
+      const double rr_new = tot[c];
+      be = rr_new / rr_s[c];
+      const int it = it_s[c];
+      const double rel = sqrt(rr_new / S->bn2[c]);
+      const bool stop = !(rel > rtol) || it + 1 >= maxit || !isfinite(rel);
+      if (writer) {
+        if (it < kMaxK) S->bhist[it][c] = be;
+        S->iters[c] = it + 1;
+        S->rr[c] = rr_new;
+        S->beta[c] = be;
+        S->relres[c] = rel;
+        if (stop) S->active[c] = 0;
+      }
+      if (stop)
+        act_s[c] = 0;
+      else
+        atomicAdd(&cnt, 1);
+    }
+    coef_s[c] = be;
+  }
+  __syncthreads();
+  if (writer && threadIdx.x == 0) {
+    S->n_active = cnt;
+    S->iter = S->iter + 1;
+  }
+
+  // C: p = r + beta p on the columns still iterating.
+  if (L.live && act_s[L.c]) {
+    const float be = static_cast<float>(coef_s[L.c]);
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      P[idx] = fmaf(be, P[idx], R[idx]);
+    }
   }
 }
 
@@ -903,6 +1076,38 @@ cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pa
   cg_pupdate_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, R, P, n_pad, w_pad);
   count_launch();
   return cudaGetLastError();
+}
+
+bool cg_step_fits(int64_t n_pad) {
+  int dev = 0, sms = 0, per_sm = 0, coop = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, cg_step_kernel, kRedThreads, 0) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return coop != 0 && static_cast<int64_t>(red_blocks(n_pad)) <= static_cast<int64_t>(per_sm) * sms;
+}
+
+cudaError_t launch_cg_step(CgState* S, const float* part_k, int split, float* X, float* R, float* P,
+                           float* Q, int64_t n_pad, int64_t n, int w_pad, double f2, double snoise,
+                           double* red, cudaStream_t st) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(red_blocks(n_pad));
+  cfg.blockDim = dim3(kRedThreads);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelEx(&cfg, cg_step_kernel, S, part_k, split, X, R, P, Q, n_pad,
+                                           n, w_pad, f2, snoise, red);
+  count_launch();
+  return e;
 }
 
 cudaError_t launch_lz_init(CgState* S, const float* B, float* Q0, int64_t n_pad, int w_pad, int col0,

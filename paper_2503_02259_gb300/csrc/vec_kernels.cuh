@@ -36,6 +36,8 @@ struct CgState {
   double yalpha;
   double out[16];            // assembled results (see assemble kernel)
   unsigned ticket2;
+  unsigned bar_count;        // grid barrier of the fused CG step: arrivals
+  unsigned bar_gen;          // grid barrier of the fused CG step: generation
 };
 
 // Reduction geometry for the O(n w) kernels.
@@ -88,6 +90,13 @@ cudaError_t launch_cg_update(CgState* S, float* X, float* R, const float* P, con
 // P = R + beta P.
 cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad,
                               cudaStream_t st);
+// The three calls above as one cooperative launch with two grid barriers (the
+// same arithmetic and summation order, so the same bits).  Usable when
+// cg_step_fits(n_pad): every block of the reduction grid can be resident at once.
+bool cg_step_fits(int64_t n_pad);
+cudaError_t launch_cg_step(CgState* S, const float* part_k, int split, float* X, float* R, float* P,
+                           float* Q, int64_t n_pad, int64_t n, int w_pad, double f2, double snoise,
+                           double* red, cudaStream_t st);
 
 // Lanczos with full reorthogonalisation, one independent process per column of
 // a padded [n_pad][w_pad] block (columns [col0, col0 + p) active).

@@ -196,3 +196,43 @@ def test_slq_arithmetic_is_chosen_separately(api, small):
                                  api.solve_opts(nprobe=10, nlanczos=30, seed=1234, prec=0, slq_prec=3))
     assert rel(ld_same, ld_tf) <= 1e-12
     assert rel(ld_tf, est["logdet"]) <= 1e-4
+
+
+# The fused CG step (one cooperative launch with two grid barriers) against the
+# three separate kernels it replaces: same sums in the same order, so the same
+# bits.  Shapes: the small problem (w = 11, 63 reduction blocks), a ragged n,
+# the largest reduction grid (608 blocks, all resident at once), a column
+# that stops at maxit, and the split-TF32 product.
+@pytest.mark.parametrize("n,w,prec,maxit", [(2000, 11, 0, 0), (1037, 5, 0, 0), (20000, 33, 0, 0),
+                                            (3001, 17, 0, 7), (4096, 16, 3, 0)])
+def test_fused_cg_step_equals_separate_kernels(api, monkeypatch, n, w, prec, maxit):
+    import torch
+    prob = inputs.uniform_problem(n, 3, 0, (0.05, 1.0, 0.2), seed=5)
+    Bm = _dev(inputs.multivector(prob.y, w, seed=6))
+    X = _dev(prob.X)
+    opts = api.solve_opts(cg_rtol=1e-7, cg_maxit=maxit, prec=prec)
+    runs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GP_CG_FUSED", flag)
+        Xs, iters, relres, st = api.gp_pcg_solve(X, Bm, prob.kind, prob.theta, opts,
+                                                 raise_not_converged=False)
+        torch.cuda.synchronize()
+        runs.append((Xs.cpu(), iters, relres, st))
+    (xa, ia, ra, sa), (xb, ib, rb, sb) = runs
+    assert sa == sb and ia == ib and ra == rb
+    assert torch.equal(xa, xb)
+    if maxit:
+        assert sa == 4 and max(ia) == maxit
+    elif prec == 0:
+        assert sa == 0 and max(ra) <= 1e-7
+
+
+def test_fused_cg_step_loss_and_grad_bits(api, small, monkeypatch):
+    prob, _, _ = small
+    opts = api.solve_opts(nprobe=10, nlanczos=30, cg_rtol=1e-8, seed=1234)
+    out = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("GP_CG_FUSED", flag)
+        loss, grad, info = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+        out.append((loss, grad, info["cg_iters"]))
+    assert out[0] == out[1]
