@@ -21,20 +21,23 @@ namespace gp {
 #define GP_HD inline
 #endif
 
-// c, s with [c s; -s c]^T [x; z] = [r; 0].
+// c, s with [c s; -s c]^T [x; z] = [r; 0], r = sqrt(x^2 + z^2): c = x / r,
+// s = -z / r from one reciprocal hypotenuse (an FP64 division or square root is
+// a long dependent instruction sequence, and this sits on the serial path of
+// every rotation).
 GP_HD void givens_cs(double x, double z, double& c, double& s) {
   if (z == 0.0) {
     c = 1.0;
     s = 0.0;
-  } else if (fabs(z) > fabs(x)) {
-    const double tau = -x / z;
-    s = 1.0 / sqrt(1.0 + tau * tau);
-    c = s * tau;
-  } else {
-    const double tau = -z / x;
-    c = 1.0 / sqrt(1.0 + tau * tau);
-    s = c * tau;
+    return;
   }
+#ifdef __CUDA_ARCH__
+  const double r = rhypot(x, z);
+#else
+  const double r = 1.0 / hypot(x, z);
+#endif
+  c = x * r;
+  s = -z * r;
 }
 
 // a[0..m-1]: diagonal (overwritten by the eigenvalues); b[0..m-2]: off-diagonal

@@ -686,10 +686,11 @@ __global__ void lz_dots_kernel(CgState* S, const float* W, const float* Q, int64
   int64_t r0, r1;
   block_rows(n_pad, r0, r1);
   const int64_t plane = n_pad * w_pad;
-  __shared__ double sm[kRedThreads];
   // Eight basis vectors per pass: their loads are independent, so they are in
-  // flight together instead of one round trip per basis vector.
+  // flight together instead of one round trip per basis vector; the block sums
+  // of the eight are then formed by eight groups of threads at once.
   constexpr int kChunk = 8;
+  __shared__ double sm[kChunk][kRedThreads];
   for (int i0 = 0; i0 < nq; i0 += kChunk) {
     double acc[kChunk];
 #pragma unroll
@@ -705,17 +706,17 @@ __global__ void lz_dots_kernel(CgState* S, const float* W, const float* Q, int64
       }
     }
 #pragma unroll
-    for (int k = 0; k < kChunk; ++k) {
-      if (i0 + k >= nq) break;
-      sm[threadIdx.x] = L.live ? acc[k] : 0.0;
-      __syncthreads();
-      if (threadIdx.x < w_pad) {
-        double sum = 0.0;
-        for (int q = 0; q < L.nrl; ++q) sum += sm[q * w_pad + threadIdx.x];
-        red[(static_cast<int64_t>(i0 + k) * gridDim.x + blockIdx.x) * w_pad + threadIdx.x] = sum;
-      }
-      __syncthreads();
+    for (int k = 0; k < kChunk; ++k) sm[k][threadIdx.x] = L.live ? acc[k] : 0.0;
+    __syncthreads();
+    const int nk = min(kChunk, nq - i0);
+    for (int t = threadIdx.x; t < nk * w_pad; t += blockDim.x) {
+      const int k = t / w_pad;
+      const int c = t - k * w_pad;
+      double sum = 0.0;
+      for (int q = 0; q < L.nrl; ++q) sum += sm[k][q * w_pad + c];
+      red[(static_cast<int64_t>(i0 + k) * gridDim.x + blockIdx.x) * w_pad + c] = sum;
     }
+    __syncthreads();
   }
   if (!last_block(&S->ticket)) return;
   for (int t = threadIdx.x; t < nq * w_pad; t += blockDim.x) {
@@ -788,7 +789,9 @@ __global__ void slq_kernel(CgState* S, int col0, int p, int k) {
     const int c = col0 + i;
     int m = S->iters[c];
     if (m > k) m = k;
-    double a[kMaxK], b[kMaxK], q[kMaxK];
+    // The QR sweeps' working arrays in shared memory (shorter latency than the
+    // local-memory stack frame on their serial path).
+    __shared__ double a[kMaxK], b[kMaxK], q[kMaxK];
     bool ok = true;
     const double v = lanczos_logquad(&S->ahist[0][c], &S->bhist[0][c], kMaxW, m, S->bn2[c], a, b,
                                      q, &ok);
