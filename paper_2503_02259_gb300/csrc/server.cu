@@ -29,56 +29,13 @@
 #include <vector>
 
 #include "gp_api_internal.h"
+#include "admission.h"
 
 namespace {
 
-constexpr size_t kAlign = 256;
-
-size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
-
-// First-fit allocator over [0, size) of the pool, with coalescing frees.
-class PoolAllocator {
- public:
-  explicit PoolAllocator(size_t size) : size_(size) { free_[0] = size; }
-  bool alloc(size_t bytes, size_t* off) {
-    bytes = align_up(bytes);
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second >= bytes) {
-        *off = it->first;
-        const size_t rest = it->second - bytes;
-        const size_t start = it->first + bytes;
-        free_.erase(it);
-        if (rest > 0) free_[start] = rest;
-        in_use_ += bytes;
-        return true;
-      }
-    }
-    return false;
-  }
-  void release(size_t off, size_t bytes) {
-    bytes = align_up(bytes);
-    in_use_ -= bytes;
-    auto it = free_.emplace(off, bytes).first;
-    auto next = std::next(it);
-    if (next != free_.end() && it->first + it->second == next->first) {
-      it->second += next->second;
-      free_.erase(next);
-    }
-    if (it != free_.begin()) {
-      auto prev = std::prev(it);
-      if (prev->first + prev->second == it->first) {
-        prev->second += it->second;
-        free_.erase(it);
-      }
-    }
-  }
-  size_t in_use() const { return in_use_; }
-
- private:
-  size_t size_;
-  size_t in_use_ = 0;
-  std::map<size_t, size_t> free_;
-};
+using gp::sched::align_up;
+using gp::sched::kAlign;
+using gp::sched::PoolAllocator;
 
 // Device sub-buffers of one request inside its pool block.
 struct JobLayout {
@@ -239,57 +196,22 @@ void run_job(gp_server* srv, Job& j, char* base, cudaStream_t st) {
   (void)srv;
 }
 
-// Entries x columns of the products a request issues (its CG, Lanczos and
-// gradient passes, or its CG and the prediction product).
-double request_work(const gp_request& r) {
-  const double n = static_cast<double>(r.n);
-  const int maxit = r.cg_maxit > 0 ? r.cg_maxit : 1000;
-  if (r.kind == 0) {
-    const int k = r.nlanczos > 0 ? r.nlanczos : 20;
-    return n * n * (1.0 + r.nprobe) * (maxit + k + 1);
-  }
-  return n * n * maxit + n * static_cast<double>(r.m);
-}
+using gp::sched::kAgeSeconds;
+using gp::sched::priority_level;
+using gp::sched::request_work;
 
-// Stream priority level (0 = highest) of a request: one level per decade of
-// work above 1e9 entries x columns, clamped to the levels the device offers.
-int priority_level(const gp_request& r, int levels) {
-  const double w = request_work(r);
-  int b = 0;
-  for (double t = 1e10; w >= t && b < levels - 1; t *= 10.0) ++b;
-  return b;
-}
-
-// Waiting time after which a queued request is admitted before any younger one
-// (bounds how long the least-work-first order can hold a large request back).
-constexpr double kAgeSeconds = 30.0;
-
-// Called with srv->mu held: picks the next request to admit and reserves its
-// pool block (returns false if none can start now).  The oldest request goes
-// first once it has waited kAgeSeconds (it waits for room if it does not fit);
-// otherwise the request with the least work that fits.
+// Called with srv->mu held: picks the next request to admit by the rule of
+// gp::sched::pick_next and reserves its pool block (returns false if none can
+// start now).
 bool admit_next(gp_server* srv, std::shared_ptr<Job>* job, size_t* off) {
   auto& q = srv->queue;
-  if (q.empty()) return false;
-  const double now = seconds_since(srv->t0);
-  if (now - q.front()->res.t_submit_s >= kAgeSeconds) {
-    if (!srv->alloc->alloc(q.front()->lay.total, off)) return false;
-    *job = q.front();
-    q.pop_front();
-    return true;
-  }
-  std::vector<size_t> order(q.size());
-  for (size_t i = 0; i < q.size(); ++i) order[i] = i;
-  std::stable_sort(order.begin(), order.end(),
-                   [&](size_t a, size_t b) { return q[a]->work < q[b]->work; });
-  for (size_t i : order) {
-    if (srv->alloc->alloc(q[i]->lay.total, off)) {
-      *job = q[i];
-      q.erase(q.begin() + static_cast<std::ptrdiff_t>(i));
-      return true;
-    }
-  }
-  return false;
+  const long i = gp::sched::pick_next(
+      q.size(), seconds_since(srv->t0), *srv->alloc, [&](size_t k) { return q[k]->work; },
+      [&](size_t k) { return q[k]->res.t_submit_s; }, [&](size_t k) { return q[k]->lay.total; }, off);
+  if (i < 0) return false;
+  *job = q[static_cast<size_t>(i)];
+  q.erase(q.begin() + i);
+  return true;
 }
 
 void worker_main(gp_server* srv) {
