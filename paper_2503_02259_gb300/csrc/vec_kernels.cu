@@ -1,7 +1,8 @@
 // O(n w) kernels around the on-the-fly product: staging, epilogues, block CG
 // (per-column CG with FP64 step scalars), probe generation, SLQ and the
 // loss/gradient assembly.  All reductions are deterministic: per-block FP64
-// partials in a fixed order, summed by the last block to finish.
+// partials in a fixed order, summed by the last block to finish (or, in the
+// fused CG step, by every block after a grid barrier, in the same order).
 #include <math.h>
 
 #include <algorithm>
@@ -83,7 +84,8 @@ __device__ __forceinline__ double final_sum(const double* red, int q, int c, int
   return s;
 }
 
-// Called by every thread of the last block: the sums over the grid's blocks of
+// Called by every thread of a block that has seen all partials (the last block
+// to finish, or any block after a grid barrier): the sums over the grid's blocks of
 // red[q][b][c] for q < nq (<= 3), c < w_pad, into shared memory (index
 // q * w_pad + c).  With np = nq * w_pad pairs, lane l of the blockDim / np lanes
 // of a pair adds blocks l, l + lanes, ...; the lanes are then added in lane
