@@ -578,12 +578,19 @@ def main() -> int:
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        extras["loss_grad"] = loss_grad_small(api, torch)
-        extras["precision_modes"] = precision_modes(api, B, torch, prob, X, V, dev)
-        extras["precision_config"] = precision_config(api, B, torch, dev)
-        extras["refinement"] = refinement(api, torch)
-        extras["loss_grad_mixed_vs_fp32"] = loss_grad_mixed_vs_fp32(api, torch)
-        extras["serving"] = serving(torch, count=args.serving_requests)
+        # Each extra leg runs after the headline measurement; a leg that fails
+        # records its error in the line instead of taking the line with it.
+        legs = (("loss_grad", lambda: loss_grad_small(api, torch)),
+                ("precision_modes", lambda: precision_modes(api, B, torch, prob, X, V, dev)),
+                ("precision_config", lambda: precision_config(api, B, torch, dev)),
+                ("refinement", lambda: refinement(api, torch)),
+                ("loss_grad_mixed_vs_fp32", lambda: loss_grad_mixed_vs_fp32(api, torch)),
+                ("serving", lambda: serving(torch, count=args.serving_requests)))
+        for name, leg in legs:
+            try:
+                extras[name] = leg()
+            except Exception as exc:  # noqa: BLE001 - reported in the JSON line
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"[:500]}
 
     if rank != 0:
         if dist:
