@@ -152,3 +152,36 @@ def test_device_gauss_quadrature_host_build_matches_lapack_rule(tri):
                  ctypes.c_double(150.0))
     ref = O.gauss_quadrature_log(a, b, 150.0)
     assert v == pytest.approx(ref, rel=1e-11)
+
+
+@pytest.mark.parametrize("d,kind,theta,k", [
+    (3, 0, (0.1, 1.0, 0.3), 30),     # the small problem's kernel and SLQ length
+    (2, 0, (0.01, 1.0, 0.05), 40),   # the ill-conditioned precision problem's kernel
+    (3, 1, (0.05, 1.5, 0.2), 30),    # Matern-3/2 of the product workload
+    (8, 0, (0.1, 1.0, 1.2), 40),     # the differentiation problem's kernel (d = 8)
+])
+def test_device_gauss_quadrature_on_workload_lanczos_matrices(tri, d, kind, theta, k):
+    # Lanczos matrices of the workloads' kernels (n = 1500 stand-ins), several
+    # probes each: the device's Gauss rule (host build) against LAPACK's, and
+    # its exact response to scaling T by c, which adds ||z||^2 log c (the first
+    # components sum to one) and must not under- or overflow.
+    import oracle as O
+    from paper_2503_02259_gb300 import inputs
+    n = 1500
+    X = inputs.points(n, d, seed=11 + d).astype(np.float64)
+    if d == 8:
+        X = 0.5 * np.random.default_rng(5).standard_normal((n, d))
+    A = O.khat_dense(X, kind, theta)
+    Z = O.rademacher_probes(n, 3, 21)
+    tri.quad.restype = ctypes.c_double
+    vp = ctypes.c_void_p
+    for i in range(3):
+        a, b = O.lanczos(A, Z[:, i], k)
+        bb = np.append(b, 0.0)
+        v = tri.quad(vp(a.ctypes.data), vp(bb.ctypes.data), a.size, ctypes.c_double(n))
+        ref = O.gauss_quadrature_log(a, b, float(n))
+        assert v == pytest.approx(ref, rel=1e-11, abs=1e-9 * n)
+        for c in (1e-150, 1e150):
+            ac, bc = a * c, np.append(b * c, 0.0)
+            vc = tri.quad(vp(ac.ctypes.data), vp(bc.ctypes.data), a.size, ctypes.c_double(n))
+            assert vc == pytest.approx(v + n * np.log(c), rel=1e-11, abs=1e-9 * n)
