@@ -345,6 +345,13 @@ def test_est_nll_approaches_exact():
     assert abs(es["logdet"] - ex["logdet"]) < 3 * sig_ld
     sig_tr = es["trace_probes"].std(axis=1, ddof=1) / 16.0
     assert np.all(np.abs(es["trace"] - ex["trace"]) < 3 * sig_tr + 1e-10)
+    # The estimator's loss and gradient differ from the exact ones only through
+    # the two estimated terms: L~ - L = (logdet~ - logdet) / 2 and
+    # g~ - g = (tr~ - tr) / 2 (the paper's NLL and gradient equations).
+    assert es["loss"] - ex["loss"] == pytest.approx(0.5 * (es["logdet"] - ex["logdet"]),
+                                                    abs=1e-9 * abs(ex["loss"]))
+    np.testing.assert_allclose(es["grad"] - ex["grad"], 0.5 * (es["trace"] - ex["trace"]),
+                               atol=1e-9 * np.abs(ex["grad"]).max())
 
 
 # -------------------------------------------------------------------- CG --
@@ -393,3 +400,36 @@ def test_planted_transposed_cross_product_is_caught(monkeypatch):
     monkeypatch.setattr(O.gp_oracle, "sqdist", lambda A, B: orig(B, A).T * 1.0001)
     with pytest.raises(AssertionError):
         test_kmv_rows_brute_force(O.GAUSSIAN)
+
+
+def test_planted_first_column_quadrature_is_caught(monkeypatch):
+    # Weights from the first column of the eigenvector matrix instead of the first row.
+    def wrong(a, b, znorm2):
+        if a.size == 1:
+            return znorm2 * math.log(a[0])
+        lam, U = sla.eigh_tridiagonal(a, b)
+        return znorm2 * float(np.sum(U[:, 0] ** 2 * np.log(lam)))
+    monkeypatch.setattr(O.gp_oracle, "gauss_quadrature_log", wrong)
+    monkeypatch.setattr(O, "gauss_quadrature_log", wrong)
+    with pytest.raises(AssertionError):
+        test_lanczos_full_length_equals_matrix_log()
+
+
+def test_planted_normalised_probes_in_slq_are_caught(monkeypatch):
+    # ||z||^2 dropped from the SLQ value (probes taken as unit vectors).
+    good = O.gp_oracle.gauss_quadrature_log
+    monkeypatch.setattr(O.gp_oracle, "gauss_quadrature_log", lambda a, b, z2: good(a, b, 1.0))
+    with pytest.raises(AssertionError):
+        test_slq_converges_to_logdet_within_3_sigma()
+
+
+def test_planted_trace_sign_in_estimated_gradient_is_caught(monkeypatch):
+    orig_est = O.gp_oracle.est_nll
+    def est_wrong(X, y, kind, theta, Z, k):
+        out = orig_est(X, y, kind, theta, Z, k)
+        out["grad"] = 0.5 * (-out["quad"] - out["trace"])
+        return out
+    monkeypatch.setattr(O.gp_oracle, "est_nll", est_wrong)
+    monkeypatch.setattr(O, "est_nll", est_wrong)
+    with pytest.raises(AssertionError):
+        test_est_nll_approaches_exact()
