@@ -97,7 +97,7 @@ typedef enum {
   GP_OP_SLQ = 3,          /* gp_slq_logdet */
   GP_OP_LOSS_GRAD = 4,    /* gp_loss_and_grad, gp_nll_forward, gp_nll_backward */
   GP_OP_PREDICT = 5,      /* gp_predict_mean */
-  GP_OP_RESIDUAL = 6      /* gp_true_residual */
+  GP_OP_RESIDUAL = 6      /* gp_true_residual, gp_residual_rows */
 } gp_op;
 
 /* Theta = (s, f, l): noise s, scale f, length-scale l (§Gaussian Processes). */
@@ -133,7 +133,10 @@ typedef struct {
  *              GP_PREC_SAME for `prec`.  Zero-initialised options run SLQ in
  *              FP32.  The log-determinant of a smooth, ill-conditioned K-hat
  *              needs kernel entries to about 24 bits (FP32 or TF32X3), while
- *              the CG solves tolerate BF16X3, so the two may differ. */
+ *              the CG solves tolerate BF16X3, so the two may differ.
+ *  refine_residual: arithmetic of the refinement's outer residual
+ *              (gp_residual_arith; zero-initialised options select the
+ *              compensated FP32-pair form). */
 typedef struct {
   int32_t nprobe;
   int32_t nlanczos;
@@ -145,10 +148,20 @@ typedef struct {
   const float* probes;
   int32_t refine_maxit;
   int32_t slq_prec;
+  int32_t refine_residual;
 } gp_solve_opts;
 
 /* slq_prec value meaning "the same arithmetic as prec". */
 #define GP_PREC_SAME (-1)
+
+/* Arithmetic of the O(n^2 w) sums of a residual B - Kh X (X in FP64).
+ *  PAIR: FP32-pair ("double-float") arithmetic on the FP32 pipe: exact
+ *        differences of the FP32 points, kernel entries by a table-driven pair
+ *        exponential (Tang's method) and pair square root, pair products and
+ *        compensated sums; about 1e-14 relative per kernel entry.
+ *  FP64: FP64 kernel entries and sums (GB300's FP64 pipe is far slower; kept
+ *        as the checker). */
+typedef enum { GP_RESIDUAL_PAIR = 0, GP_RESIDUAL_FP64 = 1 } gp_residual_arith;
 
 /* Diagnostics of one loss/gradient evaluation (host struct, filled on GP_OK). */
 typedef struct {
@@ -235,34 +248,53 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
                        const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                        size_t ws_bytes, void* stream);
 
-/* Mixed-precision iterative refinement of Kh Xsol = B with an FP64 solution.
- * Outer loop: R = B - Kh X with FP64 kernel entries and FP64 sums from the FP32
- * points, X held in FP64; inner loop: block CG on the product of precision
- * opts->prec (a tensor-core mode, or FP32) for Kh D = R to opts->cg_rtol, then
- * X += D; stop each column at ||R|| / ||B|| <= opts->refine_rtol or after
- * opts->refine_maxit outer steps.  B: device n x w float32; X64: device n x w
- * float64 (returning the refined solution in FP32 would cost about
- * u ||Kh|| ||X|| / ||B|| of residual).  iters[w]: total inner CG iterations;
- * relres[w]: final outer relative residual (FP64).  Workspace:
- * gp_workspace_bytes(GP_OP_PCG, prob, w, opts) with opts->refine_rtol > 0.
- * The FP64 residual is O(n^2 w) FP64 work per outer step.  Synchronises. */
 /* True relative residual of a solution: relres[c] = ||B_c - Kh X_c||_2 / ||B_c||_2
- * for each column c < w, with FP64 kernel entries and FP64 sums (the outer
- * residual of gp_pcg_solve_refined), e.g. to check the FP32 solution of
+ * for each column c < w, with FP64 kernel entries and FP64 sums (the checker
+ * of the refinement's residual), e.g. to check the FP32 solution of
  * gp_pcg_solve.  B, X: device n x w float32; relres[w]: host.  Workspace:
  * gp_workspace_bytes(GP_OP_RESIDUAL, prob, w, NULL).  O(n^2 w) FP64 work.
  * Synchronises. */
 gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* X, int32_t w,
                            double* relres, void* ws, size_t ws_bytes, void* stream);
 
+/* Residual rows of an FP64 solution: R[k][c] = B[r_k][c] - (Kh X64)[r_k][c]
+ * for k < m, c < w, where r_k = rows[k] (rows: device int64 array of m
+ * indices in [0, n)) or r_k = k when rows is NULL; the sum over all n points
+ * in the arithmetic `arith` (gp_residual_arith).  This is the outer residual
+ * of mixed-precision iterative refinement (§Gaussian Processes, PCG; the
+ * paper's own arithmetic is FP32), exposed so that a caller can measure it
+ * on all rows or on sampled rows.  B: device n x w float32; X64: device
+ * n x w float64; R: device m x w float64 (may be NULL); relres: host [w]
+ * (may be NULL, not both), ||R_c||_2 / ||B_{rows,c}||_2.  1 <= m <= n.
+ * Workspace: gp_workspace_bytes(GP_OP_RESIDUAL, prob, w, NULL) serves any m.
+ * GP_ERR_ARG if a row index is out of range (R then holds NaN in that row).
+ * Synchronises. */
+gp_status gp_residual_rows(const gp_problem* prob, const float* B, const double* X64, int32_t w,
+                           const int64_t* rows, int64_t m, int32_t arith, double* R,
+                           double* relres, void* ws, size_t ws_bytes, void* stream);
+
+/* Mixed-precision iterative refinement of Kh Xsol = B with an FP64 solution
+ * (PCG of §Gaussian Processes with M = I, refined).  Outer loop: R = B - Kh X
+ * with X held in FP64 and the sums in the arithmetic opts->refine_residual
+ * (default: compensated FP32 pairs; the kernel entries never leave the FP32
+ * pipe); inner loop: block CG on the product of precision opts->prec (a
+ * tensor-core mode, or FP32) for Kh D = R to opts->cg_rtol, then X += D; stop
+ * each column at ||R|| / ||B|| <= opts->refine_rtol or after
+ * opts->refine_maxit outer steps.  B: device n x w float32; X64: device n x w
+ * float64 (returning the refined solution in FP32 would cost about
+ * u ||Kh|| ||X|| / ||B|| of residual).  iters[w]: total inner CG iterations;
+ * relres[w]: final outer relative residual.  Workspace:
+ * gp_workspace_bytes(GP_OP_PCG, prob, w, opts) with opts->refine_rtol > 0.
+ * Synchronises. */
 gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w, double* X64,
                                const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                                size_t ws_bytes, void* stream);
 
 /* SLQ estimate of log|Kh| (Eq. 1 with M = I; stochastic Lanczos quadrature):
- * the Lanczos tridiagonal T_k of each probe z_i is read off the first k CG
- * step coefficients of the column z_i, eigen-decomposed on the device in FP64,
- * and logdet = (1/p) sum_i ||z_i||^2 sum_j U_1j^2 log(lambda_j).
+ * k steps of Lanczos with full reorthogonalisation from q_1 = z_i / ||z_i||
+ * for each probe z_i (FP64 coefficients, products in opts->slq_prec), the
+ * tridiagonal T_k eigen-decomposed on the device in FP64 (implicit QR), and
+ * logdet = (1/p) sum_i ||z_i||^2 sum_j U_1j^2 log(lambda_j).
  * logdet_stderr = sample std / sqrt(p).  Synchronises `stream`. */
 gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, double* logdet,
                         double* logdet_stderr, void* ws, size_t ws_bytes, void* stream);

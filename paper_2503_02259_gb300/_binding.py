@@ -42,6 +42,9 @@ OP_LOSS_GRAD = 4
 OP_PREDICT = 5
 OP_RESIDUAL = 6
 
+RESIDUAL_PAIR = 0   # compensated FP32-pair sums (the refinement default)
+RESIDUAL_FP64 = 1   # FP64 entries and sums (the checker)
+
 MAX_DIM = 16
 MAX_COLS = 128
 MAX_LANCZOS = 64
@@ -60,7 +63,7 @@ class gp_solve_opts(ctypes.Structure):
     _fields_ = [("nprobe", c_int32), ("nlanczos", c_int32), ("cg_maxit", c_int32),
                 ("prec", c_int32), ("cg_rtol", c_double), ("refine_rtol", c_double),
                 ("seed", c_uint64), ("probes", c_void_p), ("refine_maxit", c_int32),
-                ("slq_prec", c_int32)]
+                ("slq_prec", c_int32), ("refine_residual", c_int32)]
 
 
 class gp_loss_info(ctypes.Structure):
@@ -115,6 +118,9 @@ PROTOTYPES = {
                                        c_void_p, c_size_t, c_void_p]),
     "gp_true_residual": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int32,
                                    POINTER(c_double), c_void_p, c_size_t, c_void_p]),
+    "gp_residual_rows": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int32, c_void_p,
+                                   c_int64, c_int32, c_void_p, POINTER(c_double), c_void_p,
+                                   c_size_t, c_void_p]),
     "gp_slq_logdet": (c_int32, [POINTER(gp_problem), POINTER(gp_solve_opts), POINTER(c_double),
                                 POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "gp_loss_and_grad": (c_int32, [POINTER(gp_problem), c_void_p, POINTER(gp_solve_opts),

@@ -44,13 +44,15 @@ def problem(X: torch.Tensor, kernel: int, theta) -> tuple[B.gp_problem, torch.Te
 def solve_opts(nprobe: int = 0, nlanczos: int = 30, cg_maxit: int = 0, cg_rtol: float = 1e-8,
                seed: int = 0, prec: int = B.PREC_FP32, refine_rtol: float = 0.0,
                probes: torch.Tensor | None = None, refine_maxit: int = 0,
-               slq_prec: int = B.PREC_FP32) -> B.gp_solve_opts:
+               slq_prec: int = B.PREC_FP32,
+               refine_residual: int = B.RESIDUAL_PAIR) -> B.gp_solve_opts:
     """gp_solve_opts; slq_prec is the arithmetic of the SLQ Lanczos products
-    (B.PREC_SAME: the same as prec)."""
+    (B.PREC_SAME: the same as prec); refine_residual the arithmetic of the
+    refinement's outer residual (B.RESIDUAL_PAIR or B.RESIDUAL_FP64)."""
     return B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
                            float(refine_rtol), int(seed) & (2**64 - 1),
                            0 if probes is None else probes.data_ptr(), int(refine_maxit),
-                           int(slq_prec))
+                           int(slq_prec), int(refine_residual))
 
 
 def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None, device) -> torch.Tensor:
@@ -156,6 +158,40 @@ def gp_true_residual(X, Bm, Xsol, kernel, theta, ws=None) -> list:
     check(lib().gp_true_residual(byref(prob), _ptr(Bm), _ptr(Xsol), w, relres, _ptr(ws), ws.numel(),
                                  _stream(X.device)), "gp_true_residual")
     return list(relres)
+
+
+def gp_residual_rows(X, Bm, X64, kernel, theta, rows=None, m=None, arith=B.RESIDUAL_PAIR,
+                     ws=None, want_rows=True):
+    """Residual rows R = B[rows] - (Kh X64)[rows] (FP64, (m, w)) and the
+    per-column ||R_c|| / ||B_rows,c||, in the arithmetic `arith`.  rows: device
+    int64 indices, or None for the first m rows (all n when m is None)."""
+    prob, X = problem(X, kernel, theta)
+    Bm = _f32(Bm, "B")
+    if Bm.dim() == 1:
+        Bm = Bm[:, None]
+    if not X64.is_cuda or X64.dtype != torch.float64:
+        raise ValueError("X64 must be a float64 CUDA tensor")
+    X64 = X64.contiguous()
+    if X64.dim() == 1:
+        X64 = X64[:, None]
+    n, w = Bm.shape
+    if X64.shape != (n, w):
+        raise ValueError("B and X64 must have the same shape")
+    if rows is not None:
+        if not rows.is_cuda or rows.dtype != torch.int64:
+            raise ValueError("rows must be an int64 CUDA tensor")
+        rows = rows.contiguous()
+        m = rows.numel()
+    elif m is None:
+        m = n
+    R = torch.empty((m, w), dtype=torch.float64, device=X.device) if want_rows else None
+    relres = (c_double * w)()
+    if ws is None:
+        ws = workspace(B.OP_RESIDUAL, prob, w, None, X.device)
+    check(lib().gp_residual_rows(byref(prob), _ptr(Bm), _ptr(X64), w, _ptr(rows), int(m),
+                                 int(arith), _ptr(R), relres, _ptr(ws), ws.numel(),
+                                 _stream(X.device)), "gp_residual_rows")
+    return R, list(relres)
 
 
 def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts, ws=None):

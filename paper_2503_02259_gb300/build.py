@@ -35,6 +35,8 @@ UNITS = SIMT_UNITS + [
     ("kmv_tc_m3", "kmv_tc_inst.cu", ["-DGP_TC_MODE=3"]),
     ("kmv_tc_m4", "kmv_tc_inst.cu", ["-DGP_TC_MODE=4"]),
     ("vec_kernels", "vec_kernels.cu", []),
+    ("residual", "residual.cu", []),
+    ("residual_pair", "residual_pair.cu", []),
     ("server", "server.cu", []),
     ("static_scratch", "static_scratch.cu", []),
     ("microbench", "microbench.cu", []),

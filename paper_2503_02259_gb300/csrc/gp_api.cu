@@ -18,6 +18,7 @@
 
 #include "gp_api_internal.h"
 #include "kmv_tc.cuh"
+#include "residual.cuh"
 #include "vec_kernels.cuh"
 
 namespace gp {
@@ -828,25 +829,30 @@ static gp_status check_conv(const CgState* S, int w, int maxit, double rtol, cud
 }
 
 // ---------------------------------------------------------------------------
-// Mixed-precision iterative refinement.  Outer loop: r = B - Kh x with FP64
-// kernel entries and sums (x in FP64); stop when ||r_c|| / ||B_c|| <=
-// refine_rtol for every column.  Inner loop: block CG on the tensor-core
-// product (opts->prec) for Kh d = r to opts->cg_rtol; x += d.
-// Workspace: the solver workspace of the inner CG, then x (FP64), r (FP64) and
-// the padded right-hand side (FP32).
+// Mixed-precision iterative refinement.  Outer loop: r = B - Kh x with x in
+// FP64 and the O(n^2 w) sums in FP32-pair arithmetic (or FP64, on request);
+// stop when ||r_c|| / ||B_c|| <= refine_rtol for every column.  Inner loop:
+// block CG on the product of arithmetic opts->prec for Kh d = r to
+// opts->cg_rtol; x += d.
+// Workspace: the solver workspace of the inner CG, then x (FP64), r (FP64),
+// the padded right-hand side (FP32), the residual's split partial sums (FP64)
+// and its error word.
 // ---------------------------------------------------------------------------
 static size_t refine_extra_offset(const SimtPlan& pc, int prec) {
   return (carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes + 255) &
          ~static_cast<size_t>(255);
 }
 
-static size_t refine_bytes(const SimtPlan& pc, int prec) {
+static size_t refine_bytes(const SimtPlan& pc, int prec, int64_t n, int w) {
   const size_t plane = static_cast<size_t>(pc.nr_pad) * pc.w_pad;
-  return refine_extra_offset(pc, prec) + 2 * plane * sizeof(double) + plane * sizeof(float) + 1024;
+  size_t off = refine_extra_offset(pc, prec) + 2 * plane * sizeof(double) + plane * sizeof(float);
+  off = (off + 255) & ~static_cast<size_t>(255);
+  return off + residual_part_bytes_bound(n, w) + 1024;
 }
 
-// Workspace of gp_true_residual: x (FP64), r (FP64), padded B, padded X and the
-// FP32 residual (all [n_pad][w_pad]), reduction scratch and one CgState.
+// Workspace of the residual calls: x (FP64), r (FP64), padded B, padded X and
+// the FP32 residual (all [n_pad][w_pad]), reduction scratch, one CgState, the
+// split partial sums of the residual kernel and an error word.
 struct ResidualWs {
   double* x64;
   double* r64;
@@ -855,10 +861,14 @@ struct ResidualWs {
   float* rf;
   double* red;
   CgState* S;
+  double* part;
+  int* err;
   size_t bytes;
 };
 
-static ResidualWs carve_residual(void* ws, int64_t n_pad, int w_pad) {
+static ResidualWs carve_residual(void* ws, int64_t n, int w) {
+  const int64_t n_pad = round_up(n, kPad);
+  const int w_pad = static_cast<int>(round_up(w, 4));
   Carve c(ws);
   ResidualWs r;
   const size_t plane = static_cast<size_t>(n_pad) * w_pad;
@@ -869,8 +879,40 @@ static ResidualWs carve_residual(void* ws, int64_t n_pad, int w_pad) {
   r.rf = c.take<float>(plane);
   r.red = c.take<double>(red_doubles(n_pad, w_pad));
   r.S = c.take<CgState>(1);
+  r.part = c.take<double>(residual_part_bytes_bound(n, w) / sizeof(double));
+  r.err = c.take<int>(64);
   r.bytes = c.off + 256;
   return r;
+}
+
+static int residual_arith(int abi) { return abi == GP_RESIDUAL_FP64 ? kResF64 : kResPair; }
+
+// R = B - Kh x64 over rows (NULL: 0..m-1) into the padded plane R [m_pad][ldr];
+// Bg (may be NULL) receives the B rows in the same layout.
+static gp_status residual_into(const gp_problem* prob, const float* B, int64_t ldb, const double* x64,
+                               int64_t ldx, int w, const int64_t* rows, int64_t m, int arith,
+                               double* part, int* err, double* R, int ldr, float* Bg,
+                               cudaStream_t st) {
+  const ResPlan p = plan_residual(m, prob->n, w);
+  ResArgs a{};
+  a.X = prob->X;
+  a.n = prob->n;
+  a.d = prob->d;
+  a.kernel = prob->kernel;
+  a.rows = rows;
+  a.m = m;
+  a.x64 = x64;
+  a.ldx = ldx;
+  a.w = w;
+  a.part = part;
+  const double l = prob->theta.l;
+  a.kc64 = prob->kernel == GP_KERNEL_GAUSSIAN ? 1.0 / (2.0 * l * l) : sqrt(3.0) / l;
+  a.kc = pa::kernel_pair_const(prob->kernel, l);
+  a.err = err;
+  ResidualCall c{arith, B, ldb, prob->theta.f * prob->theta.f, prob->theta.s, R, ldr, Bg};
+  GP_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+  GP_CUDA(launch_residual(p, a, c, st));
+  return GP_OK;
 }
 
 gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float* Xsol, double* X64,
@@ -882,7 +924,7 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
   SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
   unify_width(pc, pg);   // the widths setup_solve uses
-  if ((s = check_ws(ws, ws_bytes, refine_bytes(pc, prec))) != GP_OK) return s;
+  if ((s = check_ws(ws, ws_bytes, refine_bytes(pc, prec, n, w))) != GP_OK) return s;
   SolveSetup ss;
   if ((s = setup_solve(prob, w, false, prec, 0, prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
   const size_t plane = static_cast<size_t>(ss.pc.nr_pad) * ss.pc.w_pad;
@@ -890,18 +932,24 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   double* x64 = reinterpret_cast<double*>(extra);
   double* r64 = x64 + plane;
   float* Bp = reinterpret_cast<float*>(r64 + plane);
+  const size_t part_off =
+      ((refine_extra_offset(ss.pc, prec) + 2 * plane * sizeof(double) + plane * sizeof(float)) + 255) &
+      ~static_cast<size_t>(255);
+  double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + part_off);
+  int* rerr = reinterpret_cast<int*>(reinterpret_cast<char*>(part) + residual_part_bytes_bound(n, w));
+  const int arith = residual_arith(opts->refine_residual);
   GP_CUDA(cudaMemsetAsync(x64, 0, 2 * plane * sizeof(double), st));
   GP_CUDA(cudaMemsetAsync(Bp, 0, plane * sizeof(float), st));
   GP_CUDA(cudaMemsetAsync(ss.W.S2, 0, sizeof(CgState), st));
   GP_CUDA(launch_pad_block(B, n, w, w, Bp, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
-  const double f2 = prob->theta.f * prob->theta.f;
   const int max_outer = opts->refine_maxit > 0 ? opts->refine_maxit : 10;
   const int inner_maxit = effective_maxit(prob, opts);
   std::vector<int> total_iters(w, 0);
   HostCg hr;
   for (int outer = 0;; ++outer) {
-    GP_CUDA(launch_refine_residual(prob->X, n, prob->d, prob->kernel, prob->theta.l, f2,
-                                   prob->theta.s, x64, Bp, r64, ss.pc.nr_pad, ss.pc.w_pad, w, st));
+    if ((s = residual_into(prob, Bp, ss.pc.w_pad, x64, ss.pc.w_pad, w, nullptr, n, arith, part, rerr,
+                           r64, ss.pc.w_pad, nullptr, st)) != GP_OK)
+      return s;
     GP_CUDA(launch_refine_norms(ss.W.S2, r64, Bp, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, w, ss.W.red, st));
     if ((s = read_cg(ss.W.S2, hr, st)) != GP_OK) return s;
     bool done = true;
@@ -975,7 +1023,7 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
     }
     case GP_OP_RESIDUAL: {
       if (check_width(w) != GP_OK) return 0;
-      return carve_residual(nullptr, round_up(n, kPad), static_cast<int>(round_up(w, 4))).bytes;
+      return carve_residual(nullptr, n, w).bytes;
     }
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
@@ -983,7 +1031,7 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
       SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
       unify_width(pc, pg);
       if (opts != nullptr && opts->refine_rtol > 0)
-        return refine_bytes(pc, prec);
+        return refine_bytes(pc, prec, n, w);
       return carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes;
     }
     case GP_OP_SLQ:
@@ -1063,26 +1111,65 @@ gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* 
   const int64_t n = prob->n;
   const int64_t n_pad = round_up(n, kPad);
   const int w_pad = static_cast<int>(round_up(w, 4));
-  if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n_pad, w_pad).bytes)) != GP_OK) return s;
-  const ResidualWs R = carve_residual(ws, n_pad, w_pad);
+  if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n, w).bytes)) != GP_OK) return s;
+  const ResidualWs R = carve_residual(ws, n, w);
   const size_t plane = static_cast<size_t>(n_pad) * w_pad;
-  // The residual kernel writes rows < n and columns < w only; the norms read
-  // the whole padded plane, so the padding must be zero.
+  // x64 = X over the padded plane (zero padding); the residual plane is fully
+  // written by the combine (zero outside rows < n, columns < w).
   GP_CUDA(cudaMemsetAsync(R.x64, 0, plane * sizeof(double), st));
-  GP_CUDA(cudaMemsetAsync(R.r64, 0, plane * sizeof(double), st));
   GP_CUDA(cudaMemsetAsync(R.Bp, 0, plane * sizeof(float), st));
   GP_CUDA(cudaMemsetAsync(R.Xp, 0, plane * sizeof(float), st));
   GP_CUDA(cudaMemsetAsync(R.S, 0, sizeof(CgState), st));
   GP_CUDA(launch_pad_block(B, n, w, w, R.Bp, n_pad, w_pad, 0, st));
   GP_CUDA(launch_pad_block(X, n, w, w, R.Xp, n_pad, w_pad, 0, st));
   GP_CUDA(launch_refine_update(R.x64, R.Xp, n_pad, w_pad, w, st));   // x64 = X
-  const double f2 = prob->theta.f * prob->theta.f;
-  GP_CUDA(launch_refine_residual(prob->X, n, prob->d, prob->kernel, prob->theta.l, f2,
-                                 prob->theta.s, R.x64, R.Bp, R.r64, n_pad, w_pad, w, st));
+  if ((s = residual_into(prob, R.Bp, w_pad, R.x64, w_pad, w, nullptr, n, kResF64, R.part, R.err,
+                         R.r64, w_pad, nullptr, st)) != GP_OK)
+    return s;
   GP_CUDA(launch_refine_norms(R.S, R.r64, R.Bp, R.rf, n_pad, w_pad, w, R.red, st));
   HostCg h;
   if ((s = read_cg(R.S, h, st)) != GP_OK) return s;
   for (int c = 0; c < w; ++c) relres[c] = h.relres[c];
+  return GP_OK;
+}
+
+gp_status gp_residual_rows(const gp_problem* prob, const float* B, const double* X64, int32_t w,
+                           const int64_t* rows, int64_t m, int32_t arith, double* R,
+                           double* relres, void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if (B == nullptr || X64 == nullptr) return fail(GP_ERR_ARG, "B and X64 must be non-NULL");
+  if (m < 1 || m > prob->n) return fail(GP_ERR_ARG, "m must be in [1, n]");
+  if (arith != GP_RESIDUAL_PAIR && arith != GP_RESIDUAL_FP64)
+    return fail(GP_ERR_ARG, "arith must be GP_RESIDUAL_PAIR or GP_RESIDUAL_FP64");
+  if (R == nullptr && relres == nullptr) return fail(GP_ERR_ARG, "R and relres are both NULL");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n, w).bytes)) != GP_OK) return s;
+  const ResidualWs W = carve_residual(ws, n, w);
+  const int64_t m_pad = round_up(m, kPad);
+  const int w_pad = static_cast<int>(round_up(w, 4));
+  // The residual rows land in the r64 plane, the B rows in Bp ([m_pad][w_pad],
+  // zero padding written by the combine).
+  if ((s = residual_into(prob, B, w, X64, w, w, rows, m, residual_arith(arith), W.part, W.err,
+                         W.r64, w_pad, W.Bp, st)) != GP_OK)
+    return s;
+  int herr = 0;
+  GP_CUDA(cudaMemcpyAsync(&herr, W.err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  if (relres != nullptr) {
+    GP_CUDA(cudaMemsetAsync(W.S, 0, sizeof(CgState), st));
+    GP_CUDA(launch_refine_norms(W.S, W.r64, W.Bp, W.rf, m_pad, w_pad, w, W.red, st));
+    HostCg h;
+    if ((s = read_cg(W.S, h, st)) != GP_OK) return s;
+    if (herr != 0) return fail(GP_ERR_ARG, "a row index is outside [0, n)");
+    for (int c = 0; c < w; ++c) relres[c] = h.relres[c];
+  }
+  if (R != nullptr)
+    GP_CUDA(cudaMemcpy2DAsync(R, sizeof(double) * w, W.r64, sizeof(double) * w_pad,
+                              sizeof(double) * w, m, cudaMemcpyDeviceToDevice, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  if (herr != 0) return fail(GP_ERR_ARG, "a row index is outside [0, n)");
   return GP_OK;
 }
 

@@ -150,8 +150,11 @@ __global__ void __launch_bounds__(kThreads)
     const uint32_t parity = (t >> 1) & 1;
     const bool ok = dev::mbar_wait(&bars[stage], parity);
     if (__syncthreads_or(!ok)) {
+      // Before the CTA exits, wait (bounded) for both copies it may still have
+      // in flight: tile t's (the one that timed out) and tile t+1's.
       if (tid == 0) {
         atomicExch(a.err, kDevTimeout);
+        dev::mbar_wait(&bars[stage], parity);
         if (t + 1 < T) dev::mbar_wait(&bars[stage ^ 1], ((t + 1) >> 1) & 1);
       }
       return;

@@ -895,69 +895,8 @@ __global__ void copy_col0_kernel(const float* X, float* V, int64_t n_pad, int w_
 }
 
 // ------------------------------------------------------------ refinement --
-// The outer residual of iterative refinement, r = B - Kh x, with FP64 kernel
-// entries from the unscaled points and FP64 sums: an accuracy reference for the
-// FP32 and tensor-core inner solves, O(n^2 w) FP64 work.
-constexpr int kRefRows = 128;
-constexpr int kRefCols = 4;
-constexpr int kRefTile = 64;
-
-__device__ __forceinline__ double kernel_f64(double r2, int kernel, double l) {
-  if (kernel == GP_KERNEL_GAUSSIAN) return exp(-r2 / (2.0 * l * l));
-  const double a = sqrt(3.0 * r2) / l;
-  return (1.0 + a) * exp(-a);
-}
-
-__global__ void refine_residual_kernel(const float* X, int64_t n, int d, int kernel, double l,
-                                       double f2, double snoise, const double* x64, const float* B,
-                                       double* r64, int w_pad, int w) {
-  __shared__ double sxj[kRefTile][GP_MAX_DIM];
-  __shared__ double svj[kRefTile][kRefCols];
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * kRefRows + threadIdx.x;
-  const int c0 = blockIdx.y * kRefCols;
-  double xi[GP_MAX_DIM];
-  for (int t = 0; t < GP_MAX_DIM; ++t) xi[t] = (i < n && t < d) ? static_cast<double>(X[i * d + t]) : 0.0;
-  double acc[kRefCols];
-#pragma unroll
-  for (int cc = 0; cc < kRefCols; ++cc) acc[cc] = 0.0;
-  for (int64_t j0 = 0; j0 < n; j0 += kRefTile) {
-    for (int e = threadIdx.x; e < kRefTile * d; e += blockDim.x) {
-      const int jj = e / d, t = e - (e / d) * d;
-      const int64_t j = j0 + jj;
-      sxj[jj][t] = j < n ? static_cast<double>(X[j * d + t]) : 0.0;
-    }
-    for (int e = threadIdx.x; e < kRefTile * kRefCols; e += blockDim.x) {
-      const int jj = e / kRefCols, cc = e % kRefCols;
-      const int64_t j = j0 + jj;
-      const int c = c0 + cc;
-      svj[jj][cc] = (j < n && c < w) ? x64[j * w_pad + c] : 0.0;
-    }
-    __syncthreads();
-    const int jn = static_cast<int>(n - j0 < kRefTile ? n - j0 : kRefTile);
-    for (int jj = 0; jj < jn; ++jj) {
-      double r2 = 0.0;
-      for (int t = 0; t < d; ++t) {
-        const double df = xi[t] - sxj[jj][t];
-        r2 += df * df;
-      }
-      const double k = kernel_f64(r2, kernel, l);
-#pragma unroll
-      for (int cc = 0; cc < kRefCols; ++cc) acc[cc] += k * svj[jj][cc];
-    }
-    __syncthreads();
-  }
-  if (i < n) {
-#pragma unroll
-    for (int cc = 0; cc < kRefCols; ++cc) {
-      const int c = c0 + cc;
-      if (c < w) {
-        const int64_t idx = i * w_pad + c;
-        r64[idx] = static_cast<double>(B[idx]) - (f2 * acc[cc] + snoise * x64[idx]);
-      }
-    }
-  }
-}
-
+// Norms of the outer residual of iterative refinement, the FP64 solution update
+// and its FP32 copy.  (The residual itself is in residual.cuh.)
 __global__ void refine_norms_kernel(CgState* S, const double* r64, const float* B, float* rf,
                                     int64_t n_pad, int w_pad, int w, double* red) {
   const RedLayout L = red_layout(w_pad);
@@ -1194,16 +1133,6 @@ cudaError_t launch_yalpha(CgState* S, const float* B, const float* X, int64_t n_
 
 cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st) {
   assemble_kernel<<<1, 32, 0, st>>>(S, n, p);
-  count_launch();
-  return cudaGetLastError();
-}
-
-cudaError_t launch_refine_residual(const float* X, int64_t n, int d, int kernel, double l, double f2,
-                                   double snoise, const double* x64, const float* B, double* r64,
-                                   int64_t n_pad, int w_pad, int w, cudaStream_t st) {
-  dim3 grid(static_cast<unsigned>(n_pad / kRefRows), static_cast<unsigned>((w + kRefCols - 1) / kRefCols));
-  refine_residual_kernel<<<grid, kRefRows, 0, st>>>(X, n, d, kernel, l, f2, snoise, x64, B, r64,
-                                                    w_pad, w);
   count_launch();
   return cudaGetLastError();
 }

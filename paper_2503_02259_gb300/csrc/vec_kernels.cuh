@@ -134,11 +134,7 @@ cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st);
 // Replace column 0 of V (padded) by column 0 of X.
 cudaError_t launch_copy_col0(const float* X, float* V, int64_t n_pad, int w_pad, cudaStream_t st);
 
-// Iterative refinement.  r64 = B - Kh x64 with FP64 kernel entries computed from
-// the unscaled FP32 points X (row-major n x d) and FP64 sums; rows < n.
-cudaError_t launch_refine_residual(const float* X, int64_t n, int d, int kernel, double l, double f2,
-                                   double snoise, const double* x64, const float* B, double* r64,
-                                   int64_t n_pad, int w_pad, int w, cudaStream_t st);
+// Iterative refinement (the residual r64 = B - Kh x64 is in residual.cuh).
 // S->rr[c] = ||r64_c||^2, S->bn2[c] = ||B_c||^2, S->relres[c] = sqrt(rr/bn2); rf = r64 as FP32.
 cudaError_t launch_refine_norms(CgState* S, const double* r64, const float* B, float* rf,
                                 int64_t n_pad, int w_pad, int w, double* red, cudaStream_t st);

@@ -1,11 +1,18 @@
 """GPU parity of the tcgen05 tensor-core product against the FP64 oracle.
 
 Tolerances (norm-wise per column, as for the FP32 tests):
-  * TF32 operands, FP32 accumulation: <= 3e-3 (the mixed-precision tile bound);
-  * BF16 kernel tile with a hi/lo BF16 V: <= 1e-2 (each entry rounded to BF16
-    carries up to 2^-9 relative error; the derivative sums cancel more);
+  * TF32 operands, FP32 accumulation: <= 3e-3, the tile bound of the
+    mixed-precision path before refinement;
   * split TF32 (hi*hi + hi*lo + lo*hi): <= 1e-5, the FP32 bound;
-  * split BF16: <= 3e-5 (a 16-bit hi + lo pair leaves 2^-17 per entry).
+  * split BF16: <= 3e-5 (a 16-bit hi + lo pair leaves 2^-17 per entry); this
+    is the BF16-operand path that meets the tile bound;
+  * plain BF16 (kernel tile rounded once to BF16, V as hi + lo): NOT within
+    the 3e-3 tile bound and not claimed for it.  An entry rounded to 8
+    significant bits carries about 1.7e-3 rms relative error, and products
+    with a probe column whose result cancels reach 2e-3 to 6e-3 (a CPU
+    simulation of the rounding on these cases gives up to 3.5e-3 for K-hat V
+    and 5.7e-3 for dK-hat/dl V); it is held here to 1e-2, as the fast
+    low-accuracy mode that it is.
 """
 import numpy as np
 import pytest
@@ -15,7 +22,8 @@ from paper_2503_02259_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-TOL = {1: 3e-3, 2: 1e-2, 3: 1e-5, 4: 3e-5}   # TF32, BF16, TF32X3, BF16X3
+TILE_BOUND = 3e-3
+TOL = {1: TILE_BOUND, 2: 1e-2, 3: 1e-5, 4: 3e-5}   # TF32, BF16 (outside the tile bound), TF32X3, BF16X3
 MODES = [1, 2, 3, 4]
 
 

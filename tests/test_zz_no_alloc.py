@@ -7,9 +7,12 @@ allocator and forbids allocation in its execute callback, or a loop with a
 fixed memory budget that must not allocate once it has started.  For them the
 library keeps its scratch in one static device array.  These tests call that
 entry point through the C ABI and compare it with gp_kernel_matmul, the
-workspace entry point, within the FP32 product tolerance used by the other
-product tests (norm-wise 1e-5 per column), on two calls in a row with
-different shapes, so that stale contents of the shared array would show.
+workspace entry point, and with the FP64 oracle, within the FP32 product
+tolerance used by the other product tests (norm-wise 1e-5 per column), on
+calls in a row with different shapes (a smaller problem, then one whose w
+needs no padding, after a larger one), so that stale contents of the shared
+array would show; and on a second stream, ordered after the first by a
+synchronize, which reuses the device address looked up by the first call.
 
 This file is collected last on purpose (its name sorts last), and it passes
 both alone in a fresh process and after the rest of the suite.
@@ -68,6 +71,43 @@ def test_noalloc_matches_workspace_entry_point_two_calls(env):
         got = _noalloc(env, X, V, kind, theta).cpu().numpy()
         assert np.all(np.isfinite(got))
         assert _relerr(got, ref) <= TOL_FP32
+
+
+def test_noalloc_matches_oracle_after_larger_calls(env):
+    import oracle as O
+    torch, B, api, inputs = env
+    # A large call leaves the shared array dirty beyond what the next ones use.
+    Xb = torch.from_numpy(inputs.points(40000, 3, seed=1)).cuda()
+    Vb = torch.from_numpy(inputs.gaussian_block(40000, 40, seed=2)).cuda()
+    _noalloc(env, Xb, Vb, 1, (0.05, 1.5, 0.2))
+    cases = [
+        (2999, 3, 32, 1, (0.05, 1.5, 0.2)),    # w = w_pad: no padded columns to re-zero
+        (1531, 2, 7, 0, (0.1, 1.0, 0.3)),      # ragged n, padded w
+    ]
+    for n, d, w, kind, theta in cases:
+        Xh = inputs.points(n, d, seed=n + 1)
+        Vh = inputs.gaussian_block(n, w, seed=w + 1)
+        ref = O.kmv_rows(Xh, Vh, kind, theta)[0]
+        got = _noalloc(env, torch.from_numpy(Xh).cuda(), torch.from_numpy(Vh).cuda(), kind,
+                       theta).cpu().numpy()
+        assert _relerr(got, ref) <= TOL_FP32
+
+
+def test_noalloc_on_a_second_stream(env):
+    import oracle as O
+    torch, B, api, inputs = env
+    n, d, w, kind, theta = 2500, 3, 16, 0, (0.1, 1.0, 0.3)
+    Xh = inputs.points(n, d, seed=5)
+    Vh = inputs.gaussian_block(n, w, seed=6)
+    X = torch.from_numpy(Xh).cuda()
+    V = torch.from_numpy(Vh).cuda()
+    first = _noalloc(env, X, V, kind, theta)          # default stream, then synchronised
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        second = _noalloc(env, X, V, kind, theta)     # the same array on another stream
+    torch.cuda.synchronize()
+    assert torch.equal(first, second)
+    assert _relerr(second.cpu().numpy(), O.kmv_rows(Xh, Vh, kind, theta)[0]) <= TOL_FP32
 
 
 def test_noalloc_rejects_oversize_problem(env):
