@@ -194,6 +194,24 @@ def predict_mean(X, Xstar, alpha, kind: int, theta) -> np.ndarray:
     return cross_kmv(Xstar, X, alpha, kind, theta)[:, 0]
 
 
+def predict_var(X, Xstar, kind: int, theta) -> np.ndarray:
+    """Posterior variance of the noise-free test outputs y* (§Gaussian Processes:
+    y* and the noisy y are jointly Gaussian, Cov(y*) = f^2 K(X*, X*),
+    Cov(y, y*) = f^2 K(X, X*), Cov(y) = Kh).  Conditioning on y gives, per test
+    point c with k_c = f^2 K(X, x*_c):
+
+        var_c = f^2 k(0) - k_c^T Kh^-1 k_c,   k(0) = 1 for both kernels,
+
+    with Kh^-1 k_c by a Cholesky solve.
+    """
+    s, f, l = theta
+    X = np.asarray(X, dtype=np.float64)
+    Xs = np.asarray(Xstar, dtype=np.float64)
+    Kc = f * f * kernel_value(sqdist(X, Xs), kind, l)          # n x m
+    U = sla.cho_solve(sla.cho_factor(khat_dense(X, kind, theta)), Kc)
+    return f * f - np.einsum("ij,ij->j", Kc, U)
+
+
 # ---------------------------------------------------------------------------
 # O-exact: the NLL and its gradient by Cholesky.
 # ---------------------------------------------------------------------------

@@ -12,7 +12,13 @@ Contents
       precision problem (n = 1e6, d = 2, Gaussian, V = [y | 63 Rademacher]);
   diff_loss, diff_grad: the same-probe SLQ / Hutchinson estimate of L and
       dL/d(s, f, l) on the n = 4000 differentiation subsample (32 probes from
-      seed 77, 40 Lanczos steps).
+      seed 77, 40 Lanczos steps);
+  serving_idx, serving_loss, serving_grad, serving_mu: for the first
+      SERVING_COUNT requests with n <= SERVING_NMAX of the 512-request serving
+      stream (seed 0), the same-probe estimate of L and dL/d(s, f, l) (16
+      probes from seed 0, 20 Lanczos steps, exact solves) of the loss+grad
+      requests and the posterior mean at the first 200 test points (exact
+      solve) of the predictions; NaN where a field does not apply.
 """
 import os
 import sys
@@ -51,12 +57,43 @@ def diff_refs():
     return float(est["loss"]), np.asarray(est["grad"], dtype=np.float64)
 
 
+SERVING_NMAX = 3000
+SERVING_COUNT = 24
+SERVING_MU_POINTS = 200
+
+
+def serving_selection():
+    reqs = inputs.serving_stream(seed=0, count=512)
+    idx = [i for i, r in enumerate(reqs) if r.problem.n <= SERVING_NMAX][:SERVING_COUNT]
+    return reqs, np.asarray(idx, dtype=np.int64)
+
+
+def serving_refs():
+    reqs, idx = serving_selection()
+    loss = np.full(len(idx), np.nan)
+    grad = np.full((len(idx), 3), np.nan)
+    mu = np.full((len(idx), SERVING_MU_POINTS), np.nan)
+    for k, i in enumerate(idx):
+        rq = reqs[i]
+        p = rq.problem
+        if rq.kind == 0:
+            est = O.est_nll(p.X, p.y, p.kind, p.theta, O.rademacher_probes(p.n, rq.nprobe, 0), 20)
+            loss[k] = est["loss"]
+            grad[k] = est["grad"]
+        else:
+            alpha = O.exact_nll(p.X, p.y, p.kind, p.theta)["alpha"]
+            mu[k] = O.predict_mean(p.X, rq.Xstar[:SERVING_MU_POINTS], alpha, p.kind, p.theta)
+    return idx, loss, grad, mu
+
+
 def main():
     mr, mY, mL = matvec_refs()
     pr, pY = precision_refs()
     dl, dg = diff_refs()
+    si, sl, sg, smu = serving_refs()
     np.savez_compressed(OUT, matvec_rows=mr, matvec_Y=mY, matvec_L=mL, precision_rows=pr,
-                        precision_Y=pY, diff_loss=np.float64(dl), diff_grad=dg)
+                        precision_Y=pY, diff_loss=np.float64(dl), diff_grad=dg, serving_idx=si,
+                        serving_loss=sl, serving_grad=sg, serving_mu=smu)
     print("wrote", OUT)
 
 

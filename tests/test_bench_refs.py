@@ -38,3 +38,24 @@ def test_differentiation_subsample_estimate_is_the_oracles():
     est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
     assert abs(est["loss"] - float(refs["diff_loss"])) <= 1e-9 * abs(est["loss"])
     np.testing.assert_allclose(est["grad"], refs["diff_grad"], rtol=1e-9, atol=0)
+
+
+def test_serving_references_are_the_oracles():
+    refs = np.load(REFS)
+    reqs = inputs.serving_stream(seed=0, count=512)
+    idx = refs["serving_idx"]
+    assert len(idx) == 24 and all(reqs[int(i)].problem.n <= 3000 for i in idx)
+    # The first loss+grad request and the first prediction of the selection.
+    k_loss = next(k for k, i in enumerate(idx) if reqs[int(i)].kind == 0)
+    k_pred = next(k for k, i in enumerate(idx) if reqs[int(i)].kind == 1)
+    rq = reqs[int(idx[k_loss])]
+    p = rq.problem
+    est = O.est_nll(p.X, p.y, p.kind, p.theta, O.rademacher_probes(p.n, rq.nprobe, 0), 20)
+    assert abs(est["loss"] - float(refs["serving_loss"][k_loss])) <= 1e-9 * abs(est["loss"])
+    np.testing.assert_allclose(est["grad"], refs["serving_grad"][k_loss], rtol=1e-9, atol=0)
+    rq = reqs[int(idx[k_pred])]
+    p = rq.problem
+    alpha = O.exact_nll(p.X, p.y, p.kind, p.theta)["alpha"]
+    mu = O.predict_mean(p.X, rq.Xstar[:200], alpha, p.kind, p.theta)
+    np.testing.assert_allclose(mu, refs["serving_mu"][k_pred], rtol=1e-9, atol=1e-12)
+    assert np.isnan(refs["serving_loss"][k_pred]) and np.isnan(refs["serving_mu"][k_loss]).all()

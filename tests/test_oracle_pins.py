@@ -200,6 +200,48 @@ def test_predict_mean_interpolates_at_small_noise():
     np.testing.assert_allclose(mu, y, atol=1e-5)
 
 
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_predict_var_identical_points_closed_form(kind):
+    # All n training points at x0: Kh = f^2 1 1^T + s I.  A test point at distance r
+    # has k_c = f^2 k(r) 1, and Sherman-Morrison gives
+    # var = f^2 - f^4 k(r)^2 n / (s + n f^2).
+    n, s, f, l = 30, 0.3, 1.1, 0.5
+    X = _identical_points(n, 3)
+    r = np.array([0.0, 0.2, 0.7, 1.9])
+    Xs = np.repeat(X[:1].astype(np.float64), r.size, axis=0)
+    Xs[:, 0] += r
+    var = O.predict_var(X, Xs, kind, (s, f, l))
+    kr = O.kernel_value(r * r, kind, l)
+    np.testing.assert_allclose(var, f * f - f ** 4 * kr * kr * n / (s + n * f * f), rtol=1e-10)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_predict_var_far_points_is_the_prior(kind):
+    # Test points far from every training point (>= 40 l): k_c = 0, var = f^2.
+    X = inputs.points(50, 2, seed=31)
+    Xs = inputs.points(6, 2, seed=32).astype(np.float64) + 40.0
+    theta = (0.2, 1.3, 0.4)
+    np.testing.assert_allclose(O.predict_var(X, Xs, kind, theta), theta[1] ** 2, rtol=1e-12)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_predict_var_is_the_joint_gaussian_conditional(kind):
+    # Brute force from the joint covariance C of (y, y*) (Cov(y) = Kh,
+    # Cov(y, y*) = f^2 K(X, X*), Cov(y*) = f^2 K(X*, X*)): the conditional
+    # covariance of y* given y is the inverse of the (y*, y*) block of C^-1.
+    X = inputs.points(25, 2, seed=33)
+    Xs = inputs.points(7, 2, seed=34)
+    theta = (0.15, 0.9, 0.3)
+    s, f, l = theta
+    Kc = f * f * O.kernel_value(O.sqdist(X, Xs), kind, l)
+    C = np.block([[O.khat_dense(X, kind, theta), Kc],
+                  [Kc.T, f * f * O.kernel_value(O.sqdist(Xs, Xs), kind, l)]])
+    post = np.linalg.inv(np.linalg.inv(C)[25:, 25:])
+    var = O.predict_var(X, Xs, kind, theta)
+    np.testing.assert_allclose(var, np.diag(post), rtol=1e-7)
+    assert np.all(var > 0) and np.all(var <= f * f)
+
+
 # --------------------------------------------------------- exact NLL / grad --
 
 @pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
@@ -433,3 +475,23 @@ def test_planted_trace_sign_in_estimated_gradient_is_caught(monkeypatch):
     monkeypatch.setattr(O, "est_nll", est_wrong)
     with pytest.raises(AssertionError):
         test_est_nll_approaches_exact()
+
+
+def test_planted_noisy_variance_is_caught(monkeypatch):
+    # Adding the noise s (the variance of a noisy observation) to the
+    # noise-free predictive variance.
+    good = O.gp_oracle.predict_var
+    monkeypatch.setattr(O, "predict_var", lambda X, Xs, k, th: good(X, Xs, k, th) + th[0])
+    with pytest.raises(AssertionError):
+        test_predict_var_far_points_is_the_prior(O.GAUSSIAN)
+
+
+def test_planted_unscaled_cross_covariance_is_caught(monkeypatch):
+    # k_c = K(X, x*) without the f^2 scale: the quadratic term shrinks by f^4.
+    good = O.gp_oracle.predict_var
+    def wrong(X, Xs, k, th):
+        f2 = th[1] ** 2
+        return f2 - (f2 - good(X, Xs, k, th)) / (f2 * f2)
+    monkeypatch.setattr(O, "predict_var", wrong)
+    with pytest.raises(AssertionError):
+        test_predict_var_identical_points_closed_form(O.GAUSSIAN)
