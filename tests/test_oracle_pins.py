@@ -396,6 +396,78 @@ def test_est_nll_approaches_exact():
                                atol=1e-9 * np.abs(ex["grad"]).max())
 
 
+# ------------------------------------------- per-dimension length-scales --
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_ard_equal_lengthscales_reduce_to_isotropic(kind):
+    X = inputs.points(60, 3, seed=41)
+    y = inputs.gaussian_block(60, 1, seed=42)[:, 0].astype(np.float64)
+    s, f, l = 0.2, 1.1, 0.35
+    np.testing.assert_allclose(O.kernel_ard(X, X, kind, [l] * 3),
+                               O.kernel_value(O.sqdist(X, X), kind, l), rtol=1e-12, atol=1e-15)
+    iso = O.exact_nll(X, y, kind, (s, f, l))
+    ard = O.exact_nll_ard(X, y, kind, s, f, [l] * 3)
+    assert ard["loss"] == pytest.approx(iso["loss"], rel=1e-12)
+    # d/dl of the isotropic loss is the sum of the per-dimension derivatives.
+    np.testing.assert_allclose(ard["grad"][:2], iso["grad"][:2], rtol=1e-10)
+    assert ard["grad"][2:].sum() == pytest.approx(iso["grad"][2], rel=1e-10)
+
+
+def test_ard_gaussian_is_a_product_over_dimensions():
+    rng = np.random.default_rng(43)
+    A, B = rng.random((7, 4)), rng.random((5, 4))
+    ls = [0.2, 0.5, 1.3, 0.05]
+    prod = np.ones((7, 5))
+    for t in range(4):
+        prod *= np.exp(-(A[:, t][:, None] - B[:, t][None, :]) ** 2 / (2 * ls[t] ** 2))
+    np.testing.assert_allclose(O.kernel_ard(A, B, O.GAUSSIAN, ls), prod, rtol=1e-13)
+
+
+@pytest.mark.parametrize("kind,sampler", [(O.GAUSSIAN, _bochner_gaussian),
+                                          (O.MATERN32, _bochner_matern32)])
+def test_ard_kernel_matches_spectral_representation(kind, sampler):
+    # Scaling coordinate t by 1/l_t maps the ARD kernel onto the unit isotropic
+    # one, whose spectral measure is sampled independently of the formulas.
+    rng = np.random.default_rng(44)
+    ls = np.array([0.4, 1.1, 0.7])
+    for delta in (np.array([0.3, 0.0, 0.0]), np.array([0.1, 0.5, -0.2]), np.array([0.0, 0.9, 0.4])):
+        mc = sampler(delta / ls, 1.0, 400_000, rng)
+        k = O.kernel_ard(delta[None, :], np.zeros((1, 3)), kind, ls)[0, 0]
+        assert abs(mc - k) < 6e-3, (kind, delta, mc, k)
+
+
+@pytest.mark.parametrize("kind", [O.GAUSSIAN, O.MATERN32])
+def test_ard_gradient_central_difference(kind):
+    X = inputs.points(40, 3, seed=45)
+    y = inputs.gaussian_block(40, 1, seed=46)[:, 0].astype(np.float64)
+    s, f, ls = 0.15, 0.9, [0.3, 0.6, 0.45]
+    g = O.exact_nll_ard(X, y, kind, s, f, ls)["grad"]
+    params = [s, f] + list(ls)
+
+    def L(p):
+        return O.exact_nll_ard(X, y, kind, p[0], p[1], p[2:])["loss"]
+    for t in range(len(params)):
+        h = 1e-5 * params[t]
+        up, dn = list(params), list(params)
+        up[t] += h
+        dn[t] -= h
+        fd = (L(up) - L(dn)) / (2 * h)
+        assert g[t] == pytest.approx(fd, rel=1e-6, abs=1e-8), (t, g[t], fd)
+
+
+def test_est_nll_ard_approaches_exact():
+    X = inputs.points(200, 2, seed=47)
+    y = inputs.gaussian_block(200, 1, seed=48)[:, 0].astype(np.float64)
+    s, f, ls = 0.1, 1.0, [0.15, 0.4]
+    ex = O.exact_nll_ard(X, y, O.GAUSSIAN, s, f, ls)
+    es = O.est_nll_ard(X, y, O.GAUSSIAN, s, f, ls, O.rademacher_probes(200, 256, 2), 30)
+    np.testing.assert_allclose(es["quad"], ex["quad"], rtol=1e-12)
+    assert es["loss"] - ex["loss"] == pytest.approx(0.5 * (es["logdet"] - ex["logdet"]),
+                                                    abs=1e-9 * abs(ex["loss"]))
+    # 256 probes: the estimated traces are within a few percent of the exact ones.
+    assert np.all(np.abs(es["trace"] - ex["trace"]) <= 0.05 * np.abs(ex["trace"]) + 1.0)
+
+
 # -------------------------------------------------------------------- CG --
 
 def test_cg_matches_cholesky_solve():
@@ -495,3 +567,13 @@ def test_planted_unscaled_cross_covariance_is_caught(monkeypatch):
     monkeypatch.setattr(O, "predict_var", wrong)
     with pytest.raises(AssertionError):
         test_predict_var_identical_points_closed_form(O.GAUSSIAN)
+
+
+def test_planted_wrong_ard_derivative_power_is_caught(monkeypatch):
+    # dK/dl_t with l_t^2 in place of l_t^3.
+    good = O.gp_oracle.kernel_dls
+    def wrong(A, B, kind, ls):
+        return [D * ls[t] for t, D in enumerate(good(A, B, kind, ls))]
+    monkeypatch.setattr(O.gp_oracle, "kernel_dls", wrong)
+    with pytest.raises(AssertionError):
+        test_ard_gradient_central_difference(O.GAUSSIAN)
