@@ -188,9 +188,66 @@ def run_reference(args) -> int:
 
 
 PRECS = {"fp32": 0, "tf32": 1, "bf16": 2, "tf32x3": 3, "bf16x3": 4}
+NPROD = {1: 1, 2: 2, 3: 3, 4: 3}   # tensor-core products per operand pair (BF16: A B_hi + A B_lo)
 
 
-def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
+def measure_rates(B, api, dev) -> dict:
+    """The FP32 FMA-pipe rate (packed FFMA2, TFLOP/s) and the MUFU ex2 rate (1e9/s)
+    of this GPU, from the library's microbenchmarks."""
+    fma_t, mufu_g = B.c_double(), B.c_double()
+    B.check(B.lib().gp_measure_pipe_rates(B.ctypes.byref(fma_t), B.ctypes.byref(mufu_g),
+                                          api._stream(dev)), "gp_measure_pipe_rates")
+    return {"fp32_ffma2_tflops": fma_t.value, "mufu_ex2_gops": mufu_g.value}
+
+
+def eval_flops(d: int, matern: bool) -> int:
+    """FP32 flops of one kernel entry's evaluation besides MUFU operations: the
+    squared distance (3d) and the kernel's own arithmetic."""
+    return 3 * d + (6 if matern else 1)
+
+
+def tc_roofline(n: int, d: int, w_pad: int, matern: bool, grad: bool, prec: int, kms: float,
+                rates: dict, peaks: dict) -> dict:
+    """Floors of one tensor-core product launch: the tensor pipe (NPROD products of
+    2 w_pad flops per entry per accumulator, against the measured cuBLAS BF16 peak,
+    x 0.5 for TF32) and the MUFU evaluation (sqrt + ex2 for Matern-3/2, ex2 for the
+    Gaussian, per entry, against the measured ex2 rate); the binding one is the
+    larger, and frac = that floor / the kernel's time."""
+    ratio = 0.5 if prec in (1, 3) else 1.0
+    tpeak = peaks.get("bf16_tflops", 1900.0) * ratio
+    tflops = n * n * 2 * w_pad * NPROD[prec] * (2 if grad else 1)
+    t_tensor = tflops / (tpeak * 1e12) * 1e3
+    mufu = n * n * (2 if matern else 1)
+    t_mufu = mufu / (rates["mufu_ex2_gops"] * 1e9) * 1e3
+    bind = "mufu" if t_mufu >= t_tensor else "tensor"
+    return {"tensor_floor_ms": t_tensor, "tensor_frac": t_tensor / kms,
+            "tensor_peak_tflops": tpeak, "mufu_floor_ms": t_mufu, "mufu_frac": t_mufu / kms,
+            "mufu_peak_gops": rates["mufu_ex2_gops"], "binding": bind,
+            "frac": max(t_tensor, t_mufu) / kms}
+
+
+def lossgrad_roofline(n: int, d: int, matern: bool, p: int, k: int, iters: int, ms: float,
+                      rates: dict) -> dict:
+    """Algorithmic work of one loss + gradient evaluation: block CG on [y | Z]
+    (iters products of n^2 entries x (2 w + eval) flops, w = 1 + p), k Lanczos
+    products on the p probes and one fused derivative product (4 w + eval + 1), in
+    FP32 flops, against the measured FP32 FMA-pipe rate; and the MUFU count of the
+    same entries against the measured ex2 rate."""
+    w = 1 + p
+    e = eval_flops(d, matern)
+    flops = float(n) * n * (iters * (2 * w + e) + k * (2 * p + e) + (4 * w + e + 1))
+    mufu = float(n) * n * (iters + k + 1) * (2 if matern else 1)
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"algorithmic_flops": flops, "achieved_tflops": achieved,
+            "fp32_peak_tflops": rates["fp32_ffma2_tflops"],
+            "frac_of_fp32_pipe": achieved / rates["fp32_ffma2_tflops"],
+            "mufu_floor_ms": mufu / (rates["mufu_ex2_gops"] * 1e9) * 1e3,
+            "frac_of_mufu_floor": mufu / (rates["mufu_ex2_gops"] * 1e9) / (ms * 1e-3),
+            "counted": "iters = the largest CG iteration count over the columns (the block "
+                       "product runs all columns until the last converges)"}
+
+
+def precision_modes(api, B, torch, prob, X, V, dev, rates: dict, steps: int = 5) -> dict:
     """Each tensor-core mode on the bench workload: product-kernel throughput and the
     norm-wise error of K.V and dK/dl.V against FP64 oracle values on 100 sampled rows
     (tests/golden/bench_refs.npz)."""
@@ -228,6 +285,8 @@ def precision_modes(api, B, torch, prob, X, V, dev, steps: int = 5) -> dict:
         out[name] = {"kernel_ms": kms, "value": N_PTS * N_PTS * W / (kms * 1e-3), "unit": UNIT,
                      "relerr_Y": err, "relerr_dYl": errl,
                      "within_3e-3_tile_bound": bool(max(err, errl) <= 3e-3)}
+        if prec != 0:
+            out[name]["roofline"] = tc_roofline(N_PTS, D, 32, True, True, prec, kms, rates, _peaks())
     out["modes_claimed_for_the_3e-3_tile_bound"] = ["tf32", "tf32x3", "bf16x3"]
     return out
 
@@ -366,7 +425,7 @@ def precision_refinement(api, B, torch, cap_inner: int = 25, cap_outer: int = 2,
     return out
 
 
-def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
+def loss_grad_mixed_vs_fp32(api, torch, rates: dict, full_n: int = 200_000) -> dict:
     """L(Theta) and dL/dTheta on the differentiation problem (d = 8, 0.5 N(0,I), Gaussian
     s = 0.1, f = 1, l = 1.2; 32 probes x 40 Lanczos steps, CG to 1e-6): accuracy of each
     arithmetic (CG products / SLQ products) against the FP64 oracle's same-probe estimator
@@ -375,7 +434,9 @@ def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     same = -1
     arms = {"fp32": (0, 0), "tf32x3": (3, same), "bf16x3": (4, same),
             "bf16x3_slq_tf32x3": (4, 3)}
-    timed = ("fp32", "tf32x3", "bf16x3_slq_tf32x3")
+    # Timed at the full n: FP32 and the fastest mixed form (split TF32 throughout
+    # measured 28.9 s, between the two).
+    timed = ("fp32", "bf16x3_slq_tf32x3")
     sub = inputs.diff_problem(seed=0, n=4000)
     refs = _refs()
     est = {"loss": float(refs["diff_loss"]), "grad": refs["diff_grad"]}
@@ -400,8 +461,11 @@ def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
         t0 = time.perf_counter()
         loss, grad, info = api.gp_loss_and_grad(Xf, yf, full.kind, full.theta, opts)
         torch.cuda.synchronize()
-        out[name].update({"ms_per_theta": (time.perf_counter() - t0) * 1e3, "loss": loss,
-                          "grad": grad, "cg_iters": info["cg_iters"]})
+        ms = (time.perf_counter() - t0) * 1e3
+        out[name].update({"ms_per_theta": ms, "loss": loss, "grad": grad,
+                          "cg_iters": info["cg_iters"],
+                          "roofline": lossgrad_roofline(full_n, 8, False, 32, 40, info["cg_iters"],
+                                                        ms, rates)})
     for name in timed[1:]:
         out[f"speedup_{name}_vs_fp32"] = out["fp32"]["ms_per_theta"] / out[name]["ms_per_theta"]
     # The fastest timed mixed arithmetic whose loss and gradient stay within 1e-4.
@@ -414,9 +478,77 @@ def loss_grad_mixed_vs_fp32(api, torch, full_n: int = 200_000) -> dict:
     return out
 
 
-def serving(torch, count: int = 64,
-            precs=(("fp32", 0, 0), ("bf16x3_slq_tf32x3", 4, 3), ("tf32x3", 3, 3)),
-            slots: int = 8, budget_gb: int = 96) -> dict:
+# (name, CG arithmetic, SLQ arithmetic, max_batch): max_batch > 1 runs compatible
+# loss + gradient requests as batches with one grouped product launch per step.
+SERVING_ARMS = (("fp32", 0, 0, 1), ("bf16x3_slq_tf32x3", 4, 3, 1))
+SERVING_ARMS_ALL = SERVING_ARMS + (("fp32_batched", 0, 0, 8), ("tf32x3", 3, 3, 1))
+
+
+def serving_accuracy(torch, precs=SERVING_ARMS, slots: int = 8, budget_gb: int = 32) -> dict:
+    """The served result at convergence: the stream's small requests (the first 24 with
+    n <= 3000; tests/golden/bench_refs.npz) solved to cg_rtol 1e-8 (cap 6000
+    iterations) in each arithmetic, against FP64 oracle values (the same-probe
+    estimator with exact solves for loss+grad, the exact posterior mean at 200 test
+    points for predictions).  Errors are reported over the requests that converged
+    in every arm, for all of them and for those with kappa(Kh) <= 1e4 (the stored
+    condition numbers): a solution's error is about kappa times the product's
+    relative error in any arithmetic."""
+    from paper_2503_02259_gb300 import inputs, server
+    refs = _refs()
+    idx = refs["serving_idx"]
+    reqs = inputs.serving_stream(seed=0, count=512)
+    sel = [reqs[int(i)] for i in idx]
+    kappa = refs["serving_kappa"]
+    out = {"workload": f"{len(sel)} requests of the serving stream with n <= 3000 (16 probes, "
+                       "20 Lanczos steps), CG to rtol 1e-8 (cap 6000), vs FP64 oracle values",
+           "kappa_p50": float(np.median(kappa)), "kappa_max": float(kappa.max()),
+           "requests_kappa_le_1e4": int((kappa <= 1e4).sum())}
+    res = {}
+    for name, prec, slq, mb in precs:
+        with server.Server(budget_gb << 30, slots, max_batch=mb) as srv:
+            tickets = []
+            for rq in sel:
+                p = rq.problem
+                r, keep = server.Server.request(rq.kind, p.X, p.y, p.kind, p.theta, nprobe=rq.nprobe,
+                                                Xstar=rq.Xstar, cg_maxit=6000, nlanczos=20,
+                                                cg_rtol=1e-8, seed=0, prec=prec, slq_prec=slq)
+                tickets.append(srv.submit(r, keep))
+            t0 = time.perf_counter()
+            srv.drain(600)
+            wall = time.perf_counter() - t0
+            res[name] = [srv.poll(t) for t in tickets]
+        out[name] = {"converged": sum(r["status"] == 0 for r in res[name]), "of": len(sel),
+                     "wall_s": wall}
+    both = [k for k in range(len(sel)) if all(res[nm][k]["status"] == 0 for nm, _, _, _ in precs)]
+
+    def q(v, pc):
+        return float(np.percentile(v, pc)) if v else None
+
+    for name, _, _, _ in precs:
+        for tag, keep in (("", both), ("_kappa_le_1e4", [k for k in both if kappa[k] <= 1e4])):
+            el, eg, em = [], [], []
+            for k in keep:
+                r = res[name][k]
+                if sel[k].kind == 0:
+                    lref = float(refs["serving_loss"][k])
+                    gref = np.asarray(refs["serving_grad"][k])
+                    floor = 1e-3 * np.linalg.norm(gref)
+                    el.append(abs(r["loss"] - lref) / abs(lref))
+                    eg.append(float(np.max(np.abs(np.asarray(r["grad"]) - gref) /
+                                           np.maximum(np.abs(gref), floor))))
+                else:
+                    mref = refs["serving_mu"][k]
+                    em.append(float(np.linalg.norm(r["mu"][:mref.size] - mref) /
+                                    np.linalg.norm(mref)))
+            out[name].update({f"requests_compared{tag}": len(keep),
+                              f"relerr_loss_p50{tag}": q(el, 50), f"relerr_loss_p90{tag}": q(el, 90),
+                              f"relerr_grad_p50{tag}": q(eg, 50), f"relerr_grad_p90{tag}": q(eg, 90),
+                              f"relerr_mu_p50{tag}": q(em, 50), f"relerr_mu_p90{tag}": q(em, 90),
+                              f"relerr_max{tag}": max(el + eg + em) if keep else None})
+    return out
+
+
+def serving(torch, count: int = 512, precs=SERVING_ARMS, slots: int = 8, budget_gb: int = 96) -> dict:
     """Replay one Poisson stream of mixed loss+grad and prediction requests through the
     server once per arithmetic: throughput, p50/p99 latency, and how far each mixed
     run's losses, gradients and predictions are from the FP32 run's (same probes, same
@@ -432,8 +564,8 @@ def serving(torch, count: int = 64,
                        "m=10000); fixed CG budget 20 (training) / 50 (prediction), SLQ 20 steps",
            "slots": slots, "budget_gb": budget_gb}
     results = {}
-    for name, prec, slq in precs:
-        with server.Server(budget_gb << 30, slots) as srv:
+    for name, prec, slq, mb in precs:
+        with server.Server(budget_gb << 30, slots, max_batch=mb) as srv:
             t0 = time.perf_counter()
             res = server.replay(srv, reqs, prec=prec, slq_prec=slq, nlanczos=20, cg_rtol=1e-12)
             wall = time.perf_counter() - t0
@@ -448,7 +580,10 @@ def serving(torch, count: int = 64,
                      "latency_p99_s": float(np.percentile(lat, 99)),
                      "latency_from": "scheduled arrival (Poisson stream time) to completion",
                      "latency_p99_s_n_le_2e4": float(np.percentile(small, 99)) if small.size else None,
-                     "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"]}
+                     "peak_active": stats["peak_active"], "peak_bytes": stats["peak_bytes"],
+                     "max_batch": mb, "batches": stats["batches"],
+                     "batched_requests": stats["batched_requests"],
+                     "largest_batch": stats["largest_batch"]}
     # Accuracy of a fixed-budget solve is its final CG residual (the budget, not the
     # arithmetic, decides how far from K-hat^-1 y the iterate is): compare each mixed
     # arm's residual with the FP32 arm's, request by request, and report how far the
@@ -458,7 +593,7 @@ def serving(torch, count: int = 64,
 
     ref = results.get("fp32")
     if ref is not None:
-        for name, _, _ in precs:
+        for name, _, _, _ in precs:
             if name == "fp32":
                 continue
             ratio, dl, dg, dm = [], [], [], []
@@ -482,7 +617,7 @@ def serving(torch, count: int = 64,
     return out
 
 
-def loss_grad_small(api, torch, reps: int = 3) -> dict:
+def loss_grad_small(api, torch, rates: dict, reps: int = 3) -> dict:
     """Loss + gradient per Theta on the small configuration (n=2000, d=3, Gaussian)."""
     from paper_2503_02259_gb300 import inputs
     prob = inputs.small_problem(seed=0)
@@ -496,10 +631,11 @@ def loss_grad_small(api, torch, reps: int = 3) -> dict:
         t0 = time.perf_counter()
         loss, grad, info = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, opts)
         ts.append((time.perf_counter() - t0) * 1e3)
+    ms = statistics.median(ts)
     return {"workload": "n=2000 d=3 uniform, Gaussian f=1 l=0.3 s=0.1, block CG on [y|10 probes] "
                         "to rtol 1e-8, SLQ 10x30, Hutchinson, FP32",
-            "ms": statistics.median(ts), "loss": loss, "grad": grad,
-            "cg_iters": info["cg_iters"]}
+            "ms": ms, "loss": loss, "grad": grad, "cg_iters": info["cg_iters"],
+            "roofline": lossgrad_roofline(prob.n, 3, False, 10, 30, info["cg_iters"], ms, rates)}
 
 
 def run_leg(args) -> int:
@@ -508,11 +644,17 @@ def run_leg(args) -> int:
     from paper_2503_02259_gb300 import build
     build.build()
     from paper_2503_02259_gb300 import _binding as B
-    from paper_2503_02259_gb300 import api
+    from paper_2503_02259_gb300 import api, inputs
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
+    rates = measure_rates(B, api, dev)
     if args.leg == "loss_grad":
-        out = loss_grad_small(api, torch)
+        out = loss_grad_small(api, torch, rates)
+    elif args.leg == "precision_modes":
+        prob = inputs.matvec_problem(seed=0)
+        X = torch.from_numpy(prob.X).to(dev)
+        V = torch.from_numpy(inputs.multivector(prob.y, W, seed=0)).to(dev)
+        out = precision_modes(api, B, torch, prob, X, V, dev, rates)
     elif args.leg == "precision_config":
         out = precision_config(api, B, torch, dev)
     elif args.leg == "refinement":
@@ -520,9 +662,12 @@ def run_leg(args) -> int:
     elif args.leg == "precision_refinement":
         out = precision_refinement(api, B, torch)
     elif args.leg == "loss_grad_mixed_vs_fp32":
-        out = loss_grad_mixed_vs_fp32(api, torch)
+        out = loss_grad_mixed_vs_fp32(api, torch, rates)
+    elif args.leg == "serving_accuracy":
+        out = serving_accuracy(torch)
     else:
-        out = serving(torch, count=args.serving_requests)
+        out = serving(torch, count=args.serving_requests,
+                      precs=SERVING_ARMS_ALL if args.serving_all_arms else SERVING_ARMS)
     print(json.dumps({"leg": args.leg, **out}), flush=True)
     return 0
 
@@ -536,11 +681,14 @@ def main() -> int:
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--prec", default="fp32", choices=list(PRECS), help="arithmetic of the product")
-    ap.add_argument("--serving-requests", type=int, default=64,
+    ap.add_argument("--serving-requests", type=int, default=512,
                     help="requests replayed by the serving leg (the full stream is 512)")
+    ap.add_argument("--serving-all-arms", action="store_true",
+                    help="also replay the stream with batched FP32 requests and in split TF32")
     ap.add_argument("--leg", default=None,
-                    choices=["loss_grad", "precision_config", "refinement", "precision_refinement",
-                             "loss_grad_mixed_vs_fp32", "serving"],
+                    choices=["loss_grad", "precision_modes", "precision_config", "refinement",
+                             "precision_refinement",
+                             "loss_grad_mixed_vs_fp32", "serving", "serving_accuracy"],
                     help="run one extra leg alone on cuda:0 and print its JSON (for profiling)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -642,17 +790,22 @@ def main() -> int:
     h2d = Xp.numel() * 4 + Vp.numel() * 4
     d2h = 3 * N_PTS * W * 4
 
+    # Measured pipe rates of this GPU (microbenchmarks, after the timed region).
+    rates = measure_rates(B, api, dev)
     extras = {}
     if rank == 0 and not args.no_extras:
         # Each extra leg runs after the headline measurement; a leg that fails
         # records its error in the line instead of taking the line with it.
-        legs = (("loss_grad", lambda: loss_grad_small(api, torch)),
-                ("precision_modes", lambda: precision_modes(api, B, torch, prob, X, V, dev)),
+        legs = (("loss_grad", lambda: loss_grad_small(api, torch, rates)),
+                ("precision_modes", lambda: precision_modes(api, B, torch, prob, X, V, dev, rates)),
                 ("precision_config", lambda: precision_config(api, B, torch, dev)),
                 ("refinement", lambda: refinement(api, torch)),
                 ("precision_refinement", lambda: precision_refinement(api, B, torch)),
-                ("loss_grad_mixed_vs_fp32", lambda: loss_grad_mixed_vs_fp32(api, torch)),
-                ("serving", lambda: serving(torch, count=args.serving_requests)))
+                ("loss_grad_mixed_vs_fp32", lambda: loss_grad_mixed_vs_fp32(api, torch, rates)),
+                ("serving", lambda: serving(torch, count=args.serving_requests,
+                                            precs=SERVING_ARMS_ALL if args.serving_all_arms
+                                            else SERVING_ARMS)),
+                ("serving_accuracy", lambda: serving_accuracy(torch)))
         for name, leg in legs:
             try:
                 extras[name] = leg()
@@ -692,20 +845,29 @@ def main() -> int:
         psrc = ("measured cuBLAS bf16 dense peak (MEASURED_PEAKS.json)"
                 + (" x 0.5, the nominal tf32:bf16 ratio" if ratio != 1.0 else ""))
     achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
-    # Measured pipe rates of this GPU (microbenchmarks, run after the timed region).
-    fma_t, mufu_g = B.c_double(), B.c_double()
-    B.check(B.lib().gp_measure_pipe_rates(B.ctypes.byref(fma_t), B.ctypes.byref(mufu_g),
-                                          api._stream(dev)), "gp_measure_pipe_rates")
     roofline = {"bound": bound, "kernel": kname,
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": tr.get("bytes_per_launch") if tr else None,
                 "peak_source": psrc,
                 "kernel_ms": kern_ms, "algorithmic_flops_per_launch": flops_per_launch,
                 "kernel_share_of_step": kern_ms / per_step_ms,
-                "pipe_rates_measured": {"fp32_ffma2_tflops": fma_t.value,
-                                        "mufu_ex2_gops": mufu_g.value,
-                                        "frac_of_measured_fp32": (achieved / fma_t.value
+                "pipe_rates_measured": {**rates,
+                                        "frac_of_measured_fp32": (achieved / rates["fp32_ffma2_tflops"]
                                                                   if prec == 0 else None)}}
+    if prec != 0:
+        # The tensor-core product is bound by the kernel evaluation (MUFU) far
+        # more than by the tensor pipe at these widths: report against the
+        # binding floor, with both fractions alongside.
+        tcr = tc_roofline(N_PTS, D, 32, True, True, prec, kern_ms, rates, peaks)
+        roofline["evaluation_and_tensor"] = tcr
+        if tcr["binding"] == "mufu":
+            mufu_ops = N_PTS * N_PTS * 2.0
+            roofline.update({"bound": "alu", "achieved": mufu_ops / (kern_ms * 1e-3) / 1e12,
+                             "peak": rates["mufu_ex2_gops"] / 1e3, "unit": "Top/s (MUFU)",
+                             "frac": tcr["mufu_frac"],
+                             "peak_source": "measured MUFU ex2 rate of this GPU "
+                                            "(gp_measure_pipe_rates); 2 MUFU (sqrt, ex2) per "
+                                            "Matern-3/2 entry"})
     cpu = None
     if not args.no_cpu_baseline:
         cpu = cpu_oracle_rate()

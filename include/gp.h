@@ -97,7 +97,9 @@ typedef enum {
   GP_OP_SLQ = 3,          /* gp_slq_logdet */
   GP_OP_LOSS_GRAD = 4,    /* gp_loss_and_grad, gp_nll_forward, gp_nll_backward */
   GP_OP_PREDICT = 5,      /* gp_predict_mean */
-  GP_OP_RESIDUAL = 6      /* gp_true_residual, gp_residual_rows */
+  GP_OP_RESIDUAL = 6,     /* gp_true_residual, gp_residual_rows */
+  GP_OP_PREDICT_VAR = 7,  /* gp_predict_var */
+  GP_OP_LOSS_GRAD_BATCH = 8  /* one member of gp_loss_and_grad_batch */
 } gp_op;
 
 /* Theta = (s, f, l): noise s, scale f, length-scale l (§Gaussian Processes). */
@@ -105,13 +107,24 @@ typedef struct {
   double s, f, l;
 } gp_theta;
 
-/* X: device, n x d row-major float32 training points. kernel: a gp_kernel. */
+/* X: device, n x d row-major float32 training points. kernel: a gp_kernel.
+ * ls: optional HOST array of d per-dimension length-scales l_1..l_d (the
+ * "kernel parameters l" of §Gaussian Processes taken one per coordinate;
+ * theta.l is then unused but must still be > 0), or NULL for the isotropic
+ * theta.l.  The kernel sees rho^2 = sum_t (x_t - y_t)^2 / l_t^2:
+ * exp(-rho^2/2) or (1 + sqrt(3) rho) exp(-sqrt(3) rho).  Per-dimension
+ * length-scales are taken by the products (but not by the dKh/dl output of
+ * gp_kernel_grad_matmul), CG, SLQ, the loss and its gradient (which then has
+ * 2 + d entries), and the predictions; iterative refinement and the residual
+ * calls return GP_ERR_UNIMPLEMENTED for them, as does the request server,
+ * whose requests carry no ls. */
 typedef struct {
   const float* X;
   int64_t n;
   int32_t d;
   int32_t kernel;
   gp_theta theta;
+  const double* ls;
 } gp_problem;
 
 /* Options of the iterative solvers.
@@ -304,10 +317,37 @@ gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, doubl
  * gradient equations; Eq. 1 and Eq. 2 with M = I).  One block CG on [y | Z],
  * SLQ from the probe columns, and one fused derivative product with [alpha | Z].
  * y: device n float32.  loss, grad[3] (s, f, l), info (may be NULL): host.
+ * With per-dimension length-scales (prob->ls) grad has 2 + d entries
+ * (s, f, l_1..l_d), from one fused contraction of the kernel entries and
+ * their d derivatives with alpha alpha^T and U Z^T / p (no derivative
+ * product is formed); 1 + nprobe <= 48 then, info->quad/trace hold s and f
+ * in [0..1] and NaN in [2], and no trace standard errors are formed.
  * Synchronises `stream`. */
 gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
                            double* loss, double* grad, gp_loss_info* info, void* ws,
                            size_t ws_bytes, void* stream);
+
+/* gp_loss_and_grad for `count` independent problems at once (1 <= count <=
+ * 64): the members advance together, and every CG iteration, every Lanczos
+ * step and the gradient pass run ONE grouped product launch covering all
+ * members' tiles (a persistent kernel whose CTAs take (member, row tile,
+ * j-split) work items from a counter, largest members first), followed by
+ * each member's O(n w) steps.  Each member's results are those of its own
+ * problem; a member that has converged skips its tiles on the device.  The
+ * members share the kernel, the dimension template (d in {1}, {2}, {3}, {4},
+ * {5..8}, {9..16}), nprobe (1 + nprobe <= 64) and nlanczos; each has its own
+ * X, n, Theta, y, seed, cg_rtol and cg_maxit; products are FP32 and the
+ * length-scale isotropic (GP_ERR_UNIMPLEMENTED otherwise).  probs, y (device
+ * pointers), opts, ws, ws_bytes: arrays of count; ws[k] of at least
+ * gp_workspace_bytes(GP_OP_LOSS_GRAD_BATCH, &probs[k], 0, &opts[k]) bytes.
+ * loss[count], grad[3 count], info[count] (may be NULL), status[count] (may
+ * be NULL): host.  Returns GP_ERR_NOT_CONVERGED if a member missed its
+ * cg_rtol (its results are written, as for gp_loss_and_grad), else the first
+ * other error.  Synchronises `stream`. */
+gp_status gp_loss_and_grad_batch(int32_t count, const gp_problem* probs, const float* const* y,
+                                 const gp_solve_opts* opts, double* loss, double* grad,
+                                 gp_loss_info* info, int32_t* status, void* const* ws,
+                                 const size_t* ws_bytes, void* stream);
 
 /* The forward half of gp_loss_and_grad: block CG on [y | Z] and SLQ.  Writes the
  * solutions W = Kh^-1 [y | Z] to the device n x (1 + nprobe) array `W` (kept by
@@ -318,7 +358,8 @@ gp_status gp_nll_forward(const gp_problem* prob, const float* y, const gp_solve_
 
 /* The backward half: from W of gp_nll_forward (same problem, same opts, so the
  * same probes Z are regenerated rather than stored), one fused derivative
- * product with [alpha | Z] gives grad[3] = dL/d(s, f, l).  Synchronises. */
+ * product with [alpha | Z] gives grad[3] = dL/d(s, f, l) (grad[2 + d] with
+ * per-dimension length-scales, as for gp_loss_and_grad).  Synchronises. */
 gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, const float* W,
                           double* grad, gp_loss_info* info, void* ws, size_t ws_bytes,
                           void* stream);
@@ -332,6 +373,25 @@ gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, con
 gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const float* Xstar,
                           int64_t m, float* mu, int32_t prec, void* ws, size_t ws_bytes,
                           void* stream);
+
+/* Posterior variance of the noise-free test outputs at m test points
+ * (§Gaussian Processes: y* and y jointly Gaussian with Cov(y*) = f^2 K(X*, X*),
+ * Cov(y, y*) = f^2 K(X, X*), Cov(y) = Kh; the prediction call of §Design and
+ * Implementation):  var[c] = f^2 - k_c^T Kh^-1 k_c,  k_c = f^2 K(X, x*_c).
+ * Test points are taken in blocks of up to GP_MAX_COLS: the block's columns
+ * k_c are formed on the device, Kh^-1 k_c by block CG (opts->cg_rtol,
+ * opts->cg_maxit, product arithmetic opts->prec), and the dot products in FP64.
+ * In exact arithmetic a CG iterate from zero underestimates k_c^T Kh^-1 k_c,
+ * so an unconverged solve overestimates the variance; the FP32 rounding of the
+ * difference (about kappa u f^2) can dominate where the variance is far below
+ * f^2 on a very ill-conditioned system, and can then even make it negative.  Xstar: device m x d; var: device m
+ * float32.  iters_max / relres_max (host, may be NULL): the largest CG
+ * iteration count and final relres over all columns.  GP_ERR_NOT_CONVERGED
+ * (var written) if a column missed cg_rtol.  Workspace:
+ * gp_workspace_bytes(GP_OP_PREDICT_VAR, prob, m, opts).  Synchronises. */
+gp_status gp_predict_var(const gp_problem* prob, const float* Xstar, int64_t m, float* var,
+                         const gp_solve_opts* opts, int32_t* iters_max, double* relres_max,
+                         void* ws, size_t ws_bytes, void* stream);
 
 /* Z[i][c] = +-1 (the probe rule of gp_solve_opts.seed) for i < n, c < p, into the
  * device array Z with leading dimension ldz >= p.  Asynchronous. */
@@ -392,6 +452,9 @@ typedef struct {
   int64_t peak_active;     /* most requests on the device at once */
   size_t peak_bytes;       /* most pool bytes in use at once */
   size_t budget_bytes;
+  int64_t batches;         /* grouped launches of two or more requests */
+  int64_t batched_requests;/* requests that ran in them */
+  int64_t largest_batch;
 } gp_server_stats;
 
 typedef struct {
@@ -427,9 +490,23 @@ typedef struct {
 
 /* Create a server on the current device with a device-memory budget and a
  * maximum number of concurrently resident requests (1..256; budget >= 1 MiB).
- * GP_ERR_OOM if the device pool cannot be reserved.  The server clock of
+ * GP_ERR_OOM if the device pool cannot be reserved; GP_ERR_CUDA if a worker
+ * cannot create its CUDA streams (every worker has reported before this call
+ * returns, and on failure nothing is left running).  The server clock of
  * gp_result starts when this call returns. */
 gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server** out);
+/* gp_server_create with batching: a worker that admits a loss + gradient
+ * request with FP32 products also takes up to max_batch - 1 queued requests
+ * that can share its grouped launches (same kernel, dimension class, nprobe
+ * and nlanczos; work within a factor 16; blocks that fit the pool, least
+ * work first) and runs them together as one gp_loss_and_grad_batch: one
+ * grouped product launch per CG iteration, Lanczos step and gradient pass
+ * for all of them.  Requests that arrive meanwhile queue for the next free
+ * worker, as without batching.  Each result is the same as the request's
+ * own gp_loss_and_grad (bit for bit when its padded width is one of the
+ * grouped widths, e.g. 1 + nprobe = 17).  1 <= max_batch <= 64. */
+gp_status gp_server_create_batched(size_t hbm_budget_bytes, int32_t max_slots, int32_t max_batch,
+                                   gp_server** out);
 /* Queue a request (host arrays copied at submit); returns a ticket.
  * GP_ERR_OOM if the request can never fit the budget. */
 gp_status gp_server_submit(gp_server* srv, const gp_request* req, uint64_t* ticket);

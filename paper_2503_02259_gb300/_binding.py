@@ -41,6 +41,8 @@ OP_SLQ = 3
 OP_LOSS_GRAD = 4
 OP_PREDICT = 5
 OP_RESIDUAL = 6
+OP_PREDICT_VAR = 7
+OP_LOSS_GRAD_BATCH = 8
 
 RESIDUAL_PAIR = 0   # compensated FP32-pair sums (the refinement default)
 RESIDUAL_FP64 = 1   # FP64 entries and sums (the checker)
@@ -56,7 +58,7 @@ class gp_theta(ctypes.Structure):
 
 class gp_problem(ctypes.Structure):
     _fields_ = [("X", c_void_p), ("n", c_int64), ("d", c_int32), ("kernel", c_int32),
-                ("theta", gp_theta)]
+                ("theta", gp_theta), ("ls", c_void_p)]
 
 
 class gp_solve_opts(ctypes.Structure):
@@ -89,7 +91,8 @@ class gp_request(ctypes.Structure):
 
 class gp_server_stats(ctypes.Structure):
     _fields_ = [("submitted", c_int64), ("completed", c_int64), ("refused", c_int64),
-                ("peak_active", c_int64), ("peak_bytes", c_size_t), ("budget_bytes", c_size_t)]
+                ("peak_active", c_int64), ("peak_bytes", c_size_t), ("budget_bytes", c_size_t),
+                ("batches", c_int64), ("batched_requests", c_int64), ("largest_batch", c_int64)]
 
 
 class gp_result(ctypes.Structure):
@@ -126,6 +129,11 @@ PROTOTYPES = {
     "gp_loss_and_grad": (c_int32, [POINTER(gp_problem), c_void_p, POINTER(gp_solve_opts),
                                    POINTER(c_double), POINTER(c_double), POINTER(gp_loss_info),
                                    c_void_p, c_size_t, c_void_p]),
+    "gp_loss_and_grad_batch": (c_int32, [c_int32, POINTER(gp_problem), POINTER(c_void_p),
+                                         POINTER(gp_solve_opts), POINTER(c_double),
+                                         POINTER(c_double), POINTER(gp_loss_info),
+                                         POINTER(c_int32), POINTER(c_void_p), POINTER(c_size_t),
+                                         c_void_p]),
     "gp_nll_forward": (c_int32, [POINTER(gp_problem), c_void_p, POINTER(gp_solve_opts), c_void_p,
                                  POINTER(c_double), POINTER(gp_loss_info), c_void_p, c_size_t,
                                  c_void_p]),
@@ -134,11 +142,15 @@ PROTOTYPES = {
                                   c_void_p]),
     "gp_predict_mean": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int64, c_void_p,
                                   c_int32, c_void_p, c_size_t, c_void_p]),
+    "gp_predict_var": (c_int32, [POINTER(gp_problem), c_void_p, c_int64, c_void_p,
+                                 POINTER(gp_solve_opts), POINTER(c_int32), POINTER(c_double),
+                                 c_void_p, c_size_t, c_void_p]),
     "gp_generate_probes": (c_int32, [c_int64, c_int32, c_uint64, c_void_p, c_int64, c_void_p]),
     "gp_profile_begin": (c_int32, []),
     "gp_profile_end": (c_int32, [POINTER(c_double), POINTER(c_int64), POINTER(c_int64)]),
     "gp_measure_pipe_rates": (c_int32, [POINTER(c_double), POINTER(c_double), c_void_p]),
     "gp_server_create": (c_int32, [c_size_t, c_int32, POINTER(c_void_p)]),
+    "gp_server_create_batched": (c_int32, [c_size_t, c_int32, c_int32, POINTER(c_void_p)]),
     "gp_server_submit": (c_int32, [c_void_p, POINTER(gp_request), POINTER(c_uint64)]),
     "gp_server_poll": (c_int32, [c_void_p, c_uint64, POINTER(gp_result)]),
     "gp_server_drain": (c_int32, [c_void_p, c_double]),

@@ -31,13 +31,20 @@ def _f32(t: torch.Tensor, name: str) -> torch.Tensor:
     return t.contiguous()
 
 
-def problem(X: torch.Tensor, kernel: int, theta) -> tuple[B.gp_problem, torch.Tensor]:
-    """gp_problem for device points X (n, d) float32 and theta = (s, f, l)."""
+def problem(X: torch.Tensor, kernel: int, theta, ls=None) -> tuple[B.gp_problem, torch.Tensor]:
+    """gp_problem for device points X (n, d) float32 and theta = (s, f, l); ls:
+    optional d per-dimension length-scales (theta's l is then unused)."""
     X = _f32(X, "X")
     if X.dim() != 2:
         raise ValueError("X must be (n, d)")
     s, f, l = (float(v) for v in theta)
     p = B.gp_problem(X.data_ptr(), X.shape[0], X.shape[1], int(kernel), B.gp_theta(s, f, l))
+    if ls is not None:
+        if len(ls) != X.shape[1]:
+            raise ValueError("ls must have d entries")
+        arr = (ctypes.c_double * len(ls))(*(float(v) for v in ls))
+        p.ls = ctypes.cast(arr, ctypes.c_void_p)
+        p._ls_keep = arr   # the host array lives as long as the struct
     return p, X
 
 
@@ -65,9 +72,9 @@ def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None,
     return ws
 
 
-def gp_kernel_matmul(X, V, kernel, theta, prec=B.PREC_FP32, ws=None) -> torch.Tensor:
+def gp_kernel_matmul(X, V, kernel, theta, prec=B.PREC_FP32, ws=None, ls=None) -> torch.Tensor:
     """Y = Kh V on the device."""
-    prob, X = problem(X, kernel, theta)
+    prob, X = problem(X, kernel, theta, ls)
     V = _f32(V, "V")
     if V.dim() == 1:
         V = V[:, None]
@@ -100,9 +107,10 @@ def gp_kernel_grad_matmul(X, V, kernel, theta, ws=None):
     return Y, dYf, dYl
 
 
-def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True, ws=None):
+def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True, ws=None,
+                 ls=None):
     """Column-wise CG: returns (Xsol, iters (w,), relres (w,), status)."""
-    prob, X = problem(X, kernel, theta)
+    prob, X = problem(X, kernel, theta, ls)
     Bm = _f32(Bm, "B")
     if Bm.dim() == 1:
         Bm = Bm[:, None]
@@ -205,18 +213,48 @@ def gp_slq_logdet(X, kernel, theta, opts: B.gp_solve_opts, ws=None):
     return ld.value, se.value
 
 
-def gp_loss_and_grad(X, y, kernel, theta, opts: B.gp_solve_opts, ws=None):
-    """(loss, [dL/ds, dL/df, dL/dl], info dict)."""
-    prob, X = problem(X, kernel, theta)
+def gp_loss_and_grad(X, y, kernel, theta, opts: B.gp_solve_opts, ws=None, ls=None):
+    """(loss, [dL/ds, dL/df, dL/dl], info dict); with per-dimension length-scales
+    ls the gradient is [dL/ds, dL/df, dL/dl_1, ..., dL/dl_d]."""
+    prob, X = problem(X, kernel, theta, ls)
     y = _f32(y, "y").reshape(-1)
     loss = c_double()
-    grad = (c_double * 3)()
+    grad = (c_double * (3 if ls is None else 2 + X.shape[1]))()
     info = B.gp_loss_info()
     if ws is None:
         ws = workspace(B.OP_LOSS_GRAD, prob, 0, opts, X.device)
     check(lib().gp_loss_and_grad(byref(prob), _ptr(y), byref(opts), byref(loss), grad, byref(info),
                                  _ptr(ws), ws.numel(), _stream(X.device)), "gp_loss_and_grad")
     return loss.value, list(grad), info.as_dict()
+
+
+def gp_loss_and_grad_batch(Xs, ys, kernels, thetas, opts_list, raise_not_converged=True):
+    """gp_loss_and_grad for several problems at once (one grouped product launch
+    per solver step): returns ([loss], [[dL/ds, dL/df, dL/dl]], [info], [status])."""
+    count = len(Xs)
+    probs = (B.gp_problem * count)()
+    keep = []
+    for k in range(count):
+        p, X = problem(Xs[k], kernels[k], thetas[k])
+        probs[k] = p
+        keep.append(X)
+    yv = [_f32(y, "y").reshape(-1) for y in ys]
+    yp = (ctypes.c_void_p * count)(*[y.data_ptr() for y in yv])
+    opts = (B.gp_solve_opts * count)(*opts_list)
+    wss = [workspace(B.OP_LOSS_GRAD_BATCH, probs[k], 0, opts[k], keep[k].device)
+           for k in range(count)]
+    wsp = (ctypes.c_void_p * count)(*[w.data_ptr() for w in wss])
+    wsb = (ctypes.c_size_t * count)(*[w.numel() for w in wss])
+    loss = (c_double * count)()
+    grad = (c_double * (3 * count))()
+    info = (B.gp_loss_info * count)()
+    status = (c_int32 * count)()
+    st = lib().gp_loss_and_grad_batch(count, probs, yp, opts, loss, grad, info, status, wsp, wsb,
+                                      _stream(keep[0].device))
+    if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
+        check(st, "gp_loss_and_grad_batch")
+    return (list(loss), [list(grad[3 * k:3 * k + 3]) for k in range(count)],
+            [i.as_dict() for i in info], list(status))
 
 
 def gp_nll_forward(X, y, kernel, theta, opts: B.gp_solve_opts):
@@ -244,9 +282,9 @@ def gp_nll_backward(X, W, kernel, theta, opts: B.gp_solve_opts):
     return list(grad), info.as_dict()
 
 
-def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32, ws=None):
+def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32, ws=None, ls=None):
     """mu = f^2 K(X*, X) alpha."""
-    prob, X = problem(X, kernel, theta)
+    prob, X = problem(X, kernel, theta, ls)
     alpha = _f32(alpha, "alpha").reshape(-1)
     Xstar = _f32(Xstar, "Xstar")
     m = Xstar.shape[0]
@@ -256,6 +294,25 @@ def gp_predict_mean(X, alpha, Xstar, kernel, theta, prec=B.PREC_FP32, ws=None):
     check(lib().gp_predict_mean(byref(prob), _ptr(alpha), _ptr(Xstar), m, _ptr(mu), int(prec),
                                 _ptr(ws), ws.numel(), _stream(X.device)), "gp_predict_mean")
     return mu
+
+
+def gp_predict_var(X, Xstar, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True,
+                   ws=None, ls=None):
+    """Posterior variance of the noise-free test outputs at Xstar: returns
+    (var (m,), largest CG iteration count, largest final relres, status)."""
+    prob, X = problem(X, kernel, theta, ls)
+    Xstar = _f32(Xstar, "Xstar")
+    m = Xstar.shape[0]
+    var = torch.empty(m, dtype=torch.float32, device=X.device)
+    it = c_int32()
+    rel = c_double()
+    if ws is None:
+        ws = workspace(B.OP_PREDICT_VAR, prob, m, opts, X.device)
+    st = lib().gp_predict_var(byref(prob), _ptr(Xstar), m, _ptr(var), byref(opts), byref(it),
+                              byref(rel), _ptr(ws), ws.numel(), _stream(X.device))
+    if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
+        check(st, "gp_predict_var")
+    return var, it.value, rel.value, st
 
 
 def gp_generate_probes(n: int, p: int, seed: int, device="cuda") -> torch.Tensor:

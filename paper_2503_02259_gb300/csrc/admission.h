@@ -114,5 +114,58 @@ long pick_next(size_t count, double now, PoolAllocator& pool, Work work, Submit 
   return -1;
 }
 
+// Dimension class of a problem: the compile-time dimension template the
+// products are instantiated for (1, 2, 3, 4; 5..8 -> 8; 9..16 -> 16).
+inline int dim_class(int d) {
+  if (d <= 4) return d;
+  if (d <= 8) return 8;
+  return 16;
+}
+
+// Requests that gp_loss_and_grad_batch can take: loss + gradient with FP32
+// products and 1 + nprobe <= 64.
+inline bool batchable(const gp_request& r) {
+  const int slq = r.slq_prec == GP_PREC_SAME ? r.prec : r.slq_prec;
+  return r.kind == 0 && r.prec == GP_PREC_FP32 && slq == GP_PREC_FP32 && 1 + r.nprobe <= 64;
+}
+
+// Two requests share a batch when both are batchable and agree on what one
+// grouped launch needs in common: kernel, dimension class, nprobe, nlanczos.
+inline bool same_batch(const gp_request& a, const gp_request& b) {
+  const int ka = a.nlanczos > 0 ? a.nlanczos : 20, kb = b.nlanczos > 0 ? b.nlanczos : 20;
+  return batchable(a) && batchable(b) && a.kernel == b.kernel && dim_class(a.d) == dim_class(b.d) &&
+         a.nprobe == b.nprobe && ka == kb;
+}
+
+// Largest ratio between the work of two members of one batch: members advance
+// together, so a much smaller member would wait for the larger ones.
+constexpr double kBatchWorkRatio = 16.0;
+
+// The batch of an admitted request `first` (not in the queue any more): up to
+// max_extra queued requests k with compatible(k) and work within
+// kBatchWorkRatio of first_work (either way), taken in order of increasing
+// work (arrival order among equal work) while their blocks fit the pool; their
+// blocks are reserved (offs) and their indices returned in that order.
+template <class Compatible, class Work, class Bytes>
+std::vector<size_t> pick_batch(size_t count, double first_work, int max_extra, PoolAllocator& pool,
+                               Compatible compatible, Work work, Bytes bytes,
+                               std::vector<size_t>* offs) {
+  std::vector<size_t> order, chosen;
+  for (size_t i = 0; i < count; ++i) {
+    const double r = work(i) > first_work ? work(i) / first_work : first_work / work(i);
+    if (compatible(i) && r <= kBatchWorkRatio) order.push_back(i);
+  }
+  std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return work(a) < work(b); });
+  for (size_t i : order) {
+    if (static_cast<int>(chosen.size()) >= max_extra) break;
+    size_t off = 0;
+    if (pool.alloc(bytes(i), &off)) {
+      chosen.push_back(i);
+      offs->push_back(off);
+    }
+  }
+  return chosen;
+}
+
 }  // namespace sched
 }  // namespace gp

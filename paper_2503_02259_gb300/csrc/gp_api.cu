@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cstdlib>
 #include <cstring>
+#include <limits>
 #include <map>
 #include <mutex>
 #include <string>
@@ -17,6 +18,7 @@
 #include <vector>
 
 #include "gp_api_internal.h"
+#include "grad_ard.cuh"
 #include "kmv_tc.cuh"
 #include "residual.cuh"
 #include "vec_kernels.cuh"
@@ -26,6 +28,8 @@ namespace gp {
 // Per-(kernel, grad, dimension) instantiation units (kmv_simt_inst.cu).
 #define GP_SIMT_DECL(K, G, D)                                                                \
   cudaError_t launch_simt_k##K##_g##G##_d##D(const SimtPlan&, const SimtArgs&, cudaStream_t); \
+  cudaError_t launch_simt_group_k##K##_g##G##_d##D(const SimtPlan&, const SimtGroup&,           \
+                                                   cudaStream_t);                              \
   int occupancy_simt_k##K##_g##G##_d##D(int, int);
 #define GP_SIMT_DECL_DT(K, G) \
   GP_SIMT_DECL(K, G, 1)       \
@@ -60,6 +64,19 @@ static cudaError_t launch_simt_dt(int kernel, bool grad, const SimtPlan& p, cons
     if (grad) { GP_SIMT_DT_SWITCH(1, 1, GP_L) } else { GP_SIMT_DT_SWITCH(1, 0, GP_L) }
   }
 #undef GP_L
+  return cudaErrorInvalidValue;
+}
+
+static cudaError_t launch_simt_group_dt(int kernel, bool grad, const SimtPlan& p, const SimtGroup& g,
+                                        cudaStream_t st) {
+  const int dt = p.dt;
+#define GP_G(K, G, D) launch_simt_group_k##K##_g##G##_d##D(p, g, st)
+  if (kernel == 0) {
+    if (grad) { GP_SIMT_DT_SWITCH(0, 1, GP_G) } else { GP_SIMT_DT_SWITCH(0, 0, GP_G) }
+  } else {
+    if (grad) { GP_SIMT_DT_SWITCH(1, 1, GP_G) } else { GP_SIMT_DT_SWITCH(1, 0, GP_G) }
+  }
+#undef GP_G
   return cudaErrorInvalidValue;
 }
 
@@ -133,7 +150,7 @@ void profile_product_end(cudaStream_t st) {
 const char* last_error_cstr() { return t_err.c_str(); }
 
 KernelConsts kernel_consts(int kernel, double l) {
-  KernelConsts k;
+  KernelConsts k{};
   const double log2e = 1.4426950408889634;
   if (kernel == GP_KERNEL_GAUSSIAN) {
     k.cs = static_cast<float>(sqrt(log2e / 2.0) / l);
@@ -141,6 +158,23 @@ KernelConsts kernel_consts(int kernel, double l) {
   } else {
     k.cs = static_cast<float>(sqrt(3.0) / l);
     k.cD = 1.0 / l;
+  }
+  k.ard = false;
+  for (int t = 0; t < GP_MAX_DIM; ++t) {
+    k.csd[t] = k.cs;
+    k.ct[t] = k.cD;
+  }
+  return k;
+}
+
+KernelConsts kernel_consts(const gp_problem* prob) {
+  KernelConsts k = kernel_consts(prob->kernel, prob->theta.l);
+  if (prob->ls == nullptr) return k;
+  k.ard = true;
+  for (int t = 0; t < prob->d && t < GP_MAX_DIM; ++t) {
+    const KernelConsts kt = kernel_consts(prob->kernel, prob->ls[t]);
+    k.csd[t] = kt.cs;
+    k.ct[t] = kt.cD;
   }
   return k;
 }
@@ -233,6 +267,11 @@ SimtPlan plan_for(int64_t nr, int64_t nc, int d, int w, bool grad, int kernel, i
 cudaError_t launch_simt(const SimtPlan& p, int kernel, bool grad, const SimtArgs& a,
                         cudaStream_t st) {
   return launch_simt_dt(kernel, grad, p, a, st);
+}
+
+cudaError_t launch_simt_group(const SimtPlan& plan, int kernel, bool grad, const SimtGroup& g,
+                              cudaStream_t st) {
+  return launch_simt_group_dt(kernel, grad, plan, g, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -381,6 +420,17 @@ static gp_status check_problem(const gp_problem* prob) {
   if (!(t.s > 0) || !(t.f > 0) || !(t.l > 0) || !isfinite(t.s) || !isfinite(t.f) || !isfinite(t.l))
     return fail(GP_ERR_ARG, "theta: s, f, l must be finite and > 0");
   if (prob->n > (int64_t(1) << 31) - 4096) return fail(GP_ERR_ARG, "n too large");
+  if (prob->ls != nullptr)
+    for (int t = 0; t < prob->d; ++t)
+      if (!(prob->ls[t] > 0) || !isfinite(prob->ls[t]))
+        return fail(GP_ERR_ARG, "ls: every per-dimension length-scale must be finite and > 0");
+  return GP_OK;
+}
+
+static gp_status no_ard(const gp_problem* prob, const char* what) {
+  if (prob->ls != nullptr)
+    return fail(GP_ERR_UNIMPLEMENTED,
+                std::string(what) + " takes an isotropic length-scale (problem->ls must be NULL)");
   return GP_OK;
 }
 
@@ -462,15 +512,16 @@ static gp_status product_call(const gp_problem* prob, const float* V, int32_t w,
   if ((s = check_width(w)) != GP_OK) return s;
   if ((s = check_prec(prec)) != GP_OK) return s;
   if (V == nullptr || Y == nullptr) return fail(GP_ERR_ARG, "V and Y must be non-NULL");
+  if (grad && dYl != nullptr && (s = no_ard(prob, "the dKh/dl product")) != GP_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = prob->n;
   const SimtPlan p = plan_for(n, n, prob->d, w, grad, prob->kernel, prec);
   ProdWs L = carve_product(nullptr, p, grad, false, prec);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
   L = carve_product(ws, p, grad, false, prec);
-  const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
+  const KernelConsts kc = kernel_consts(prob);
   GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
-  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.csd, p.dp, p.nc_pad, L.xc, st));
   if (w != p.w_pad) GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
   GP_CUDA(launch_pad_block(V, n, w, w, L.vp, p.nc_pad, p.w_pad, 0, st));
   if ((s = run_product(p, prob->kernel, grad, prec, L.xc, L.xc, L.vp, L.vt, L.part_k, L.part_d,
@@ -686,12 +737,11 @@ struct SolveSetup {
   KernelConsts kc;
 };
 
-static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, int lz_k,
-                             int slq_prec, void* ws, size_t ws_bytes, cudaStream_t st,
-                             SolveSetup& out) {
+static gp_status setup_solve_plans(const gp_problem* prob, const SolvePlans& P, bool with_grad,
+                                   int prec, int lz_k, int slq_prec, void* ws, size_t ws_bytes,
+                                   cudaStream_t st, SolveSetup& out) {
   gp_status s;
   const int64_t n = prob->n;
-  const SolvePlans P = solve_plans(prob, w, prec, lz_k, slq_prec);
   out.pc = P.pc;
   out.pg = P.pg;
   out.pl = P.pl;
@@ -699,12 +749,19 @@ static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int 
   SolveWs L = carve_solve(nullptr, P.pc, P.pg, P.pl, with_grad, lz_k, prec, slq_prec);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
   out.W = carve_solve(ws, P.pc, P.pg, P.pl, with_grad, lz_k, prec, slq_prec);
-  out.kc = kernel_consts(prob->kernel, prob->theta.l);
+  out.kc = kernel_consts(prob);
   GP_CUDA(cudaMemsetAsync(out.W.S, 0, sizeof(CgState), st));
-  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.cs, out.pc.dp,
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, out.kc.csd, out.pc.dp,
                               out.pc.nc_pad, out.W.xs, st));
   GP_CUDA(cudaMemsetAsync(out.W.B, 0, sizeof(float) * out.pc.nr_pad * out.pc.w_pad, st));
   return GP_OK;
+}
+
+static gp_status setup_solve(const gp_problem* prob, int w, bool with_grad, int prec, int lz_k,
+                             int slq_prec, void* ws, size_t ws_bytes, cudaStream_t st,
+                             SolveSetup& out) {
+  return setup_solve_plans(prob, solve_plans(prob, w, prec, lz_k, slq_prec), with_grad, prec, lz_k,
+                           slq_prec, ws, ws_bytes, st, out);
 }
 
 // The arithmetic of the SLQ Lanczos products.
@@ -766,6 +823,21 @@ static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, S
   // V = B with column 0 replaced by alpha (reuse Q as V).
   GP_CUDA(cudaMemcpyAsync(W.Q, W.B, sizeof(float) * pg.nr_pad * pg.w_pad, cudaMemcpyDeviceToDevice, st));
   GP_CUDA(launch_copy_col0(W.X, W.Q, pg.nr_pad, pg.w_pad, st));
+  if (ss.kc.ard) {
+    // Per-dimension length-scales: the s terms from column dot products, the f
+    // and l_t terms from one fused contraction of the entries with Gq and Gt.
+    GP_CUDA(launch_coldots(W.S, W.X, W.Q, pg.nr_pad, pg.w_pad, w, W.red, st));
+    const GradArdPlan g = plan_grad_ard(pg.nr_pad, prob->d);
+    ArdScales c{};
+    for (int t = 0; t < prob->d; ++t) c.v[t] = ss.kc.ct[t];
+    const cudaError_t e = launch_grad_ard(g, prob->kernel, w, p, prob->d, pg.dp, W.xs, W.Q, W.X,
+                                          pg.nr_pad, pg.w_pad, reinterpret_cast<double*>(W.part),
+                                          W.S, prob->theta.f, c, st);
+    if (e == cudaErrorNotSupported)
+      return fail(GP_ERR_UNIMPLEMENTED, "per-dimension length-scales need 1 + nprobe <= 48");
+    if (e != cudaSuccess) return cuda_fail(e, "launch_grad_ard");
+    return GP_OK;
+  }
   float* part_k = W.part;
   float* part_d = W.part + static_cast<size_t>(pg.split) * pg.nr_pad * pg.w_pad;
   if ((s = run_product(pg, prob->kernel, true, GP_PREC_FP32, W.xs, W.xs, W.Q, nullptr, part_k, part_d,
@@ -977,6 +1049,276 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
 }
 
 // ---------------------------------------------------------------------------
+// Batched loss and gradient: several problems advanced together, with one
+// grouped product launch (kmv_simt_group_kernel) per CG iteration, per
+// Lanczos step and for the gradient pass, covering every member; the O(n w)
+// steps stay per member.  FP32 products; the widths are padded up to a
+// grouped TW (batch_plans), so every member shares one instantiation.
+// ---------------------------------------------------------------------------
+namespace {
+
+int group_tw(int tw) {
+  for (int t : kGroupTW)
+    if (t >= tw) return t;
+  return 0;
+}
+
+SolvePlans batch_plans(const gp_problem* prob, int w, int lz_k) {
+  SolvePlans P = solve_plans(prob, w, GP_PREC_FP32, lz_k, GP_PREC_FP32);
+  const int tw = group_tw(P.pc.tw);
+  for (SimtPlan* q : {&P.pc, &P.pg, &P.pl}) {
+    q->tw = tw;
+    q->w_pad = q->ng * tw;
+  }
+  return P;
+}
+
+struct BatchMember {
+  const gp_problem* prob;
+  const float* y;
+  const gp_solve_opts* o;
+  void* ws;
+  size_t ws_bytes;
+  SolveSetup ss;
+  gp_status status = GP_OK;
+};
+
+enum class GroupPhase { kCg, kLanczos, kGrad };
+
+// One grouped product over the members (in the given order); members whose
+// active flag is 0 are skipped on the device.
+gp_status group_product(std::vector<BatchMember*>& M, GroupPhase ph, int j, cudaStream_t st) {
+  SimtGroup g{};
+  g.count = static_cast<int>(M.size());
+  g.counter = &M[0]->ss.W.S->group_counter;
+  int items = 0;
+  for (int k = 0; k < g.count; ++k) {
+    SolveSetup& ss = M[k]->ss;
+    SolveWs& W = ss.W;
+    const SimtPlan& p = ph == GroupPhase::kGrad ? ss.pg : (ph == GroupPhase::kLanczos ? ss.pl : ss.pc);
+    const size_t plane = static_cast<size_t>(p.nr_pad) * p.w_pad;
+    SimtArgs a{W.xs, W.xs, W.P, W.part, nullptr, &W.S->n_active, &W.S->err};
+    if (ph == GroupPhase::kLanczos) {
+      a.v = W.Lq + static_cast<size_t>(j) * plane;
+      a.active = &W.S2->n_active;
+      a.err = &W.S2->err;
+    } else if (ph == GroupPhase::kGrad) {
+      a.v = W.Q;
+      a.part_d = W.part + static_cast<size_t>(p.split) * plane;
+      a.active = nullptr;
+    }
+    g.e[k] = SimtGroupEntry{a, p.nr_pad, p.row_tiles, p.split, p.jtiles, p.jt_per_split, items};
+    items += p.row_tiles * p.split;
+  }
+  g.total_items = items;
+  const SimtPlan& p0 = ph == GroupPhase::kGrad ? M[0]->ss.pg : M[0]->ss.pc;
+  GP_CUDA(cudaMemsetAsync(g.counter, 0, sizeof(int), st));
+  profile_product_begin(st);
+  const cudaError_t e =
+      launch_simt_group(p0, M[0]->prob->kernel, ph == GroupPhase::kGrad, g, st);
+  profile_product_end(st);
+  if (e != cudaSuccess) return cuda_fail(e, "launch_simt_group");
+  return GP_OK;
+}
+
+// One CG iteration of every member: the grouped product, then each member's
+// O(n w) step (fused cooperative launch where it fits).
+gp_status batch_cg_iteration(std::vector<BatchMember*>& M, cudaStream_t st) {
+  gp_status s;
+  if ((s = group_product(M, GroupPhase::kCg, 0, st)) != GP_OK) return s;
+  for (BatchMember* m : M) {
+    const gp_problem* prob = m->prob;
+    const SimtPlan& p = m->ss.pc;
+    SolveWs& W = m->ss.W;
+    const double f2 = prob->theta.f * prob->theta.f;
+    if (thread_cooperative() && cg_fused_wanted() && cg_step_fits(p.nr_pad)) {
+      GP_CUDA(launch_cg_step(W.S, W.part, p.split, W.X, W.R, W.P, W.Q, p.nr_pad, prob->n, p.w_pad,
+                             f2, prob->theta.s, W.red, st));
+    } else {
+      GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, prob->n, p.w_pad, f2,
+                                  prob->theta.s, W.red, st));
+      GP_CUDA(launch_cg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
+      GP_CUDA(launch_cg_pupdate(W.S, W.R, W.P, p.nr_pad, p.w_pad, st));
+    }
+  }
+  return GP_OK;
+}
+
+gp_status batch_run_cg(std::vector<BatchMember*>& M, int maxit, cudaStream_t st) {
+  for (BatchMember* m : M) {
+    const SimtPlan& p = m->ss.pc;
+    SolveWs& W = m->ss.W;
+    GP_CUDA(launch_cg_init(W.S, W.B, W.X, W.R, W.P, p.nr_pad, p.w_pad, 1 + m->o->nprobe,
+                           effective_maxit(m->prob, m->o), m->o->cg_rtol, W.red, st));
+  }
+  std::vector<int> h(2 * M.size());
+  IterationGraph graph;
+  bool tried = false, use_graph = false;
+  int chunk = 4, issued = 0;
+  while (issued < maxit) {
+    const int todo = std::min(chunk, maxit - issued);
+    for (int k = 0; k < todo; ++k) {
+      if (issued + k > 0 && !tried) {
+        tried = true;
+        use_graph = graph.capture([&](cudaStream_t cs) { return batch_cg_iteration(M, cs); });
+      }
+      if (use_graph) {
+        GP_CUDA(graph.launch(st));
+      } else {
+        gp_status s = batch_cg_iteration(M, st);
+        if (s != GP_OK) return s;
+      }
+    }
+    issued += todo;
+    for (size_t k = 0; k < M.size(); ++k)
+      GP_CUDA(cudaMemcpyAsync(&h[2 * k], M[k]->ss.W.S, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+    GP_CUDA(cudaStreamSynchronize(st));
+    bool any = false;
+    for (size_t k = 0; k < M.size(); ++k) {
+      if (h[2 * k + 1] == kDevTimeout) return fail(GP_ERR_TIMEOUT, "a bounded device wait gave up");
+      any = any || (h[2 * k] != 0 && h[2 * k + 1] == 0);
+    }
+    if (!any) break;
+    if (chunk < 32) chunk *= 2;
+  }
+  return GP_OK;
+}
+
+gp_status batch_run_lanczos(std::vector<BatchMember*>& M, int np, int k, cudaStream_t st) {
+  gp_status s;
+  for (BatchMember* m : M) {
+    const SimtPlan& p = m->ss.pl;
+    SolveWs& W = m->ss.W;
+    GP_CUDA(cudaMemsetAsync(W.S2, 0, sizeof(CgState), st));
+    GP_CUDA(launch_lz_init(W.S2, W.B, W.Lq, p.nr_pad, p.w_pad, 1, np, W.red, st));
+  }
+  for (int j = 0; j < k; ++j) {
+    if ((s = group_product(M, GroupPhase::kLanczos, j, st)) != GP_OK) return s;
+    for (BatchMember* m : M) {
+      const gp_problem* prob = m->prob;
+      const SimtPlan& p = m->ss.pl;
+      SolveWs& W = m->ss.W;
+      CgState* S = W.S2;
+      const float* Qj = W.Lq + static_cast<size_t>(j) * p.nr_pad * p.w_pad;
+      GP_CUDA(launch_lz_epi_alpha(S, W.part, p.split, Qj, W.R, p.nr_pad, prob->n, p.w_pad,
+                                  prob->theta.f * prob->theta.f, prob->theta.s, j, W.red, st));
+      GP_CUDA(launch_lz_three_term(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, st));
+      GP_CUDA(launch_lz_reorth(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, W.red, st));
+      GP_CUDA(launch_lz_reorth(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, W.red, st));
+      GP_CUDA(launch_lz_norm_next(S, W.R, W.Lq, p.nr_pad, p.w_pad, j, k, W.red, st));
+    }
+  }
+  for (BatchMember* m : M) {
+    SolveWs& W = m->ss.W;
+    GP_CUDA(launch_slq(W.S2, 1, np, k, st));
+    GP_CUDA(cudaMemcpyAsync(W.S->out, W.S2->out, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  return GP_OK;
+}
+
+gp_status check_batch(int32_t count, const gp_problem* probs, const float* const* ys,
+                      const gp_solve_opts* opts) {
+  gp_status s;
+  if (count < 1 || count > kMaxGroup) return fail(GP_ERR_ARG, "count must be in [1, 64]");
+  if (probs == nullptr || ys == nullptr || opts == nullptr)
+    return fail(GP_ERR_ARG, "probs, y and opts must be non-NULL");
+  for (int k = 0; k < count; ++k) {
+    if ((s = check_problem(&probs[k])) != GP_OK) return s;
+    if ((s = check_opts(&opts[k], false)) != GP_OK) return s;
+    if (ys[k] == nullptr) return fail(GP_ERR_ARG, "y[k] is NULL");
+    if (probs[k].ls != nullptr)
+      return fail(GP_ERR_UNIMPLEMENTED, "batched solves take isotropic length-scales");
+    if (opts[k].prec != GP_PREC_FP32 || slq_prec_of(&opts[k]) != GP_PREC_FP32)
+      return fail(GP_ERR_UNIMPLEMENTED, "batched solves use FP32 products");
+    if (1 + opts[k].nprobe > 64) return fail(GP_ERR_UNIMPLEMENTED, "batched solves need 1 + nprobe <= 64");
+    if (probs[k].kernel != probs[0].kernel || dim_template(probs[k].d) != dim_template(probs[0].d))
+      return fail(GP_ERR_ARG, "batch members must share the kernel and the dimension template");
+    if (opts[k].nprobe != opts[0].nprobe || opts[k].nlanczos != opts[0].nlanczos)
+      return fail(GP_ERR_ARG, "batch members must share nprobe and nlanczos");
+  }
+  return GP_OK;
+}
+
+}  // namespace
+
+static gp_status loss_and_grad_batch(int32_t count, const gp_problem* probs, const float* const* ys,
+                                     const gp_solve_opts* opts, double* loss, double* grad,
+                                     gp_loss_info* info, int32_t* status, void* const* ws,
+                                     const size_t* ws_bytes, cudaStream_t st) {
+  gp_status s;
+  if ((s = check_batch(count, probs, ys, opts)) != GP_OK) return s;
+  if (ws == nullptr || ws_bytes == nullptr) return fail(GP_ERR_ARG, "ws and ws_bytes must be non-NULL");
+  std::vector<BatchMember> mem(count);
+  const int p = opts[0].nprobe;
+  const int w = 1 + p;
+  const int lz_k = p > 0 ? opts[0].nlanczos : 0;
+  int maxit = 0;
+  for (int k = 0; k < count; ++k) {
+    BatchMember& m = mem[k];
+    m.prob = &probs[k];
+    m.y = ys[k];
+    m.o = &opts[k];
+    const SolvePlans P = batch_plans(m.prob, w, lz_k);
+    if ((s = setup_solve_plans(m.prob, P, true, GP_PREC_FP32, lz_k, GP_PREC_FP32, ws[k],
+                               ws_bytes[k], st, m.ss)) != GP_OK)
+      return s;
+    SolveWs& W = m.ss.W;
+    GP_CUDA(launch_pad_block(m.y, m.prob->n, 1, 1, W.B, m.ss.pc.nr_pad, m.ss.pc.w_pad, 0, st));
+    if ((s = fill_probes(m.prob, m.o, W.B, m.ss.pc.nr_pad, m.ss.pc.w_pad, 1, st)) != GP_OK) return s;
+    maxit = std::max(maxit, effective_maxit(m.prob, m.o));
+  }
+  // Largest problems first, so that the persistent CTAs start on the longest items.
+  std::vector<BatchMember*> M;
+  for (BatchMember& m : mem) M.push_back(&m);
+  std::stable_sort(M.begin(), M.end(),
+                   [](const BatchMember* a, const BatchMember* b) { return a->prob->n > b->prob->n; });
+  // The loop runs to the largest cg_maxit; each member's state carries its own
+  // cap, after which its columns are inactive and its tiles are skipped.
+  if ((s = batch_run_cg(M, maxit, st)) != GP_OK) return s;
+  if (p > 0 && (s = batch_run_lanczos(M, p, opts[0].nlanczos, st)) != GP_OK) return s;
+  for (BatchMember* m : M) {
+    SolveWs& W = m->ss.W;
+    const SimtPlan& pc = m->ss.pc;
+    GP_CUDA(launch_yalpha(W.S, W.B, W.X, pc.nr_pad, pc.w_pad, W.red, st));
+    GP_CUDA(launch_assemble(W.S, m->prob->n, p, st));
+    // Gradient pass operands: V = B with column 0 replaced by alpha.
+    const SimtPlan& pg = m->ss.pg;
+    GP_CUDA(cudaMemcpyAsync(W.Q, W.B, sizeof(float) * pg.nr_pad * pg.w_pad, cudaMemcpyDeviceToDevice,
+                            st));
+    GP_CUDA(launch_copy_col0(W.X, W.Q, pg.nr_pad, pg.w_pad, st));
+  }
+  if ((s = group_product(M, GroupPhase::kGrad, 0, st)) != GP_OK) return s;
+  for (BatchMember* m : M) {
+    SolveWs& W = m->ss.W;
+    const SimtPlan& pg = m->ss.pg;
+    const double f = m->prob->theta.f;
+    float* part_k = W.part;
+    float* part_d = W.part + static_cast<size_t>(pg.split) * pg.nr_pad * pg.w_pad;
+    GP_CUDA(launch_grad_dots(W.S, part_k, part_d, pg.split, W.Q, W.X, pg.nr_pad, pg.w_pad, w,
+                             2.0 * f, f * f * m->ss.kc.cD, W.red, st));
+    GP_CUDA(launch_assemble(W.S, m->prob->n, p, st));
+  }
+  gp_status worst = GP_OK;
+  for (int k = 0; k < count; ++k) {
+    BatchMember& m = mem[k];
+    double out[16];
+    gp_status sk = read_outputs(m.ss.W.S, p > 0 ? m.ss.W.S2 : nullptr, w, out,
+                                info ? &info[k] : nullptr, st);
+    if (sk == GP_OK) {
+      if (loss) loss[k] = out[2];
+      if (grad)
+        for (int t = 0; t < 3; ++t) grad[3 * k + t] = out[3 + t];
+      sk = check_conv(m.ss.W.S, w, effective_maxit(m.prob, m.o), m.o->cg_rtol, st);
+    }
+    if (status) status[k] = sk;
+    if (sk != GP_OK && (worst == GP_OK || worst == GP_ERR_NOT_CONVERGED)) worst = sk;
+  }
+  if (worst == GP_ERR_NOT_CONVERGED)
+    return fail(GP_ERR_NOT_CONVERGED, "a batch member reached cg_maxit before cg_rtol");
+  return worst;
+}
+
+// ---------------------------------------------------------------------------
 // Exported entry points.
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -1025,6 +1367,25 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
       if (check_width(w) != GP_OK) return 0;
       return carve_residual(nullptr, n, w).bytes;
     }
+    case GP_OP_LOSS_GRAD_BATCH: {
+      if (check_opts(opts, false) != GP_OK) return 0;
+      if (1 + opts->nprobe > 64) {
+        set_error("batched solves need 1 + nprobe <= 64");
+        return 0;
+      }
+      const int lz_k = opts->nprobe > 0 ? opts->nlanczos : 0;
+      const SolvePlans P = batch_plans(prob, 1 + opts->nprobe, lz_k);
+      return carve_solve(nullptr, P.pc, P.pg, P.pl, true, lz_k, GP_PREC_FP32, GP_PREC_FP32).bytes;
+    }
+    case GP_OP_PREDICT_VAR: {
+      if (w < 1) {
+        set_error("predict_var: m must be >= 1");
+        return 0;
+      }
+      const int wb = static_cast<int>(std::min<int64_t>(w, GP_MAX_COLS));
+      const SolvePlans P = solve_plans(prob, wb, prec, 0, prec);
+      return carve_solve(nullptr, P.pc, P.pg, P.pl, false, 0, prec, prec).bytes;
+    }
     case GP_OP_PCG: {
       if (check_width(w) != GP_OK) return 0;
       SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
@@ -1068,6 +1429,9 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if ((s = check_opts(opts, false)) != GP_OK) return s;
   if (B == nullptr || Xsol == nullptr) return fail(GP_ERR_ARG, "B and Xsol must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0 &&
+      (s = no_ard(prob, "iterative refinement")) != GP_OK)
+    return s;
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
     return refine_solve(prob, B, w, Xsol, nullptr, opts, iters, relres, ws, ws_bytes, st);
   SolveSetup ss;
@@ -1096,6 +1460,7 @@ gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w
   if ((s = check_opts(opts, false)) != GP_OK) return s;
   if (B == nullptr || X64 == nullptr) return fail(GP_ERR_ARG, "B and X64 must be non-NULL");
   if (!(opts->refine_rtol > 0)) return fail(GP_ERR_ARG, "refine_rtol must be > 0");
+  if ((s = no_ard(prob, "iterative refinement")) != GP_OK) return s;
   return refine_solve(prob, B, w, nullptr, X64, opts, iters, relres, ws, ws_bytes,
                       static_cast<cudaStream_t>(stream));
 }
@@ -1107,6 +1472,7 @@ gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* 
   if ((s = check_width(w)) != GP_OK) return s;
   if (B == nullptr || X == nullptr || relres == nullptr)
     return fail(GP_ERR_ARG, "B, X and relres must be non-NULL");
+  if ((s = no_ard(prob, "gp_true_residual")) != GP_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = prob->n;
   const int64_t n_pad = round_up(n, kPad);
@@ -1144,6 +1510,7 @@ gp_status gp_residual_rows(const gp_problem* prob, const float* B, const double*
   if (arith != GP_RESIDUAL_PAIR && arith != GP_RESIDUAL_FP64)
     return fail(GP_ERR_ARG, "arith must be GP_RESIDUAL_PAIR or GP_RESIDUAL_FP64");
   if (R == nullptr && relres == nullptr) return fail(GP_ERR_ARG, "R and relres are both NULL");
+  if ((s = no_ard(prob, "gp_residual_rows")) != GP_OK) return s;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t n = prob->n;
   if ((s = check_ws(ws, ws_bytes, carve_residual(nullptr, n, w).bytes)) != GP_OK) return s;
@@ -1194,6 +1561,40 @@ gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, doubl
   return GP_OK;
 }
 
+// Gradient outputs of a backward pass: grad[3] (s, f, l), or grad[2 + d]
+// (s, f, l_1..l_d) with per-dimension length-scales, whose info->quad/trace
+// hold s and f in [0..1] and NaN in [2] (and no standard errors).
+static gp_status write_grad(const gp_problem* prob, const SolveSetup& ss, const double out[16],
+                            double* grad, gp_loss_info* info, cudaStream_t st) {
+  if (!ss.kc.ard) {
+    if (grad)
+      for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
+    if (info != nullptr)
+      for (int t = 0; t < 3; ++t) {
+        info->quad[t] = out[6 + t];
+        info->trace[t] = out[9 + t];
+        info->trace_stderr[t] = out[12 + t];
+      }
+    return GP_OK;
+  }
+  double g[2 + GP_MAX_DIM], q[2 + GP_MAX_DIM], tr[2 + GP_MAX_DIM];
+  GP_CUDA(cudaMemcpyAsync(g, ss.W.S->ard_grad, sizeof(g), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaMemcpyAsync(q, ss.W.S->ard_quad, sizeof(q), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaMemcpyAsync(tr, ss.W.S->ard_trace, sizeof(tr), cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  if (grad)
+    for (int t = 0; t < 2 + prob->d; ++t) grad[t] = g[t];
+  if (info != nullptr) {
+    const double nan = std::numeric_limits<double>::quiet_NaN();
+    for (int t = 0; t < 3; ++t) {
+      info->quad[t] = t < 2 ? q[t] : nan;
+      info->trace[t] = t < 2 ? tr[t] : nan;
+      info->trace_stderr[t] = nan;
+    }
+  }
+  return GP_OK;
+}
+
 gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
                            double* loss, double* grad, gp_loss_info* info, void* ws, size_t ws_bytes,
                            void* stream) {
@@ -1211,9 +1612,16 @@ gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solv
                         st)) != GP_OK)
     return s;
   if (loss) *loss = out[2];
-  if (grad)
-    for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
+  if ((s = write_grad(prob, ss, out, grad, info, st)) != GP_OK) return s;
   return check_conv(ss.W.S, 1 + opts->nprobe, effective_maxit(prob, opts), opts->cg_rtol, st);
+}
+
+gp_status gp_loss_and_grad_batch(int32_t count, const gp_problem* probs, const float* const* y,
+                                 const gp_solve_opts* opts, double* loss, double* grad,
+                                 gp_loss_info* info, int32_t* status, void* const* ws,
+                                 const size_t* ws_bytes, void* stream) {
+  return loss_and_grad_batch(count, probs, y, opts, loss, grad, info, status, ws, ws_bytes,
+                             static_cast<cudaStream_t>(stream));
 }
 
 gp_status gp_nll_forward(const gp_problem* prob, const float* y, const gp_solve_opts* opts, float* W,
@@ -1256,15 +1664,7 @@ gp_status gp_nll_backward(const gp_problem* prob, const gp_solve_opts* opts, con
   double out[16];
   GP_CUDA(cudaMemcpyAsync(out, ss.W.S->out, sizeof(out), cudaMemcpyDeviceToHost, st));
   GP_CUDA(cudaStreamSynchronize(st));
-  if (grad)
-    for (int t = 0; t < 3; ++t) grad[t] = out[3 + t];
-  if (info != nullptr) {
-    for (int t = 0; t < 3; ++t) {
-      info->quad[t] = out[6 + t];
-      info->trace[t] = out[9 + t];
-      info->trace_stderr[t] = out[12 + t];
-    }
-  }
+  if ((s = write_grad(prob, ss, out, grad, info, st)) != GP_OK) return s;
   return device_status(&ss.W.S->err, st);
 }
 
@@ -1282,10 +1682,10 @@ gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const floa
   ProdWs L = carve_product(nullptr, p, false, true, GP_PREC_FP32);
   if ((s = check_ws(ws, ws_bytes, L.bytes)) != GP_OK) return s;
   L = carve_product(ws, p, false, true, GP_PREC_FP32);
-  const KernelConsts kc = kernel_consts(prob->kernel, prob->theta.l);
+  const KernelConsts kc = kernel_consts(prob);
   GP_CUDA(cudaMemsetAsync(L.err, 0, sizeof(int), st));
-  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, L.xc, st));
-  GP_CUDA(launch_stage_points(Xstar, m, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nr_pad, L.xr, st));
+  GP_CUDA(launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.csd, p.dp, p.nc_pad, L.xc, st));
+  GP_CUDA(launch_stage_points(Xstar, m, prob->d, prob->d, prob->X, kc.csd, p.dp, p.nr_pad, L.xr, st));
   GP_CUDA(cudaMemsetAsync(L.vp, 0, sizeof(float) * p.nc_pad * p.w_pad, st));
   GP_CUDA(launch_pad_block(alpha, n, 1, 1, L.vp, p.nc_pad, p.w_pad, 0, st));
   if ((s = run_product(p, prob->kernel, false, GP_PREC_FP32, L.xr, L.xc, L.vp, nullptr, L.part_k, nullptr,
@@ -1303,6 +1703,52 @@ gp_status gp_predict_mean(const gp_problem* prob, const float* alpha, const floa
   e.ldy = 1;
   e.err = L.err;
   GP_CUDA(launch_epilogue(e, st));
+  return GP_OK;
+}
+
+gp_status gp_predict_var(const gp_problem* prob, const float* Xstar, int64_t m, float* var,
+                         const gp_solve_opts* opts, int32_t* iters_max, double* relres_max,
+                         void* ws, size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if (Xstar == nullptr || var == nullptr) return fail(GP_ERR_ARG, "Xstar and var must be non-NULL");
+  if (m < 1 || m > (int64_t(1) << 31) - 4096) return fail(GP_ERR_ARG, "m out of range");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  const int prec = opts->prec;
+  const int wb = static_cast<int>(std::min<int64_t>(m, GP_MAX_COLS));
+  SolveSetup ss;
+  if ((s = setup_solve(prob, wb, false, prec, 0, prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  const double f2 = prob->theta.f * prob->theta.f;
+  const int maxit = effective_maxit(prob, opts);
+  double inv_l[GP_MAX_DIM];
+  for (int t = 0; t < prob->d; ++t) inv_l[t] = 1.0 / (prob->ls ? prob->ls[t] : prob->theta.l);
+  int it_max = 0;
+  double rel_max = 0.0;
+  bool conv = true;
+  // Test points in blocks of up to GP_MAX_COLS columns: B = f^2 K(X, X*_block),
+  // U = Kh^-1 B by block CG, var = f^2 - diag(B^T U).
+  for (int64_t c0 = 0; c0 < m; c0 += wb) {
+    const int wl = static_cast<int>(std::min<int64_t>(wb, m - c0));
+    GP_CUDA(cudaMemsetAsync(ss.W.S, 0, sizeof(CgState), st));
+    GP_CUDA(cudaMemsetAsync(ss.W.S2, 0, sizeof(CgState), st));
+    GP_CUDA(launch_cross_cols(prob->X, n, prob->d, Xstar + c0 * prob->d, wl, prob->kernel, inv_l,
+                              f2, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, st));
+    if ((s = run_cg(prob, ss.pc, prec, ss.W, wl, maxit, opts->cg_rtol, st)) != GP_OK) return s;
+    GP_CUDA(launch_pred_var(ss.W.S2, ss.W.B, ss.W.X, ss.pc.nr_pad, ss.pc.w_pad, wl, f2, var + c0,
+                            ss.W.red, st));
+    HostCg h;
+    if ((s = read_cg(ss.W.S, h, st)) != GP_OK) return s;
+    for (int c = 0; c < wl; ++c) {
+      it_max = std::max(it_max, h.iters[c]);
+      rel_max = std::max(rel_max, h.relres[c]);
+      conv = conv && !(h.relres[c] > opts->cg_rtol);
+    }
+  }
+  if (iters_max) *iters_max = it_max;
+  if (relres_max) *relres_max = rel_max;
+  if (!conv) return fail(GP_ERR_NOT_CONVERGED, "predict_var: CG reached cg_maxit before cg_rtol");
   return GP_OK;
 }
 

@@ -33,12 +33,19 @@ constexpr long long kSpinLimit = 1ll << 22;
 //   Gaussian : q = r^2 log2(e) / (2 l^2);  k = 2^-q;        D' = k q
 //   Matern32 : q = 3 r^2 / l^2, a = sqrt(q); k = (1+a) 2^-(a log2 e); D' = a^2 e^-a
 // and dk/dl = cD * D'  with cD = 2/(l log2 e) (Gaussian) or 1/l (Matern32).
+// With per-dimension length-scales l_t (gp_problem.ls) coordinate t is scaled
+// by csd[t], the same formula with l_t, and dk/dl_t = ct[t] E dd_t (see
+// grad_ard.cu) with ct[t] the cD formula at l_t.
 // ---------------------------------------------------------------------------
 struct KernelConsts {
-  float cs;        // coordinate scale
-  double cD;       // derivative scale
+  float cs;                  // coordinate scale (isotropic)
+  double cD;                 // derivative scale (isotropic)
+  bool ard;                  // per-dimension length-scales
+  float csd[GP_MAX_DIM];     // coordinate scale per dimension (all cs when isotropic)
+  double ct[GP_MAX_DIM];     // derivative scale per dimension (ARD)
 };
 KernelConsts kernel_consts(int kernel, double l);
+KernelConsts kernel_consts(const gp_problem* prob);
 
 // Padded dimension used for the AoS point layout of a problem of dimension d.
 int dim_template(int d);   // 1,2,3,4,8,16: the compile-time dimension
@@ -72,6 +79,30 @@ struct SimtArgs {
 };
 cudaError_t launch_simt(const SimtPlan& p, int kernel, bool grad, const SimtArgs& a,
                         cudaStream_t st);
+
+// Several problems' products in one persistent launch (kmv_simt_group_kernel):
+// the problems share kernel, grad, dimension template, TW, ng and w_pad; the
+// table travels as a kernel parameter.  Work items are numbered problem by
+// problem: item0 is the first item of entry k, and an entry's items are
+// (row tile, split) in row-tile-fastest order.
+constexpr int kMaxGroup = 64;
+// TW values the grouped product is built for (a group pads w up to one).
+constexpr int kGroupTW[4] = {4, 12, 20, 36};
+struct SimtGroupEntry {
+  SimtArgs a;
+  int64_t nr_pad;
+  int row_tiles, split, jtiles, jt_per_split;
+  int item0;
+};
+struct SimtGroup {
+  int count;
+  int total_items;
+  int* counter;   // device word, zero before the launch
+  SimtGroupEntry e[kMaxGroup];
+};
+// plan: the shared dt / tw / ng / w_pad (of any member); blocks: persistent CTAs.
+cudaError_t launch_simt_group(const SimtPlan& plan, int kernel, bool grad, const SimtGroup& g,
+                              cudaStream_t st);
 // Occupancy (resident CTAs per SM) of one instantiation.
 int simt_occupancy(int kernel, bool grad, int dt, int tw, int w_pad, int dp);
 

@@ -81,9 +81,19 @@ __device__ __forceinline__ void load_row_point(const float* xr, int64_t i, float
   }
 }
 
+// One work item of the product: row tile `row_tile` and j-split `s` of the
+// problem `a`, on the calling CTA (shared memory smem_raw).  Returns
+// kTileSkipped if the problem's active flag is 0 (nothing touched),
+// kTileDone, or kTileTimeout if a bounded wait gave up (the CTA's copies are
+// drained, bounded, and *a.err is set).
+constexpr int kTileSkipped = 0;
+constexpr int kTileDone = 1;
+constexpr int kTileTimeout = 2;
+
 template <int KIND, bool GRAD, int DT, int TW>
-__global__ void __launch_bounds__(kThreads)
-    kmv_simt_kernel(SimtArgs a, int w_pad, int ng, int64_t nr_pad, int jtiles, int jt_per_split) {
+__device__ __forceinline__ int simt_tile(const SimtArgs& a, int w_pad, int ng, int64_t nr_pad,
+                                          int jtiles, int jt_per_split, int row_tile, int s,
+                                          unsigned char* smem_raw) {
   constexpr int DP = DimTraits<DT>::DP;
   constexpr int TW2 = TW / 2;
   // Quads of entries per loop iteration: eight let the scheduler overlap one
@@ -92,9 +102,8 @@ __global__ void __launch_bounds__(kThreads)
   constexpr int kQuadUnroll = DT >= 16 ? 2 : (DT >= 8 ? 4 : 8);
   static_assert(TW % 4 == 0, "TW must be a multiple of 4");
 
-  if (a.active != nullptr && *a.active == 0) return;
+  if (a.active != nullptr && *a.active == 0) return kTileSkipped;
 
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
   float* sX = reinterpret_cast<float*>(smem_raw + 128);
   float* sV = sX + 2 * kBN * DP;
@@ -103,8 +112,7 @@ __global__ void __launch_bounds__(kThreads)
   const int bm = kBM / ng;
   const int g = tid / bm;
   const int r = tid - g * bm;
-  const int64_t row = static_cast<int64_t>(blockIdx.x) * bm + r;
-  const int s = blockIdx.y;
+  const int64_t row = static_cast<int64_t>(row_tile) * bm + r;
   const int jt0 = s * jt_per_split;
   const int jt1 = min(jt0 + jt_per_split, jtiles);
   const int T = jt1 - jt0;
@@ -157,7 +165,7 @@ __global__ void __launch_bounds__(kThreads)
         dev::mbar_wait(&bars[stage], parity);
         if (t + 1 < T) dev::mbar_wait(&bars[stage ^ 1], ((t + 1) >> 1) & 1);
       }
-      return;
+      return kTileTimeout;
     }
     const float* xs = sX + stage * kBN * DP;
     const float* vs = sV + stage * kBN * w_pad + g * TW;
@@ -212,6 +220,54 @@ __global__ void __launch_bounds__(kThreads)
 #pragma unroll
     for (int c = 0; c < TW / 4; ++c)
       pd[c] = make_float4(runD[2 * c].x, runD[2 * c].y, runD[2 * c + 1].x, runD[2 * c + 1].y);
+  }
+  return kTileDone;
+}
+
+template <int KIND, bool GRAD, int DT, int TW>
+__global__ void __launch_bounds__(kThreads)
+    kmv_simt_kernel(SimtArgs a, int w_pad, int ng, int64_t nr_pad, int jtiles, int jt_per_split) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  simt_tile<KIND, GRAD, DT, TW>(a, w_pad, ng, nr_pad, jtiles, jt_per_split, blockIdx.x, blockIdx.y,
+                                smem_raw);
+}
+
+// The product of several problems in one persistent launch: every CTA takes
+// work items (problem, row tile, j-split) from a global counter until none is
+// left, so the tiles of all the problems share the SMs.  Each item writes its
+// own partial-sum slot, so the result does not depend on which CTA ran it.
+// The problems share the instantiation (kernel, grad, dimension template, TW)
+// and the padded width; the table is a kernel parameter.
+template <int KIND, bool GRAD, int DT, int TW>
+__global__ void __launch_bounds__(kThreads)
+    kmv_simt_group_kernel(const __grid_constant__ SimtGroup G, int w_pad, int ng) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  __shared__ int item_s;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);
+  for (;;) {
+    if (threadIdx.x == 0) item_s = atomicAdd(G.counter, 1);
+    __syncthreads();
+    const int item = item_s;
+    if (item >= G.total_items) return;
+    int k = 0;
+    while (k + 1 < G.count && G.e[k + 1].item0 <= item) ++k;
+    const SimtGroupEntry& e = G.e[k];
+    const int local = item - e.item0;
+    const int row_tile = local % e.row_tiles;
+    const int split = local / e.row_tiles;
+    const int st = simt_tile<KIND, GRAD, DT, TW>(e.a, w_pad, ng, e.nr_pad, e.jtiles,
+                                                 e.jt_per_split, row_tile, split, smem_raw);
+    // A timed-out item may leave a copy in flight: this CTA stops (the
+    // problem's error word is set; the other CTAs finish the other items).
+    if (st == kTileTimeout) return;
+    // Every thread is past the item (it has read item_s, and its barriers are
+    // idle); a finished item's barriers are invalidated so that the next item
+    // initialises them afresh.
+    __syncthreads();
+    if (st == kTileDone && threadIdx.x == 0) {
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(dev::smem_addr(&bars[0])) : "memory");
+      asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(dev::smem_addr(&bars[1])) : "memory");
+    }
   }
 }
 

@@ -74,6 +74,9 @@ bool layout_of(const gp_request& r, JobLayout* L) {
   if (r.kind == 0) {
     const gp_solve_opts o = opts_of(r, true);
     wsb = gp_workspace_bytes(GP_OP_LOSS_GRAD, &prob, 0, &o);
+    // A request that may run in a batch gets room for either workspace.
+    if (gp::sched::batchable(r))
+      wsb = std::max(wsb, gp_workspace_bytes(GP_OP_LOSS_GRAD_BATCH, &prob, 0, &o));
   } else {
     L->xs = take(sizeof(float) * r.m * r.d);
     L->mu = take(sizeof(float) * r.m);
@@ -125,10 +128,18 @@ struct gp_server {
   std::deque<std::shared_ptr<Job>> queue;
   std::map<uint64_t, std::shared_ptr<Job>> jobs;
   std::vector<std::thread> workers;
+  // Start-up latch: each worker reports whether it created its streams;
+  // gp_server_create waits for every report (cv_start).
+  int workers_ready = 0, workers_failed = 0;
+  std::condition_variable cv_start;
   bool stop = false;
   uint64_t next_ticket = 1;
   int64_t submitted = 0, completed = 0, refused = 0, active = 0, peak_active = 0;
   size_t peak_bytes = 0;
+  // Grouped launches: up to max_batch compatible loss + gradient requests run
+  // as one gp_loss_and_grad_batch (1: every request alone).
+  int max_batch = 1;
+  int64_t batches = 0, batched_requests = 0, largest_batch = 0;
   std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
 };
 
@@ -196,6 +207,53 @@ void run_job(gp_server* srv, Job& j, char* base, cudaStream_t st) {
   (void)srv;
 }
 
+// Run a batch of compatible loss + gradient requests (each in its own pool
+// block) as one gp_loss_and_grad_batch on `st`; fills every job's result.
+void run_batch(std::vector<std::shared_ptr<Job>>& jobs, const std::vector<char*>& bases,
+               cudaStream_t st) {
+  const size_t count = jobs.size();
+  std::vector<gp_problem> probs(count);
+  std::vector<gp_solve_opts> opts(count);
+  std::vector<const float*> ys(count);
+  std::vector<void*> ws(count);
+  std::vector<size_t> wsb(count);
+  std::vector<double> loss(count), grad(3 * count);
+  std::vector<gp_loss_info> info(count);
+  std::vector<int32_t> status(count, GP_ERR_CUDA);
+  bool copied = true;
+  for (size_t k = 0; k < count; ++k) {
+    Job& j = *jobs[k];
+    const gp_request& r = j.req;
+    float* dX = reinterpret_cast<float*>(bases[k] + j.lay.x);
+    float* dy = reinterpret_cast<float*>(bases[k] + j.lay.y);
+    copied = copied && cudaMemcpyAsync(dX, j.hX, sizeof(float) * r.n * r.d, cudaMemcpyHostToDevice,
+                                       st) == cudaSuccess;
+    copied = copied &&
+             cudaMemcpyAsync(dy, j.hy, sizeof(float) * r.n, cudaMemcpyHostToDevice, st) == cudaSuccess;
+    probs[k] = gp_problem{dX, r.n, r.d, r.kernel, r.theta, nullptr};
+    opts[k] = opts_of(r, true);
+    ys[k] = dy;
+    ws[k] = bases[k] + j.lay.ws;
+    wsb[k] = j.lay.ws_bytes;
+  }
+  gp_status s = GP_ERR_CUDA;
+  if (copied)
+    s = gp_loss_and_grad_batch(static_cast<int32_t>(count), probs.data(), ys.data(), opts.data(),
+                               loss.data(), grad.data(), info.data(), status.data(), ws.data(),
+                               wsb.data(), st);
+  cudaStreamSynchronize(st);
+  for (size_t k = 0; k < count; ++k) {
+    gp_result& res = jobs[k]->res;
+    // Per-member status when the call ran; the call's own status otherwise.
+    const bool ran = s == GP_OK || s == GP_ERR_NOT_CONVERGED;
+    res.status = ran ? static_cast<gp_status>(status[k]) : s;
+    res.loss = loss[k];
+    for (int t = 0; t < 3; ++t) res.grad[t] = grad[3 * k + t];
+    res.cg_iters = info[k].cg_iters;
+    res.relres = info[k].relres_max;
+  }
+}
+
 using gp::sched::kAgeSeconds;
 using gp::sched::priority_level;
 using gp::sched::request_work;
@@ -221,36 +279,78 @@ void worker_main(gp_server* srv) {
   if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
   const int levels = std::max(1, std::min(8, least - greatest + 1));
   std::vector<cudaStream_t> streams(levels, nullptr);
-  for (int i = 0; i < levels; ++i) {
+  bool ok = true;
+  for (int i = 0; i < levels && ok; ++i) {
     // Level i has the i-th highest priority (numerically greatest + i).
     if (cudaStreamCreateWithPriority(&streams[i], cudaStreamNonBlocking, greatest + i) != cudaSuccess) {
+      cudaGetLastError();
       for (int k = 0; k < i; ++k) cudaStreamDestroy(streams[k]);
-      return;
+      ok = false;
     }
   }
+  {
+    std::lock_guard<std::mutex> lk(srv->mu);
+    if (ok)
+      ++srv->workers_ready;
+    else
+      ++srv->workers_failed;
+  }
+  srv->cv_start.notify_all();
+  if (!ok) return;   // gp_server_create reports the failure and stops the others
   for (;;) {
-    std::shared_ptr<Job> job;
-    size_t off = 0;
+    std::vector<std::shared_ptr<Job>> batch;
+    std::vector<size_t> offs;
     {
+      std::shared_ptr<Job> job;
+      size_t off = 0;
       std::unique_lock<std::mutex> lk(srv->mu);
       // Re-check at least every 100 ms, so that a request reaching kAgeSeconds
       // is noticed without another event.
       while (!srv->stop && !admit_next(srv, &job, &off))
         srv->cv_work.wait_for(lk, std::chrono::milliseconds(100));
       if (srv->stop) break;
-      ++srv->active;
+      batch.push_back(job);
+      offs.push_back(off);
+      if (srv->max_batch > 1 && gp::sched::batchable(job->req)) {
+        auto& q = srv->queue;
+        const std::vector<size_t> extra = gp::sched::pick_batch(
+            q.size(), job->work, srv->max_batch - 1, *srv->alloc,
+            [&](size_t k) { return gp::sched::same_batch(job->req, q[k]->req); },
+            [&](size_t k) { return q[k]->work; }, [&](size_t k) { return q[k]->lay.total; }, &offs);
+        for (size_t k : extra) batch.push_back(q[k]);
+        std::vector<size_t> rm(extra);
+        std::sort(rm.rbegin(), rm.rend());
+        for (size_t k : rm) q.erase(q.begin() + static_cast<long>(k));
+      }
+      srv->active += static_cast<int64_t>(batch.size());
       srv->peak_active = std::max(srv->peak_active, srv->active);
       srv->peak_bytes = std::max(srv->peak_bytes, srv->alloc->in_use());
-      job->res.t_start_s = seconds_since(srv->t0);
+      const double now = seconds_since(srv->t0);
+      for (auto& j : batch) j->res.t_start_s = now;
+      if (batch.size() > 1) {
+        ++srv->batches;
+        srv->batched_requests += static_cast<int64_t>(batch.size());
+        srv->largest_batch = std::max<int64_t>(srv->largest_batch, static_cast<int64_t>(batch.size()));
+      }
     }
-    run_job(srv, *job, srv->pool + off, streams[priority_level(job->req, levels)]);
+    cudaStream_t st = streams[priority_level(batch[0]->req, levels)];
+    if (batch.size() == 1) {
+      run_job(srv, *batch[0], srv->pool + offs[0], st);
+    } else {
+      std::vector<char*> bases;
+      for (size_t o : offs) bases.push_back(srv->pool + o);
+      run_batch(batch, bases, st);
+    }
     {
       std::lock_guard<std::mutex> lk(srv->mu);
-      srv->alloc->release(off, job->lay.total);
-      --srv->active;
-      ++srv->completed;
-      job->res.t_done_s = seconds_since(srv->t0);
-      job->done = true;
+      const double now = seconds_since(srv->t0);
+      for (size_t k = 0; k < batch.size(); ++k) {
+        srv->alloc->release(offs[k], batch[k]->lay.total);
+        --srv->active;
+        ++srv->completed;
+        batch[k]->res.t_done_s = now;
+        batch[k]->done = true;
+      }
     }
     srv->cv_work.notify_all();
     srv->cv_done.notify_all();
@@ -273,10 +373,28 @@ size_t gp_server_footprint(const gp_request* req) {
   return L.total;
 }
 
+gp_status gp_server_destroy(gp_server* srv);
+
+static gp_status server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t max_batch,
+                               gp_server** out);
+
 gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server** out) {
+  return server_create(hbm_budget_bytes, max_slots, 1, out);
+}
+
+gp_status gp_server_create_batched(size_t hbm_budget_bytes, int32_t max_slots, int32_t max_batch,
+                                   gp_server** out) {
+  if (max_batch < 1 || max_batch > 64)
+    return fail(GP_ERR_ARG, "gp_server_create_batched: max_batch must be in [1, 64]");
+  return server_create(hbm_budget_bytes, max_slots, max_batch, out);
+}
+
+static gp_status server_create(size_t hbm_budget_bytes, int32_t max_slots, int32_t max_batch,
+                               gp_server** out) {
   if (out == nullptr || max_slots < 1 || max_slots > 256 || hbm_budget_bytes < (1u << 20))
     return fail(GP_ERR_ARG, "gp_server_create: need out != NULL, 1 <= max_slots <= 256, budget >= 1 MiB");
   auto* srv = new gp_server();
+  srv->max_batch = max_batch;
   if (cudaGetDevice(&srv->device) != cudaSuccess) {
     delete srv;
     return fail(GP_ERR_CUDA, "gp_server_create: no current device");
@@ -300,8 +418,23 @@ gp_status gp_server_create(size_t hbm_budget_bytes, int32_t max_slots, gp_server
   }
   srv->hpool = static_cast<char*>(hp);
   srv->halloc = std::make_unique<PoolAllocator>(srv->hbudget);
-  srv->t0 = std::chrono::steady_clock::now();   // the clock of t_submit_s / t_done_s
   for (int i = 0; i < max_slots; ++i) srv->workers.emplace_back(worker_main, srv);
+  bool all_ready = false;
+  {
+    std::unique_lock<std::mutex> lk(srv->mu);
+    srv->cv_start.wait_for(lk, std::chrono::seconds(60), [&] {
+      return srv->workers_ready + srv->workers_failed == max_slots;
+    });
+    all_ready = srv->workers_ready == max_slots;
+  }
+  if (!all_ready) {
+    // A worker could not create its streams (or did not report in time): stop
+    // the others and release everything, so no request can queue without a
+    // worker to run it.
+    gp_server_destroy(srv);
+    return fail(GP_ERR_CUDA, "gp_server_create: a worker could not create its CUDA streams");
+  }
+  srv->t0 = std::chrono::steady_clock::now();   // the clock of t_submit_s / t_done_s
   *out = srv;
   return GP_OK;
 }
@@ -402,6 +535,9 @@ gp_status gp_server_get_stats(gp_server* srv, gp_server_stats* out) {
   out->peak_active = srv->peak_active;
   out->peak_bytes = srv->peak_bytes;
   out->budget_bytes = srv->budget;
+  out->batches = srv->batches;
+  out->batched_requests = srv->batched_requests;
+  out->largest_batch = srv->largest_batch;
   return GP_OK;
 }
 

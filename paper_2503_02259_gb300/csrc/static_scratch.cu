@@ -127,10 +127,10 @@ extern "C" gp_status gp_kernel_matmul_noalloc(const gp_problem* prob, const floa
   int* err = reinterpret_cast<int*>(b + L.err);
 
   cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  const gp::KernelConsts kc = gp::kernel_consts(prob->kernel, t.l);
+  const gp::KernelConsts kc = gp::kernel_consts(prob);
   cudaError_t e = cudaMemsetAsync(err, 0, sizeof(int), cs);
   if (e == cudaSuccess)
-    e = gp::launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.cs, p.dp, p.nc_pad, xs, cs);
+    e = gp::launch_stage_points(prob->X, n, prob->d, prob->d, prob->X, kc.csd, p.dp, p.nc_pad, xs, cs);
   // The array keeps the previous call's contents: the pad columns must be zero.
   if (e == cudaSuccess && w != p.w_pad)
     e = cudaMemsetAsync(vp, 0, sizeof(float) * p.nc_pad * p.w_pad, cs);

@@ -123,8 +123,12 @@ __device__ const double* final_sums(const double* red, int nq, int w_pad) {
 
 // Writes the staged layout of pt_index in order: element e is coordinate
 // t = (e / 32) % dp of point i = (e / (32 dp)) * 32 + e % 32.
+struct DimScales {
+  float v[GP_MAX_DIM];
+};
+
 __global__ void stage_points_kernel(const float* X, int64_t n, int d, int64_t ld, const float* ref,
-                                    float cs, int dp, int64_t n_pad, float* out) {
+                                    DimScales cs, int dp, int64_t n_pad, float* out) {
   const int64_t total = n_pad * dp;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
@@ -133,7 +137,7 @@ __global__ void stage_points_kernel(const float* X, int64_t n, int d, int64_t ld
     const int t = rem >> 5;
     const int64_t i = tile * 32 + (rem & 31);
     float v = 0.f;
-    if (i < n && t < d) v = (X[i * ld + t] - ref[t]) * cs;
+    if (i < n && t < d) v = (X[i * ld + t] - ref[t]) * cs.v[t];
     out[e] = v;
   }
 }
@@ -943,6 +947,73 @@ __global__ void refine_out_kernel(const double* x64, float* Xsol, int64_t n, int
   }
 }
 
+// ------------------------------------------------------------ prediction --
+// The cross-covariance columns of the posterior variance: B[j][c] =
+// f^2 k(rho(x_j, x*_c)) for j < n, c < w from the unscaled FP32 points
+// (rho^2 = sum_t ((x_jt - x*_ct) / l_t)^2; CUDA's expf and sqrtf), zero
+// elsewhere in the padded [n_pad][w_pad] block.
+__global__ void cross_cols_kernel(const float* X, int64_t n, int d, const float* Xs, int w,
+                                  int kernel, DimScales inv_l, float f2, float* B, int64_t n_pad,
+                                  int w_pad) {
+  const int64_t total = n_pad * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t j = e / w_pad;
+    const int c = static_cast<int>(e - j * w_pad);
+    float v = 0.0f;
+    if (j < n && c < w) {
+      float r2 = 0.0f;
+      for (int t = 0; t < d; ++t) {
+        const float df = (X[j * d + t] - Xs[static_cast<int64_t>(c) * d + t]) * inv_l.v[t];
+        r2 = fmaf(df, df, r2);
+      }
+      if (kernel == GP_KERNEL_GAUSSIAN) {
+        v = f2 * expf(-0.5f * r2);
+      } else {
+        const float a = 1.7320508075688772f * sqrtf(r2);
+        v = f2 * (1.0f + a) * expf(-a);
+      }
+    }
+    B[e] = v;
+  }
+}
+
+// S->dots[0][c] = sum_i A[i][c] B[i][c] (FP64 sums, fixed order) for c < w.
+__global__ void coldots_kernel(CgState* S, const float* A, const float* B, int64_t n_pad, int w_pad,
+                               int w, double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live)
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      acc[0] += static_cast<double>(A[idx]) * static_cast<double>(B[idx]);
+    }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  if (threadIdx.x < w_pad) S->dots[0][threadIdx.x] = threadIdx.x < w ? tot[threadIdx.x] : 0.0;
+}
+
+// var[c] = f2 - sum_j B[j][c] U[j][c] (FP64 sums, fixed order) for c < w.
+__global__ void pred_var_kernel(CgState* S, const float* B, const float* U, int64_t n_pad,
+                                int w_pad, int w, double f2, float* var, double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live)
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      acc[0] += static_cast<double>(B[idx]) * static_cast<double>(U[idx]);
+    }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  if (threadIdx.x < w) var[threadIdx.x] = static_cast<float>(f2 - tot[threadIdx.x]);
+}
+
 }  // namespace
 
 // Blocks of the reducing O(n w) kernels: about 32 rows per block (each thread a
@@ -955,8 +1026,10 @@ int red_blocks(int64_t n_pad) {
 }
 
 cudaError_t launch_stage_points(const float* X, int64_t n, int d, int64_t ld, const float* ref,
-                                float cs, int dp, int64_t n_pad, float* out, cudaStream_t st) {
-  stage_points_kernel<<<elt_blocks(n_pad * dp), kEltThreads, 0, st>>>(X, n, d, ld, ref, cs, dp,
+                                const float* cs, int dp, int64_t n_pad, float* out, cudaStream_t st) {
+  DimScales sc{};
+  for (int t = 0; t < d && t < GP_MAX_DIM; ++t) sc.v[t] = cs[t];
+  stage_points_kernel<<<elt_blocks(n_pad * dp), kEltThreads, 0, st>>>(X, n, d, ld, ref, sc, dp,
                                                                       n_pad, out);
   count_launch();
   return cudaGetLastError();
@@ -1154,6 +1227,31 @@ cudaError_t launch_refine_update(double* x64, const float* X, int64_t n_pad, int
 cudaError_t launch_refine_out(const double* x64, float* Xsol, int64_t n, int w_pad, int w,
                               cudaStream_t st) {
   refine_out_kernel<<<elt_blocks(n * w), kEltThreads, 0, st>>>(x64, Xsol, n, w_pad, w);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cross_cols(const float* X, int64_t n, int d, const float* Xs, int w, int kernel,
+                              const double* inv_l, double f2, float* B, int64_t n_pad, int w_pad,
+                              cudaStream_t st) {
+  DimScales sc{};
+  for (int t = 0; t < d && t < GP_MAX_DIM; ++t) sc.v[t] = static_cast<float>(inv_l[t]);
+  cross_cols_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(
+      X, n, d, Xs, w, kernel, sc, static_cast<float>(f2), B, n_pad, w_pad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coldots(CgState* S, const float* A, const float* B, int64_t n_pad, int w_pad,
+                           int w, double* red, cudaStream_t st) {
+  coldots_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, A, B, n_pad, w_pad, w, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pred_var(CgState* S, const float* B, const float* U, int64_t n_pad, int w_pad,
+                            int w, double f2, float* var, double* red, cudaStream_t st) {
+  pred_var_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, U, n_pad, w_pad, w, f2, var, red);
   count_launch();
   return cudaGetLastError();
 }

@@ -36,6 +36,11 @@ struct CgState {
   double yalpha;
   double out[16];            // assembled results (see assemble kernel)
   unsigned ticket2;
+  // Per-dimension length-scales: (s, f, l_1..l_d) quadratic terms, traces, gradient.
+  double ard_quad[2 + GP_MAX_DIM];
+  double ard_trace[2 + GP_MAX_DIM];
+  double ard_grad[2 + GP_MAX_DIM];
+  int group_counter;         // work counter of a grouped product (batched solves)
   unsigned bar_count;        // grid barrier of the fused CG step: arrivals
   unsigned bar_gen;          // grid barrier of the fused CG step: generation
 };
@@ -48,8 +53,9 @@ int red_blocks(int64_t n_pad);
 size_t red_doubles(int64_t n_pad, int w_pad);
 
 // Launchers (all asynchronous on `st`).
+// Staged points: (X[i][t] - ref[t]) * cs[t] (cs: host array of d per-dimension scales).
 cudaError_t launch_stage_points(const float* X, int64_t n, int d, int64_t ld, const float* ref,
-                                float cs, int dp, int64_t n_pad, float* out, cudaStream_t st);
+                                const float* cs, int dp, int64_t n_pad, float* out, cudaStream_t st);
 cudaError_t launch_pad_block(const float* V, int64_t n, int w, int64_t ldv, float* out,
                              int64_t n_pad, int w_pad, int col_off, cudaStream_t st);
 cudaError_t launch_unpad_block(const float* in, int64_t n, int w, int w_pad, float* out,
@@ -131,8 +137,20 @@ cudaError_t launch_yalpha(CgState* S, const float* B, const float* X, int64_t n_
                           double* red, cudaStream_t st);
 // Final assembly of loss and gradient into S->out (see vec_kernels.cu).
 cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st);
+// S->dots[0][c] = sum_i A[i][c] B[i][c] (FP64, fixed order) for c < w.
+cudaError_t launch_coldots(CgState* S, const float* A, const float* B, int64_t n_pad, int w_pad,
+                           int w, double* red, cudaStream_t st);
 // Replace column 0 of V (padded) by column 0 of X.
 cudaError_t launch_copy_col0(const float* X, float* V, int64_t n_pad, int w_pad, cudaStream_t st);
+
+// Posterior variance: B = f^2 K(X, X*_block) as padded columns (unscaled FP32
+// points, rows < n, columns < w, zero elsewhere), and var[c] = f2 - B_c^T U_c.
+// inv_l: host array of the d per-dimension 1 / l_t.
+cudaError_t launch_cross_cols(const float* X, int64_t n, int d, const float* Xs, int w, int kernel,
+                              const double* inv_l, double f2, float* B, int64_t n_pad, int w_pad,
+                              cudaStream_t st);
+cudaError_t launch_pred_var(CgState* S, const float* B, const float* U, int64_t n_pad, int w_pad,
+                            int w, double f2, float* var, double* red, cudaStream_t st);
 
 // Iterative refinement (the residual r64 = B - Kh x64 is in residual.cuh).
 // S->rr[c] = ||r64_c||^2, S->bn2[c] = ||B_c||^2, S->relres[c] = sqrt(rr/bn2); rf = r64 as FP32.

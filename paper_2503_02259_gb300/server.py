@@ -11,12 +11,19 @@ from ._binding import check, lib
 
 
 class Server:
-    """gp_server on the current CUDA device with a device-memory budget and slots."""
+    """gp_server on the current CUDA device with a device-memory budget and slots;
+    max_batch > 1 lets a worker run up to that many compatible loss + gradient
+    requests as one batched solve (grouped product launches)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_slots: int):
+    def __init__(self, hbm_budget_bytes: int, max_slots: int, max_batch: int = 1):
         h = ctypes.c_void_p()
-        check(lib().gp_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
-              "gp_server_create")
+        if max_batch > 1:
+            check(lib().gp_server_create_batched(int(hbm_budget_bytes), int(max_slots),
+                                                 int(max_batch), ctypes.byref(h)),
+                  "gp_server_create_batched")
+        else:
+            check(lib().gp_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h)),
+                  "gp_server_create")
         self.t0 = time.perf_counter()   # the server clock's origin (its times are relative to it)
         self._h = h
         self._keep = {}   # host arrays of queued requests stay alive until polled

@@ -18,7 +18,8 @@ Contents
       stream (seed 0), the same-probe estimate of L and dL/d(s, f, l) (16
       probes from seed 0, 20 Lanczos steps, exact solves) of the loss+grad
       requests and the posterior mean at the first 200 test points (exact
-      solve) of the predictions; NaN where a field does not apply.
+      solve) of the predictions; NaN where a field does not apply;
+      serving_kappa: the condition number of each request's Kh (eigvalsh).
 """
 import os
 import sys
@@ -73,9 +74,12 @@ def serving_refs():
     loss = np.full(len(idx), np.nan)
     grad = np.full((len(idx), 3), np.nan)
     mu = np.full((len(idx), SERVING_MU_POINTS), np.nan)
+    kappa = np.empty(len(idx))
     for k, i in enumerate(idx):
         rq = reqs[i]
         p = rq.problem
+        ev = np.linalg.eigvalsh(O.khat_dense(p.X, p.kind, p.theta))
+        kappa[k] = ev[-1] / ev[0]
         if rq.kind == 0:
             est = O.est_nll(p.X, p.y, p.kind, p.theta, O.rademacher_probes(p.n, rq.nprobe, 0), 20)
             loss[k] = est["loss"]
@@ -83,17 +87,18 @@ def serving_refs():
         else:
             alpha = O.exact_nll(p.X, p.y, p.kind, p.theta)["alpha"]
             mu[k] = O.predict_mean(p.X, rq.Xstar[:SERVING_MU_POINTS], alpha, p.kind, p.theta)
-    return idx, loss, grad, mu
+    return idx, loss, grad, mu, kappa
 
 
 def main():
     mr, mY, mL = matvec_refs()
     pr, pY = precision_refs()
     dl, dg = diff_refs()
-    si, sl, sg, smu = serving_refs()
+    si, sl, sg, smu, sk = serving_refs()
     np.savez_compressed(OUT, matvec_rows=mr, matvec_Y=mY, matvec_L=mL, precision_rows=pr,
                         precision_Y=pY, diff_loss=np.float64(dl), diff_grad=dg, serving_idx=si,
-                        serving_loss=sl, serving_grad=sg, serving_mu=smu)
+                        serving_loss=sl, serving_grad=sg, serving_mu=smu,
+                        serving_kappa=sk)
     print("wrote", OUT)
 
 

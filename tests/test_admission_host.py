@@ -50,6 +50,26 @@ int level_of(int kind, long long n, int nprobe, int nlanczos, int maxit, long lo
   return gp::sched::priority_level(req(kind, n, nprobe, nlanczos, maxit, m), levels);
 }
 double age_seconds() { return gp::sched::kAgeSeconds; }
+// pick_batch over arrays: compatible flags, work, bytes; out: chosen indices and offsets.
+int batch(size_t count, double first_work, int max_extra, void* p, const int* compat,
+          const double* work, const size_t* bytes, long* chosen, size_t* offs) {
+  std::vector<size_t> o;
+  const std::vector<size_t> c = gp::sched::pick_batch(
+      count, first_work, max_extra, *static_cast<PoolAllocator*>(p),
+      [&](size_t k) { return compat[k] != 0; }, [&](size_t k) { return work[k]; },
+      [&](size_t k) { return bytes[k]; }, &o);
+  for (size_t i = 0; i < c.size(); ++i) { chosen[i] = static_cast<long>(c[i]); offs[i] = o[i]; }
+  return static_cast<int>(c.size());
+}
+// same_batch / batchable on requests given by their fields.
+int same(int ka, int da, int pa, int la, int prec_a, int kb, int db, int pb, int lb, int prec_b) {
+  gp_request a{}, b{};
+  a.kind = 0; a.kernel = ka; a.d = da; a.nprobe = pa; a.nlanczos = la; a.prec = prec_a;
+  a.slq_prec = GP_PREC_FP32;
+  b.kind = 0; b.kernel = kb; b.d = db; b.nprobe = pb; b.nlanczos = lb; b.prec = prec_b;
+  b.slq_prec = GP_PREC_FP32;
+  return gp::sched::same_batch(a, b) ? 1 : 0;
+}
 }
 """
 
@@ -75,6 +95,11 @@ def A(tmp_path_factory):
     lib.pick.restype = ctypes.c_long
     lib.pick.argtypes = [ctypes.c_size_t, ctypes.c_double, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_size_t)]
+    lib.batch.restype = ctypes.c_int
+    lib.batch.argtypes = [ctypes.c_size_t, ctypes.c_double, ctypes.c_int, ctypes.c_void_p,
+                          ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                          ctypes.c_void_p]
+    lib.same.restype = ctypes.c_int
     lib.work_of.restype = ctypes.c_double
     lib.work_of.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                             ctypes.c_longlong]
@@ -194,3 +219,51 @@ def test_request_work_and_priority_level(A):
     assert A.level_of(1, 1000000, 0, 0, 1000, 0, 6) == 5            # 1e15 -> 6 levels
     assert A.level_of(1, 1000000, 0, 0, 1000, 0, 3) == 2            # clamped
     assert A.level_of(1, 1000000, 0, 0, 1000, 0, 1) == 0
+
+
+def _batch(A, first_work, max_extra, pool_bytes, compat, work, nbytes):
+    p = A.pool_new(pool_bytes)
+    c = np.asarray(compat, dtype=np.int32)
+    w = np.asarray(work, dtype=np.float64)
+    b = np.asarray(nbytes, dtype=np.uint64)
+    chosen = np.zeros(len(w), dtype=np.int64)
+    offs = np.zeros(len(w), dtype=np.uint64)
+    k = A.batch(len(w), first_work, max_extra, p, c.ctypes.data, w.ctypes.data, b.ctypes.data,
+                chosen.ctypes.data, offs.ctypes.data)
+    used = A.pool_in_use(p)
+    A.pool_free(p)
+    return list(chosen[:k]), list(offs[:k]), used
+
+
+def test_batch_takes_compatible_similar_work_in_increasing_order(A):
+    work = [5.0, 1.0, 400.0, 3.0, 2.0, 3.0, 0.01]
+    compat = [1, 1, 1, 0, 1, 1, 1]
+    chosen, offs, used = _batch(A, 2.0, 8, 1 << 30, compat, work, [1000] * 7)
+    # 400 (ratio 200) and 0.01 (ratio 200) are too far from 2; index 3 is not
+    # compatible; the rest by increasing work, arrival order among equals.
+    assert chosen == [1, 4, 5, 0]
+    assert used == 4 * 1024 and len(set(offs)) == 4 and all(o % ALIGN == 0 for o in offs)
+
+
+def test_batch_respects_max_extra_and_pool(A):
+    work = [1.0, 1.5, 2.0, 2.5, 3.0]
+    chosen, _, _ = _batch(A, 1.0, 2, 1 << 30, [1] * 5, work, [256] * 5)
+    assert chosen == [0, 1]
+    # Only two blocks fit: the third and later are left in the queue.
+    chosen, _, used = _batch(A, 1.0, 8, 2 * 4096, [1] * 5, work, [4096] * 5)
+    assert chosen == [0, 1] and used == 2 * 4096
+    chosen, _, _ = _batch(A, 1.0, 0, 1 << 30, [1] * 5, work, [256] * 5)
+    assert chosen == []
+
+
+def test_batch_key(A):
+    # kernel, dimension class, nprobe, nlanczos must agree; FP32 products only.
+    assert A.same(0, 3, 16, 20, 0, 0, 3, 16, 20, 0) == 1
+    assert A.same(0, 6, 16, 20, 0, 0, 8, 16, 20, 0) == 1      # both in the class 5..8
+    assert A.same(0, 4, 16, 20, 0, 0, 5, 16, 20, 0) == 0
+    assert A.same(0, 3, 16, 20, 0, 1, 3, 16, 20, 0) == 0
+    assert A.same(0, 3, 16, 20, 0, 0, 3, 8, 20, 0) == 0
+    assert A.same(0, 3, 16, 20, 0, 0, 3, 16, 30, 0) == 0
+    assert A.same(0, 3, 16, 20, 4, 0, 3, 16, 20, 4) == 0      # split BF16 products
+    assert A.same(0, 3, 63, 20, 0, 0, 3, 63, 20, 0) == 1      # 1 + nprobe = 64
+    assert A.same(0, 3, 64, 20, 0, 0, 3, 64, 20, 0) == 0

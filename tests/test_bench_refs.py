@@ -4,6 +4,7 @@ them here and compare."""
 import os
 
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_2503_02259_gb300 import inputs
@@ -59,3 +60,12 @@ def test_serving_references_are_the_oracles():
     mu = O.predict_mean(p.X, rq.Xstar[:200], alpha, p.kind, p.theta)
     np.testing.assert_allclose(mu, refs["serving_mu"][k_pred], rtol=1e-9, atol=1e-12)
     assert np.isnan(refs["serving_loss"][k_pred]) and np.isnan(refs["serving_mu"][k_loss]).all()
+
+
+def test_serving_condition_numbers_are_the_oracles():
+    refs = np.load(REFS)
+    reqs = inputs.serving_stream(seed=0, count=512)
+    k = 3
+    p = reqs[int(refs["serving_idx"][k])].problem
+    ev = np.linalg.eigvalsh(O.khat_dense(p.X, p.kind, p.theta))
+    assert ev[-1] / ev[0] == pytest.approx(float(refs["serving_kappa"][k]), rel=1e-9)

@@ -186,3 +186,34 @@ def test_served_results_match_oracle_when_converged(env, prec, slq):
             alpha = O.exact_nll(p.X, p.y, p.kind, p.theta)["alpha"]
             ref = O.predict_mean(p.X, Xs, alpha, p.kind, p.theta)
             assert np.linalg.norm(r["mu"] - ref) / np.linalg.norm(ref) <= 1e-4
+
+
+def test_batched_server_gives_the_unbatched_results(env):
+    # Loss + gradient requests with 16 probes (1 + p = 17 columns, a grouped
+    # width) run as batches of up to 8 in one grouped launch per solver step;
+    # every result equals the one-request-at-a-time server's bit for bit.
+    torch, api, server = env
+    rng = np.random.default_rng(5)
+    reqs = []
+    for i in range(12):
+        n = int(rng.integers(500, 2500))
+        d = [2, 3][i % 2]
+        prob = inputs.uniform_problem(n, d, O.GAUSSIAN, (0.1, 1.0, 0.25), seed=200 + i)
+        reqs.append((0, prob, None))
+
+    def run(max_batch, slots):
+        with server.Server(8 << 30, slots, max_batch=max_batch) as srv:
+            tickets = []
+            for kind, p, Xs in reqs:
+                r, keep = server.Server.request(kind, p.X, p.y, p.kind, p.theta, nprobe=16,
+                                                cg_maxit=300, nlanczos=15, cg_rtol=1e-7, seed=4)
+                tickets.append(srv.submit(r, keep))
+            srv.drain(300)
+            return [srv.poll(t) for t in tickets], srv.stats()
+
+    plain, _ = run(1, 1)
+    batched, stats = run(8, 1)
+    assert stats["batches"] >= 1 and stats["largest_batch"] >= 2
+    for a, b in zip(plain, batched):
+        assert a["status"] == b["status"] == 0
+        assert a["loss"] == b["loss"] and a["grad"] == b["grad"]
