@@ -1,5 +1,6 @@
 // Instantiations of the tensor-core product for one operand mode, compiled once
 // per mode with -DGP_TC_MODE=<1|2|3|4> (TF32, BF16, split TF32, split BF16).
+#include <algorithm>
 #include <atomic>
 
 #include <cuda_bf16.h>
@@ -69,19 +70,36 @@ template <int KIND, bool GRAD, int DT>
 cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
   const int n = p.w_pad;
   if (n > 128 || n < 16 || (n & 15)) return cudaErrorNotSupported;
-  // The deepest copy ring (<= kTcBStages stages) that fits in shared memory.
-  int nbs = kTcBStages;
-  while (nbs > 2 && tc_smem<MODE, DT>(n, GRAD, nbs).total > 227u * 1024u) --nbs;
-  const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs);
-  if (L.total > 227u * 1024u) return cudaErrorNotSupported;
   cudaError_t e = ensure_attr<KIND, GRAD, DT>();
   if (e != cudaSuccess) return e;
   const uint32_t cols = tc_tmem_cols(n, GRAD);
   if (cols > 512) return cudaErrorNotSupported;
-  // Resident CTAs must fit the 512 tensor-memory columns of an SM; reserve extra
-  // shared memory when the occupancy would otherwise exceed that.
-  size_t smem = L.total;
+  // Resident CTAs must fit the 512 tensor-memory columns of an SM.
   const int max_ctas = static_cast<int>(512 / cols);
+  // Copy-ring depth: the one (2..kTcBStages stages) that lets the most CTAs
+  // reside on an SM, the deepest among those.  A tile's copies (points and one
+  // B slice, a few KB from L2) land within a fraction of the time the eval
+  // warps spend on one tile, so two stages suffice to hide them, while one
+  // more resident CTA adds eval warps to hide the evaluation's latencies.
+  int nbs = 0, best_occ = 0;
+  for (int b = kTcBStages; b >= 2; --b) {
+    const TcSmem Lb = tc_smem<MODE, DT>(n, GRAD, b);
+    if (Lb.total > 227u * 1024u) continue;
+    int occ_b = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kernel_ptr<KIND, GRAD, DT>(),
+                                                      kTcThreads, Lb.total);
+    if (e != cudaSuccess) return e;
+    occ_b = std::min(occ_b, max_ctas);
+    if (occ_b > best_occ) {
+      best_occ = occ_b;
+      nbs = b;
+    }
+  }
+  if (nbs == 0) return cudaErrorNotSupported;
+  const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs);
+  // Reserve extra shared memory when the occupancy would otherwise exceed the
+  // tensor-memory bound.
+  size_t smem = L.total;
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_ptr<KIND, GRAD, DT>(), kTcThreads,
                                                     smem);
