@@ -257,9 +257,9 @@ def gp_loss_and_grad_batch(Xs, ys, kernels, thetas, opts_list, raise_not_converg
             [i.as_dict() for i in info], list(status))
 
 
-def gp_nll_forward(X, y, kernel, theta, opts: B.gp_solve_opts):
+def gp_nll_forward(X, y, kernel, theta, opts: B.gp_solve_opts, ls=None):
     """(loss, W = Kh^-1 [y | Z] (n, 1 + p), info)."""
-    prob, X = problem(X, kernel, theta)
+    prob, X = problem(X, kernel, theta, ls)
     y = _f32(y, "y").reshape(-1)
     W = torch.empty((X.shape[0], 1 + opts.nprobe), dtype=torch.float32, device=X.device)
     loss = c_double()
@@ -270,11 +270,12 @@ def gp_nll_forward(X, y, kernel, theta, opts: B.gp_solve_opts):
     return loss.value, W, info.as_dict()
 
 
-def gp_nll_backward(X, W, kernel, theta, opts: B.gp_solve_opts):
-    """[dL/ds, dL/df, dL/dl] from the forward's W (probes regenerated, not stored)."""
-    prob, X = problem(X, kernel, theta)
+def gp_nll_backward(X, W, kernel, theta, opts: B.gp_solve_opts, ls=None):
+    """[dL/ds, dL/df, dL/dl] from the forward's W (probes regenerated, not stored);
+    [dL/ds, dL/df, dL/dl_1, ..., dL/dl_d] with per-dimension length-scales ls."""
+    prob, X = problem(X, kernel, theta, ls)
     W = _f32(W, "W")
-    grad = (c_double * 3)()
+    grad = (c_double * (3 if ls is None else 2 + X.shape[1]))()
     info = B.gp_loss_info()
     ws = workspace(B.OP_LOSS_GRAD, prob, 0, opts, X.device)
     check(lib().gp_nll_backward(byref(prob), byref(opts), _ptr(W), grad, byref(info), _ptr(ws),

@@ -8,7 +8,10 @@ same probes Z from the seed instead of storing them and runs one fused
 derivative product (gp_nll_backward).  With ``recompute=True`` the forward
 keeps nothing n-sized and the backward re-solves for W first.  ``prec`` and
 ``slq_prec`` choose the arithmetic of the CG and of the Lanczos products (the
-derivative product of the backward is FP32).
+derivative product of the backward is FP32).  ``theta`` holds (s, f, l), or
+(s, f, l_1, ..., l_d) for per-dimension length-scales, whose backward is the
+fused contraction of the entries and their d derivatives (no derivative
+product).
 """
 from __future__ import annotations
 
@@ -22,11 +25,19 @@ class GPNegLogLik(torch.autograd.Function):
     @staticmethod
     def forward(ctx, theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute,
                 prec, slq_prec):
-        th = [float(v) for v in theta.detach().cpu().tolist()]
+        vals = [float(v) for v in theta.detach().cpu().tolist()]
+        d = X.shape[1]
+        if len(vals) == 3:
+            th, ls = vals, None
+        elif len(vals) == 2 + d:
+            th, ls = [vals[0], vals[1], 1.0], vals[2:]
+        else:
+            raise ValueError("theta must hold (s, f, l) or (s, f, l_1..l_d)")
         opts = api.solve_opts(nprobe=nprobe, nlanczos=nlanczos, cg_rtol=cg_rtol, seed=seed,
                               cg_maxit=cg_maxit, prec=prec, slq_prec=slq_prec)
-        loss, W, info = api.gp_nll_forward(X, y, kernel, th, opts)
-        ctx.cfg = (kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec, slq_prec)
+        loss, W, info = api.gp_nll_forward(X, y, kernel, th, opts, ls=ls)
+        ctx.cfg = (kernel, th, ls, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec,
+                   slq_prec)
         ctx.info = info
         ctx.theta_dtype = theta.dtype
         ctx.theta_device = theta.device
@@ -36,12 +47,13 @@ class GPNegLogLik(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         X, y, W = ctx.saved_tensors
-        kernel, th, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec, slq_prec = ctx.cfg
+        (kernel, th, ls, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute, prec,
+         slq_prec) = ctx.cfg
         opts = api.solve_opts(nprobe=nprobe, nlanczos=nlanczos, cg_rtol=cg_rtol, seed=seed,
                               cg_maxit=cg_maxit, prec=prec, slq_prec=slq_prec)
         if W is None:
-            _, W, _ = api.gp_nll_forward(X, y, kernel, th, opts)
-        grad, _ = api.gp_nll_backward(X, W, kernel, th, opts)
+            _, W, _ = api.gp_nll_forward(X, y, kernel, th, opts, ls=ls)
+        grad, _ = api.gp_nll_backward(X, W, kernel, th, opts, ls=ls)
         g = torch.tensor(grad, dtype=ctx.theta_dtype, device=ctx.theta_device) * grad_out.to(
             device=ctx.theta_device, dtype=ctx.theta_dtype)
         return (g, None, None, None, None, None, None, None, None, None, None, None)
@@ -51,6 +63,7 @@ def neg_log_likelihood(theta: torch.Tensor, X: torch.Tensor, y: torch.Tensor, ke
                        nprobe: int = 16, nlanczos: int = 30, cg_rtol: float = 1e-6, seed: int = 0,
                        cg_maxit: int = 0, recompute: bool = False, prec: int = PREC_FP32,
                        slq_prec: int = PREC_FP32) -> torch.Tensor:
-    """L(theta) with theta = (s, f, l) a 3-element tensor; differentiable in theta."""
+    """L(theta) with theta = (s, f, l), or (s, f, l_1..l_d) for per-dimension
+    length-scales; differentiable in theta."""
     return GPNegLogLik.apply(theta, X, y, kernel, nprobe, nlanczos, cg_rtol, seed, cg_maxit, recompute,
                              prec, slq_prec)

@@ -135,3 +135,23 @@ def test_ard_unsupported_paths_say_so(env):
     with pytest.raises(B.GPError) as ei:
         api.gp_kernel_matmul(X, V, prob.kind, prob.theta, ls=[0.3, -1.0, 0.5])
     assert ei.value.status == B.GP_ERR_ARG
+
+
+def test_ard_autograd_backward_matches_oracle(env):
+    # The differentiable loss with theta = (s, f, l_1..l_d): one backward gives
+    # all 2 + d components, equal to the oracle's same-probe estimator.
+    torch, B, api = env
+    from paper_2503_02259_gb300.autograd import neg_log_likelihood
+    n, d, kind, s, f, ls = 1000, 3, O.GAUSSIAN, 0.1, 1.2, [0.25, 0.4, 0.6]
+    X = inputs.points(n, d, seed=61)
+    y = (np.cos(3 * X[:, 1]) + X[:, 0]).astype(np.float32)
+    theta = torch.tensor([s, f] + ls, dtype=torch.float64, requires_grad=True)
+    for recompute in (False, True):
+        L = neg_log_likelihood(theta, _dev(X), _dev(y), kind, nprobe=8, nlanczos=25, cg_rtol=1e-8,
+                               seed=13, recompute=recompute)
+        (g,) = torch.autograd.grad(L, theta)
+        est = O.est_nll_ard(X, y, kind, s, f, ls, O.rademacher_probes(n, 8, 13), 25)
+        assert abs(L.item() - est["loss"]) <= 1e-4 * abs(est["loss"])
+        gr = np.asarray(est["grad"])
+        floor = 1e-3 * np.linalg.norm(gr)
+        assert np.all(np.abs(g.numpy() - gr) <= 1e-4 * np.maximum(np.abs(gr), floor)), (g, gr)

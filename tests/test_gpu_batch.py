@@ -98,3 +98,27 @@ def test_batch_rejects_mixed_templates(env):
         api.gp_loss_and_grad_batch([_dev(a.X), _dev(b.X)], [_dev(a.y), _dev(b.y)],
                                    [a.kind, b.kind], [a.theta, b.theta], [o, o])
     assert ei.value.status == B.GP_ERR_ARG
+
+
+@pytest.mark.parametrize("count", [1, 64])
+def test_batch_sizes_one_and_the_maximum(env, count):
+    torch, B, api = env
+    rng = np.random.default_rng(count)
+    probs = [inputs.uniform_problem(int(rng.integers(129, 400)), 2, O.MATERN32,
+                                    (0.2, 1.0, float(rng.uniform(0.2, 0.5))), seed=500 + k)
+             for k in range(count)]
+    opts = [api.solve_opts(nprobe=4, nlanczos=10, cg_rtol=1e-6, seed=k) for k in range(count)]
+    Xs = [_dev(p.X) for p in probs]
+    ys = [_dev(p.y) for p in probs]
+    losses, grads, _, status = api.gp_loss_and_grad_batch(
+        Xs, ys, [p.kind for p in probs], [p.theta for p in probs], opts)
+    assert status == [0] * count
+    for k in (0, count // 2, count - 1):
+        l1, g1, _ = api.gp_loss_and_grad(Xs[k], ys[k], probs[k].kind, probs[k].theta, opts[k])
+        assert losses[k] == pytest.approx(l1, rel=1e-9)
+        np.testing.assert_allclose(grads[k], g1, rtol=1e-9, atol=1e-9 * np.abs(g1).max())
+    if count == 64:
+        with pytest.raises(B.GPError) as ei:
+            api.gp_loss_and_grad_batch(Xs + Xs[:1], ys + ys[:1], [probs[0].kind] * 65,
+                                       [p.theta for p in probs] + [probs[0].theta], opts + opts[:1])
+        assert ei.value.status == B.GP_ERR_ARG
