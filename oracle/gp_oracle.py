@@ -487,3 +487,90 @@ def lanczos_from_cg(alphas: np.ndarray, betas: np.ndarray, k: int):
         if j < m - 1:
             b[j] = math.sqrt(betas[j]) / alphas[j]
     return a, b
+
+
+# ---------------------------------------------------------------------------
+# Preconditioned CG (§Gaussian Processes: PCG with M ~ Kh).  M is the Nystrom
+# approximation of f^2 K on landmark points chosen by greedy pivoting -- the
+# rank-k partial pivoted Cholesky factor L of f^2 K (so f^2 K ~ L L^T, the
+# Nystrom form K_{:,P} K_{P,P}^-1 K_{P,:} on the pivots P) -- plus the noise:
+#     M = L L^T + s I,
+# applied through the Woodbury identity
+#     M^-1 v = (v - L (s I_k + L^T L)^-1 L^T v) / s.
+# This is the low-rank (Nystrom) part of the AFN preconditioner the paper
+# uses (Zhao et al. 2024), without AFN's sparse factor for the Schur
+# complement and with the rank k given, not chosen adaptively.
+# ---------------------------------------------------------------------------
+
+def pivoted_cholesky(A: np.ndarray, k: int, tol: float = 0.0, pivot_dtype=np.float64):
+    """Rank-k partial Cholesky of the SPD matrix A with greedy diagonal pivoting.
+
+    Step j takes the pivot p_j = argmax_i d_i of the residual diagonal
+    d = diag(A - L L^T) (the smallest index among equal values; the argmax is
+    taken over d rounded to pivot_dtype), stops early if d_{p_j} <= tol, and
+    sets L[:, j] = (A[:, p_j] - L[:, :j] L[p_j, :j]^T) / sqrt(d_{p_j}).
+    Returns (L (n x m), pivots (m,), residual diagonal d), m <= k.
+    """
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    L = np.zeros((n, k))
+    d = np.diag(A).copy()
+    piv = []
+    for j in range(k):
+        p = int(np.argmax(d.astype(pivot_dtype)))
+        if not d[p] > tol:
+            break
+        col = (A[:, p] - L[:, :j] @ L[p, :j]) / math.sqrt(d[p])
+        L[:, j] = col
+        d -= col * col
+        d[p] = 0.0
+        piv.append(p)
+    m = len(piv)
+    return L[:, :m], np.array(piv, dtype=np.int64), d
+
+
+def nystrom_apply_inverse(L: np.ndarray, s: float, V: np.ndarray) -> np.ndarray:
+    """(L L^T + s I)^-1 V by the Woodbury identity, with a Cholesky solve of the
+    k x k matrix s I + L^T L."""
+    V = np.asarray(V, dtype=np.float64)
+    C = s * np.eye(L.shape[1]) + L.T @ L
+    T = sla.cho_solve(sla.cho_factor(C), L.T @ V)
+    return (V - L @ T) / s
+
+
+def pcg(A: np.ndarray, B: np.ndarray, apply_minv, rtol: float, maxit: int):
+    """Column-wise preconditioned CG on A X = B from X = 0 (Saad 2003, Alg. 9.1):
+    z = M^-1 r, p = z; alpha = r^T z / p^T A p; x += alpha p; r -= alpha A p;
+    z' = M^-1 r'; beta = r'^T z' / r^T z; p = z' + beta p.  Stops each column
+    at ||r||_2 / ||b||_2 <= rtol (recurrence residual) or at maxit iterations.
+    Returns (X, iterations per column, relres per column)."""
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    n, w = B.shape
+    Xs = np.zeros((n, w))
+    iters = np.zeros(w, dtype=int)
+    relres = np.zeros(w)
+    for c in range(w):
+        b = B[:, c]
+        bn = np.linalg.norm(b)
+        x = np.zeros(n)
+        r = b.copy()
+        z = apply_minv(r[:, None])[:, 0]
+        p = z.copy()
+        rz = r @ z
+        it = 0
+        while it < maxit and np.linalg.norm(r) > rtol * bn:
+            q = A @ p
+            alpha = rz / (p @ q)
+            x += alpha * p
+            r -= alpha * q
+            z = apply_minv(r[:, None])[:, 0]
+            rz_new = r @ z
+            p = z + (rz_new / rz) * p
+            rz = rz_new
+            it += 1
+        Xs[:, c] = x
+        iters[c] = it
+        relres[c] = np.linalg.norm(r) / bn if bn > 0 else 0.0
+    return Xs, iters, relres

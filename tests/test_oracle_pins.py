@@ -492,6 +492,87 @@ def test_cg_maxit_reports_residual():
     assert iters[0] == 3 and relres[0] > 1e-14
 
 
+# -------------------------------------------------- pivoted Cholesky, PCG --
+
+def test_pivoted_cholesky_full_rank_is_a_permuted_cholesky():
+    prob = inputs.small_problem(seed=21, n=120)
+    A = prob.theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, prob.theta[2])
+    A += 1e-6 * np.eye(120)
+    L, piv, d = O.pivoted_cholesky(A, 120)
+    assert sorted(piv.tolist()) == list(range(120))
+    np.testing.assert_allclose(L @ L.T, A, rtol=0, atol=1e-11 * np.abs(A).max())
+    # The factor restricted to the pivot rows is the (lower) Cholesky factor of
+    # the permuted matrix, computed independently by LAPACK.
+    P = A[np.ix_(piv, piv)]
+    np.testing.assert_allclose(L[piv, :], sla.cholesky(P, lower=True), rtol=0, atol=1e-9)
+    assert np.all(np.abs(d) <= 1e-10)
+
+
+def test_pivoted_cholesky_greedy_rule_and_trace():
+    rng = np.random.default_rng(22)
+    G = rng.standard_normal((40, 40))
+    A = G @ G.T + 40 * np.eye(40)
+    L, piv, d = O.pivoted_cholesky(A, 10)
+    # The first pivot is the largest diagonal entry; the residual diagonal is
+    # diag(A - L L^T), and the residual trace never grows.
+    assert piv[0] == int(np.argmax(np.diag(A)))
+    np.testing.assert_allclose(d, np.diag(A - L @ L.T), atol=1e-9)
+    traces = [np.trace(A - L[:, :j] @ L[:, :j].T) for j in range(11)]
+    assert all(b <= a + 1e-9 for a, b in zip(traces, traces[1:]))
+    # Each pivot is the argmax of the residual diagonal before its step.
+    for j in range(10):
+        dj = np.diag(A - L[:, :j] @ L[:, :j].T)
+        assert piv[j] == int(np.argmax(dj))
+
+
+def test_pivoted_cholesky_stops_at_the_exact_rank():
+    # Points in 3 identical clusters: f^2 K has rank 3 (Gaussian, distinct
+    # cluster centres), so the greedy factor stops after 3 steps.
+    X = np.repeat(np.array([[0.1, 0.2], [0.7, 0.4], [0.3, 0.9]]), 20, axis=0)
+    A = O.kernel_value(O.sqdist(X, X), O.GAUSSIAN, 0.3)
+    L, piv, d = O.pivoted_cholesky(A, 10, tol=1e-10)
+    assert L.shape[1] == 3
+    np.testing.assert_allclose(L @ L.T, A, atol=1e-10)
+
+
+def test_nystrom_woodbury_inverse_matches_dense_solve():
+    rng = np.random.default_rng(23)
+    L = rng.standard_normal((60, 7))
+    V = rng.standard_normal((60, 3))
+    s = 0.3
+    got = O.nystrom_apply_inverse(L, s, V)
+    ref = np.linalg.solve(L @ L.T + s * np.eye(60), V)
+    np.testing.assert_allclose(got, ref, rtol=1e-10, atol=1e-12)
+
+
+def test_pcg_with_the_matrix_itself_converges_in_one_step():
+    prob = inputs.small_problem(seed=24, n=200)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    b = prob.y.astype(np.float64)
+    X, it, rel = O.pcg(Kh, b, lambda V: np.linalg.solve(Kh, V), 1e-10, 50)
+    assert it[0] == 1 and rel[0] <= 1e-10
+    np.testing.assert_allclose(X[:, 0], sla.cho_solve(sla.cho_factor(Kh), b), rtol=1e-8)
+
+
+def test_pcg_with_identity_is_cg_and_nystrom_needs_fewer_iterations():
+    prob = inputs.precision_problem(seed=25, n=1500)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    b = prob.y.astype(np.float64)
+    s, f, l = prob.theta
+    X0, it0, _, _, _ = O.cg(Kh, b, 1e-8, 5000)
+    X1, it1, _ = O.pcg(Kh, b, lambda V: V, 1e-8, 5000)
+    assert it1[0] == it0[0]
+    np.testing.assert_allclose(X1, X0, rtol=1e-10, atol=1e-10 * np.abs(X0).max())
+    A = f * f * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, l)
+    # About 500 eigenvalues of f^2 K exceed s here; a rank-600 Nystrom factor
+    # takes most of the spectrum above s out of the iteration.
+    L, _, _ = O.pivoted_cholesky(A, 600)
+    X2, it2, rel2 = O.pcg(Kh, b, lambda V: O.nystrom_apply_inverse(L, s, V), 1e-8, 5000)
+    assert rel2[0] <= 1e-8 and it2[0] < it0[0] / 5
+    ref = sla.cho_solve(sla.cho_factor(Kh), b)
+    assert np.linalg.norm(X2[:, 0] - ref) <= 1e-5 * np.linalg.norm(ref)
+
+
 # ---------------------------------------------- pins catch planted mistakes --
 
 def test_planted_sign_error_in_dl_is_caught(monkeypatch):
@@ -577,3 +658,12 @@ def test_planted_wrong_ard_derivative_power_is_caught(monkeypatch):
     monkeypatch.setattr(O.gp_oracle, "kernel_dls", wrong)
     with pytest.raises(AssertionError):
         test_ard_gradient_central_difference(O.GAUSSIAN)
+
+
+def test_planted_wrong_woodbury_sign_is_caught(monkeypatch):
+    good = O.gp_oracle.nystrom_apply_inverse
+    def wrong(L, s, V):
+        return 2.0 * V / s - good(L, s, V)
+    monkeypatch.setattr(O, "nystrom_apply_inverse", wrong)
+    with pytest.raises(AssertionError):
+        test_nystrom_woodbury_inverse_matches_dense_solve()
