@@ -57,6 +57,7 @@ extern "C" {
 #define GP_MAX_DIM 16     /* largest supported point dimension d */
 #define GP_MAX_COLS 128   /* largest multivector width w per product */
 #define GP_MAX_LANCZOS 64 /* largest number of Lanczos steps k for SLQ */
+#define GP_MAX_PRECOND_RANK 4096 /* largest rank of the Nystrom preconditioner */
 
 typedef enum {
   GP_OK = 0,
@@ -99,7 +100,8 @@ typedef enum {
   GP_OP_PREDICT = 5,      /* gp_predict_mean */
   GP_OP_RESIDUAL = 6,     /* gp_true_residual, gp_residual_rows */
   GP_OP_PREDICT_VAR = 7,  /* gp_predict_var */
-  GP_OP_LOSS_GRAD_BATCH = 8  /* one member of gp_loss_and_grad_batch */
+  GP_OP_LOSS_GRAD_BATCH = 8, /* one member of gp_loss_and_grad_batch */
+  GP_OP_NYSTROM = 9          /* gp_nystrom_apply */
 } gp_op;
 
 /* Theta = (s, f, l): noise s, scale f, length-scale l (§Gaussian Processes). */
@@ -149,7 +151,15 @@ typedef struct {
  *              the CG solves tolerate BF16X3, so the two may differ.
  *  refine_residual: arithmetic of the refinement's outer residual
  *              (gp_residual_arith; zero-initialised options select the
- *              compensated FP32-pair form). */
+ *              compensated FP32-pair form).
+ *  precond_rank: 0 = no preconditioner (M = I); k in [1, GP_MAX_PRECOND_RANK]
+ *              = the Nystrom preconditioner M = s I + L L^T with L the
+ *              rank-k pivoted partial Cholesky factor of f^2 K (see
+ *              gp_nystrom_apply), used by gp_pcg_solve and
+ *              gp_pcg_solve_refined (in the refinement's inner solves); the
+ *              other calls reject it (GP_ERR_UNIMPLEMENTED).
+ *  precond_tol: the factor stops before k columns once the largest residual
+ *              diagonal is <= precond_tol * f^2 (<= 0: only when it is <= 0). */
 typedef struct {
   int32_t nprobe;
   int32_t nlanczos;
@@ -162,6 +172,8 @@ typedef struct {
   int32_t refine_maxit;
   int32_t slq_prec;
   int32_t refine_residual;
+  int32_t precond_rank;
+  double precond_tol;
 } gp_solve_opts;
 
 /* slq_prec value meaning "the same arithmetic as prec". */
@@ -249,8 +261,8 @@ gp_status gp_kernel_grad_matmul(const gp_problem* prob, const float* V, int32_t 
                                 float* dY_f, float* dY_l, int32_t prec, void* ws,
                                 size_t ws_bytes, void* stream);
 
-/* Column-wise CG for Kh Xsol = B from Xsol = 0 (PCG of §Gaussian Processes with
- * M = I).  B, Xsol: device n x w.  iters[w], relres[w]: host outputs (iterations
+/* Column-wise CG for Kh Xsol = B from Xsol = 0 (PCG of §Gaussian Processes; M = I,
+ * or the Nystrom preconditioner when opts->precond_rank > 0).  B, Xsol: device n x w.  iters[w], relres[w]: host outputs (iterations
  * and final recurrence relres per column).  Stops each column at opts->cg_rtol
  * or opts->cg_maxit.  With opts->prec != FP32 and refine_rtol > 0 the inner
  * products run on tensor cores and an outer FP32-compensated residual loop
@@ -287,7 +299,8 @@ gp_status gp_residual_rows(const gp_problem* prob, const float* B, const double*
                            double* relres, void* ws, size_t ws_bytes, void* stream);
 
 /* Mixed-precision iterative refinement of Kh Xsol = B with an FP64 solution
- * (PCG of §Gaussian Processes with M = I, refined).  Outer loop: R = B - Kh X
+ * (PCG of §Gaussian Processes, refined; M = I, or the Nystrom preconditioner
+ * in the inner solves when opts->precond_rank > 0, built once per call).  Outer loop: R = B - Kh X
  * with X held in FP64 and the sums in the arithmetic opts->refine_residual
  * (default: compensated FP32 pairs; the kernel entries never leave the FP32
  * pipe); inner loop: block CG on the product of precision opts->prec (a
@@ -302,6 +315,31 @@ gp_status gp_residual_rows(const gp_problem* prob, const float* B, const double*
 gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w, double* X64,
                                const gp_solve_opts* opts, int32_t* iters, double* relres, void* ws,
                                size_t ws_bytes, void* stream);
+
+/* Nystrom preconditioner of Kh (the preconditioner M of the PCG in §Gaussian
+ * Processes; the paper's own M, AFN, also builds a Nystrom factor on chosen
+ * landmark points).  Builds L, the partial Cholesky factor of f^2 K with
+ * greedy diagonal pivoting: step j takes the pivot p_j = argmax_i d_i of the
+ * residual diagonal d = diag(f^2 K - L L^T) (the smallest index among equal
+ * values; the first pivot is 0) and sets
+ *   L[:, j] = (f^2 K[:, p_j] - L[:, :j] L[p_j, :j]^T) / sqrt(d_{p_j}),
+ * stopping after k columns or once the largest d_i is <= tol * f^2; then
+ * applies M^-1 = (s I + L L^T)^-1 to V by the Woodbury identity,
+ *   Z = (V - L C^-1 L^T V) / s,  C = s I + L^T L  (C^-1 formed in FP64).
+ * L is stored in FP32; its column dot products, L^T L, L^T V and L (C^-1 L^T V)
+ * are summed with exact products and FP32-pair sums, so Z is M^-1 V for the
+ * stored L up to the final rounding to FP32.  With per-dimension length-scales
+ * the points are divided by l_t in FP32 first.
+ * k: 1 <= k <= GP_MAX_PRECOND_RANK (k > n is taken as n).  V, Z: device n x w
+ * float32 (w >= 1; may not alias).  L (may be NULL): device float32, column j
+ * at L + j * n (n rows; columns >= *rank untouched).  piv (may be NULL): host
+ * int64 [k], pivots of the built columns.  rank: host, columns built.
+ * Workspace: gp_workspace_bytes(GP_OP_NYSTROM, prob, w, opts) with
+ * opts->precond_rank = k.  GP_ERR_NUMERIC if C's FP64 Cholesky factorisation
+ * meets a non-positive pivot.  Synchronises. */
+gp_status gp_nystrom_apply(const gp_problem* prob, int32_t k, double tol, const float* V, int32_t w,
+                           float* Z, float* L, int64_t* piv, int32_t* rank, void* ws,
+                           size_t ws_bytes, void* stream);
 
 /* SLQ estimate of log|Kh| (Eq. 1 with M = I; stochastic Lanczos quadrature):
  * k steps of Lanczos with full reorthogonalisation from q_1 = z_i / ||z_i||

@@ -502,7 +502,8 @@ def lanczos_from_cg(alphas: np.ndarray, betas: np.ndarray, k: int):
 # complement and with the rank k given, not chosen adaptively.
 # ---------------------------------------------------------------------------
 
-def pivoted_cholesky(A: np.ndarray, k: int, tol: float = 0.0, pivot_dtype=np.float64):
+def pivoted_cholesky(A: np.ndarray, k: int, tol: float = 0.0, pivot_dtype=np.float64,
+                     pivots=None):
     """Rank-k partial Cholesky of the SPD matrix A with greedy diagonal pivoting.
 
     Step j takes the pivot p_j = argmax_i d_i of the residual diagonal
@@ -510,6 +511,8 @@ def pivoted_cholesky(A: np.ndarray, k: int, tol: float = 0.0, pivot_dtype=np.flo
     taken over d rounded to pivot_dtype), stops early if d_{p_j} <= tol, and
     sets L[:, j] = (A[:, p_j] - L[:, :j] L[p_j, :j]^T) / sqrt(d_{p_j}).
     Returns (L (n x m), pivots (m,), residual diagonal d), m <= k.
+    `pivots` (optional) replaces the greedy choice by a given sequence (the
+    factor of another implementation is then checked on its own pivots).
     """
     A = np.asarray(A, dtype=np.float64)
     n = A.shape[0]
@@ -517,7 +520,12 @@ def pivoted_cholesky(A: np.ndarray, k: int, tol: float = 0.0, pivot_dtype=np.flo
     d = np.diag(A).copy()
     piv = []
     for j in range(k):
-        p = int(np.argmax(d.astype(pivot_dtype)))
+        if pivots is not None:
+            if j >= len(pivots):
+                break
+            p = int(pivots[j])
+        else:
+            p = int(np.argmax(d.astype(pivot_dtype)))
         if not d[p] > tol:
             break
         col = (A[:, p] - L[:, :j] @ L[p, :j]) / math.sqrt(d[p])

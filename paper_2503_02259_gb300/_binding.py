@@ -43,6 +43,8 @@ OP_PREDICT = 5
 OP_RESIDUAL = 6
 OP_PREDICT_VAR = 7
 OP_LOSS_GRAD_BATCH = 8
+OP_NYSTROM = 9
+MAX_PRECOND_RANK = 4096
 
 RESIDUAL_PAIR = 0   # compensated FP32-pair sums (the refinement default)
 RESIDUAL_FP64 = 1   # FP64 entries and sums (the checker)
@@ -65,7 +67,8 @@ class gp_solve_opts(ctypes.Structure):
     _fields_ = [("nprobe", c_int32), ("nlanczos", c_int32), ("cg_maxit", c_int32),
                 ("prec", c_int32), ("cg_rtol", c_double), ("refine_rtol", c_double),
                 ("seed", c_uint64), ("probes", c_void_p), ("refine_maxit", c_int32),
-                ("slq_prec", c_int32), ("refine_residual", c_int32)]
+                ("slq_prec", c_int32), ("refine_residual", c_int32),
+                ("precond_rank", c_int32), ("precond_tol", c_double)]
 
 
 class gp_loss_info(ctypes.Structure):
@@ -119,6 +122,9 @@ PROTOTYPES = {
     "gp_pcg_solve_refined": (c_int32, [POINTER(gp_problem), c_void_p, c_int32, c_void_p,
                                        POINTER(gp_solve_opts), POINTER(c_int32), POINTER(c_double),
                                        c_void_p, c_size_t, c_void_p]),
+    "gp_nystrom_apply": (c_int32, [POINTER(gp_problem), c_int32, c_double, c_void_p, c_int32,
+                                   c_void_p, c_void_p, POINTER(c_int64), POINTER(c_int32),
+                                   c_void_p, c_size_t, c_void_p]),
     "gp_true_residual": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int32,
                                    POINTER(c_double), c_void_p, c_size_t, c_void_p]),
     "gp_residual_rows": (c_int32, [POINTER(gp_problem), c_void_p, c_void_p, c_int32, c_void_p,

@@ -52,14 +52,18 @@ def solve_opts(nprobe: int = 0, nlanczos: int = 30, cg_maxit: int = 0, cg_rtol: 
                seed: int = 0, prec: int = B.PREC_FP32, refine_rtol: float = 0.0,
                probes: torch.Tensor | None = None, refine_maxit: int = 0,
                slq_prec: int = B.PREC_FP32,
-               refine_residual: int = B.RESIDUAL_PAIR) -> B.gp_solve_opts:
+               refine_residual: int = B.RESIDUAL_PAIR, precond_rank: int = 0,
+               precond_tol: float = 0.0) -> B.gp_solve_opts:
     """gp_solve_opts; slq_prec is the arithmetic of the SLQ Lanczos products
     (B.PREC_SAME: the same as prec); refine_residual the arithmetic of the
-    refinement's outer residual (B.RESIDUAL_PAIR or B.RESIDUAL_FP64)."""
+    refinement's outer residual (B.RESIDUAL_PAIR or B.RESIDUAL_FP64);
+    precond_rank > 0 selects the Nystrom preconditioner of that rank for the
+    solves (precond_tol: its early stop, relative to f^2)."""
     return B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
                            float(refine_rtol), int(seed) & (2**64 - 1),
                            0 if probes is None else probes.data_ptr(), int(refine_maxit),
-                           int(slq_prec), int(refine_residual))
+                           int(slq_prec), int(refine_residual), int(precond_rank),
+                           float(precond_tol))
 
 
 def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None, device) -> torch.Tensor:
@@ -125,6 +129,32 @@ def gp_pcg_solve(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converge
     if st != B.GP_OK and not (st == B.GP_ERR_NOT_CONVERGED and not raise_not_converged):
         check(st, "gp_pcg_solve")
     return Xsol, list(iters), list(relres), st
+
+
+def gp_nystrom_apply(X, V, kernel, theta, k: int, tol: float = 0.0, want_L: bool = False,
+                     ls=None, ws=None):
+    """Nystrom preconditioner of rank <= k: returns (Z = M^-1 V (n, w), L (n, rank)
+    float32 or None, pivots (rank,), rank)."""
+    prob, X = problem(X, kernel, theta, ls)
+    V = _f32(V, "V")
+    if V.dim() == 1:
+        V = V[:, None]
+    n, w = V.shape
+    if n != X.shape[0]:
+        raise ValueError("V must have n rows")
+    Z = torch.empty_like(V)
+    kk = min(int(k), n)
+    Lc = torch.empty((kk, n), dtype=torch.float32, device=X.device) if want_L else None
+    piv = (ctypes.c_int64 * max(kk, 1))()
+    rank = c_int32()
+    if ws is None:
+        ws = workspace(B.OP_NYSTROM, prob, w, solve_opts(precond_rank=k), X.device)
+    check(lib().gp_nystrom_apply(byref(prob), int(k), float(tol), _ptr(V), w, _ptr(Z), _ptr(Lc),
+                                 piv, byref(rank), _ptr(ws), ws.numel(), _stream(X.device)),
+          "gp_nystrom_apply")
+    r = rank.value
+    L = None if Lc is None else Lc[:r].t()
+    return Z, L, list(piv)[:r], r
 
 
 def gp_pcg_solve_refined(X, Bm, kernel, theta, opts: B.gp_solve_opts, raise_not_converged=True,

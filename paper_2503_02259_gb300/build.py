@@ -37,6 +37,7 @@ UNITS = SIMT_UNITS + [
     ("vec_kernels", "vec_kernels.cu", []),
     ("residual", "residual.cu", []),
     ("residual_pair", "residual_pair.cu", []),
+    ("nystrom", "nystrom.cu", []),
     ("grad_ard", "grad_ard.cu", []),
     ("server", "server.cu", []),
     ("static_scratch", "static_scratch.cu", []),

@@ -19,6 +19,7 @@
 
 #include "gp_api_internal.h"
 #include "grad_ard.cuh"
+#include "nystrom.cuh"
 #include "kmv_tc.cuh"
 #include "residual.cuh"
 #include "vec_kernels.cuh"
@@ -439,8 +440,15 @@ static gp_status check_width(int32_t w) {
   return GP_OK;
 }
 
-static gp_status check_opts(const gp_solve_opts* o, bool need_probes) {
+static gp_status check_opts(const gp_solve_opts* o, bool need_probes, bool precond_ok = false) {
   if (o == nullptr) return fail(GP_ERR_ARG, "opts is NULL");
+  if (o->precond_rank < 0 || o->precond_rank > GP_MAX_PRECOND_RANK)
+    return fail(GP_ERR_ARG, "precond_rank must be in [0, 4096]");
+  if (o->precond_rank > 0 && !precond_ok)
+    return fail(GP_ERR_UNIMPLEMENTED,
+                "the Nystrom preconditioner is taken by gp_pcg_solve and gp_pcg_solve_refined only");
+  if (!(o->precond_tol <= 1.0) && !(o->precond_tol > 1.0))
+    return fail(GP_ERR_ARG, "precond_tol is NaN");
   if (o->nprobe < 0 || o->nprobe + 1 > GP_MAX_COLS) return fail(GP_ERR_ARG, "nprobe must be in [0, 127]");
   if (need_probes && o->nprobe < 1) return fail(GP_ERR_ARG, "nprobe must be >= 1");
   if (o->nlanczos < 1 || o->nlanczos > GP_MAX_LANCZOS)
@@ -553,6 +561,73 @@ static gp_status product_call(const gp_problem* prob, const float* V, int32_t w,
 }
 
 // ---------------------------------------------------------------------------
+// Nystrom preconditioner of a solve (nystrom.cuh): the preconditioned residual
+// plane Z and the factor's workspace, placed after the solver's workspace.
+// ---------------------------------------------------------------------------
+namespace gp {
+
+struct Precond {
+  NysWs ws;
+  float* Z = nullptr;   // [n_pad][w_pad]
+  int rank = 0;
+  double s = 0.0;
+};
+
+static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+static size_t precond_bytes(int64_t n_pad, int d, int kmax, int w_pad) {
+  return align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad) +
+         nys_bytes(n_pad, d, kmax, w_pad) + 256;
+}
+
+static Precond carve_precond(void* base, int64_t n_pad, int d, int kmax, int w_pad) {
+  Precond pc;
+  char* b = static_cast<char*>(base);
+  pc.Z = reinterpret_cast<float*>(b);
+  pc.ws = carve_nys(b + align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad), n_pad, d, kmax,
+                    w_pad);
+  return pc;
+}
+
+static int precond_kmax(const gp_problem* prob, int rank) {
+  return static_cast<int>(std::min<int64_t>(rank, prob->n));
+}
+
+}  // namespace gp
+
+// Bytes of the plain (unrefined) solver workspace of gp_pcg_solve.
+static size_t solve_bytes(const gp_problem* prob, int w, int prec) {
+  SimtPlan pc = plan_for(prob->n, prob->n, prob->d, w, false, prob->kernel, prec);
+  SimtPlan pg = plan_for(prob->n, prob->n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
+  unify_width(pc, pg);
+  return carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes;
+}
+
+// gp_nystrom_apply: the padded V block, then the preconditioner (whose Z plane
+// receives M^-1 V).
+static size_t nystrom_entry_bytes(const gp_problem* prob, int w, int kmax) {
+  const int64_t n_pad = round_up(prob->n, kPad);
+  const int w_pad = static_cast<int>(round_up(w, 4));
+  return align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad) +
+         precond_bytes(n_pad, prob->d, kmax, w_pad);
+}
+
+static gp_status build_precond(const gp_problem* prob, int kmax, double tol, Precond& pc,
+                               cudaStream_t st) {
+  NysProblem P{prob->X, prob->n, prob->d, prob->kernel, prob->theta.f, prob->theta.l, prob->theta.s,
+               prob->ls};
+  int rank = 0, derr = 0;
+  const double tol_abs = tol > 0 ? tol * prob->theta.f * prob->theta.f : 0.0;
+  const cudaError_t e = nys_build(pc.ws, P, kmax, tol_abs, &rank, &derr, st);
+  if (e == cudaErrorInvalidValue && derr != 0)
+    return fail(GP_ERR_NUMERIC, "Nystrom preconditioner: C = s I + L^T L met a non-positive pivot");
+  if (e != cudaSuccess) return cuda_fail(e, "nys_build");
+  pc.rank = rank;
+  pc.s = prob->theta.s;
+  return GP_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Block CG host loop.
 // ---------------------------------------------------------------------------
 namespace gp {
@@ -561,12 +636,22 @@ namespace gp {
 // p update (vec_kernels.cu), as one cooperative launch when `fused`, else as
 // three launches with the same arithmetic.
 static gp_status cg_iteration(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W,
-                              bool fused, cudaStream_t st) {
+                              bool fused, const Precond* pc, cudaStream_t st) {
   const int64_t n = prob->n;
   const double f2 = prob->theta.f * prob->theta.f;
   gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, W.P, W.vt, W.part, nullptr,
                             &W.S->n_active, &W.S->err, st);
   if (s != GP_OK) return s;
+  if (pc != nullptr) {
+    // Preconditioned: alpha = r^T z / p^T Kh p; x, r; z = M^-1 r; beta; p = z + beta p.
+    GP_CUDA(launch_cg_epi_alpha(W.S, W.part, p.split, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
+                                prob->theta.s, W.red, st));
+    GP_CUDA(launch_pcg_update(W.S, W.X, W.R, W.P, W.Q, p.nr_pad, p.w_pad, W.red, st));
+    GP_CUDA(nys_apply(pc->ws, pc->rank, n, pc->s, W.R, pc->Z, &W.S->n_active, st));
+    GP_CUDA(launch_pcg_rz(W.S, W.R, pc->Z, p.nr_pad, p.w_pad, false, W.red, st));
+    GP_CUDA(launch_cg_pupdate(W.S, pc->Z, W.P, p.nr_pad, p.w_pad, st));
+    return GP_OK;
+  }
   if (fused) {
     GP_CUDA(launch_cg_step(W.S, W.part, p.split, W.X, W.R, W.P, W.Q, p.nr_pad, n, p.w_pad, f2,
                            prob->theta.s, W.red, st));
@@ -648,8 +733,14 @@ class IterationGraph {
 };
 
 gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W, int w, int maxit,
-                 double rtol, cudaStream_t st) {
+                 double rtol, cudaStream_t st, const Precond* pc = nullptr) {
   GP_CUDA(launch_cg_init(W.S, W.B, W.X, W.R, W.P, p.nr_pad, p.w_pad, w, maxit, rtol, W.red, st));
+  if (pc != nullptr) {
+    // z_0 = M^-1 r_0, r^T z, p_0 = z_0.
+    GP_CUDA(nys_apply(pc->ws, pc->rank, prob->n, pc->s, W.R, pc->Z, &W.S->n_active, st));
+    GP_CUDA(launch_pcg_rz(W.S, W.R, pc->Z, p.nr_pad, p.w_pad, true, W.red, st));
+    GP_CUDA(launch_cg_pupdate(W.S, pc->Z, W.P, p.nr_pad, p.w_pad, st));
+  }
   int chunk = 4;
   int issued = 0;
   struct {
@@ -661,19 +752,20 @@ gp_status run_cg(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W
   // graph could not be built.
   IterationGraph graph;
   bool tried = false, use_graph = false;
-  const bool fused = thread_cooperative() && cg_fused_wanted() && cg_step_fits(p.nr_pad);
+  const bool fused =
+      pc == nullptr && thread_cooperative() && cg_fused_wanted() && cg_step_fits(p.nr_pad);
   while (issued < maxit) {
     const int todo = std::min(chunk, maxit - issued);
     for (int k = 0; k < todo; ++k) {
       if (issued + k > 0 && !tried) {
         tried = true;
         use_graph = graph.capture(
-            [&](cudaStream_t cs) { return cg_iteration(prob, p, prec, W, fused, cs); });
+            [&](cudaStream_t cs) { return cg_iteration(prob, p, prec, W, fused, pc, cs); });
       }
       if (use_graph) {
         GP_CUDA(graph.launch(st));
       } else {
-        gp_status s = cg_iteration(prob, p, prec, W, fused, st);
+        gp_status s = cg_iteration(prob, p, prec, W, fused, pc, st);
         if (s != GP_OK) return s;
       }
     }
@@ -996,9 +1088,18 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
   SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
   unify_width(pc, pg);   // the widths setup_solve uses
-  if ((s = check_ws(ws, ws_bytes, refine_bytes(pc, prec, n, w))) != GP_OK) return s;
+  const size_t base = refine_bytes(pc, prec, n, w);
+  const int kmax = precond_kmax(prob, opts->precond_rank);
+  const size_t need = kmax > 0 ? align256(base) + precond_bytes(pc.nr_pad, prob->d, kmax, pc.w_pad) : base;
+  if ((s = check_ws(ws, ws_bytes, need)) != GP_OK) return s;
   SolveSetup ss;
   if ((s = setup_solve(prob, w, false, prec, 0, prec, ws, ws_bytes, st, ss)) != GP_OK) return s;
+  Precond pcond;
+  if (kmax > 0) {
+    pcond = carve_precond(static_cast<char*>(ws) + align256(base), ss.pc.nr_pad, prob->d, kmax,
+                          ss.pc.w_pad);
+    if ((s = build_precond(prob, kmax, opts->precond_tol, pcond, st)) != GP_OK) return s;
+  }
   const size_t plane = static_cast<size_t>(ss.pc.nr_pad) * ss.pc.w_pad;
   char* extra = static_cast<char*>(ws) + refine_extra_offset(ss.pc, prec);
   double* x64 = reinterpret_cast<double*>(extra);
@@ -1027,7 +1128,9 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
     bool done = true;
     for (int c = 0; c < w; ++c) done = done && !(hr.relres[c] > opts->refine_rtol);
     if (done || outer >= max_outer) break;
-    if ((s = run_cg(prob, ss.pc, prec, ss.W, w, inner_maxit, opts->cg_rtol, st)) != GP_OK) return s;
+    if ((s = run_cg(prob, ss.pc, prec, ss.W, w, inner_maxit, opts->cg_rtol, st,
+                    kmax > 0 ? &pcond : nullptr)) != GP_OK)
+      return s;
     HostCg hi;
     if ((s = read_cg(ss.W.S, hi, st)) != GP_OK) return s;
     for (int c = 0; c < w; ++c) total_iters[c] += hi.iters[c];
@@ -1391,9 +1494,21 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
       SimtPlan pc = plan_for(n, n, prob->d, w, false, prob->kernel, prec);
       SimtPlan pg = plan_for(n, n, prob->d, w, true, prob->kernel, GP_PREC_FP32);
       unify_width(pc, pg);
-      if (opts != nullptr && opts->refine_rtol > 0)
-        return refine_bytes(pc, prec, n, w);
-      return carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes;
+      const size_t base = opts != nullptr && opts->refine_rtol > 0
+                              ? refine_bytes(pc, prec, n, w)
+                              : carve_solve(nullptr, pc, pc, pc, false, 0, prec, prec).bytes;
+      if (opts == nullptr || opts->precond_rank == 0) return base;
+      if (check_opts(opts, false, true) != GP_OK) return 0;
+      return align256(base) +
+             precond_bytes(pc.nr_pad, prob->d, precond_kmax(prob, opts->precond_rank), pc.w_pad);
+    }
+    case GP_OP_NYSTROM: {
+      if (check_width(w) != GP_OK) return 0;
+      if (opts == nullptr || opts->precond_rank < 1 || opts->precond_rank > GP_MAX_PRECOND_RANK) {
+        set_error("GP_OP_NYSTROM needs opts->precond_rank in [1, 4096]");
+        return 0;
+      }
+      return nystrom_entry_bytes(prob, w, precond_kmax(prob, opts->precond_rank));
     }
     case GP_OP_SLQ:
     case GP_OP_LOSS_GRAD: {
@@ -1426,7 +1541,7 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   gp_status s;
   if ((s = check_problem(prob)) != GP_OK) return s;
   if ((s = check_width(w)) != GP_OK) return s;
-  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if ((s = check_opts(opts, false, true)) != GP_OK) return s;
   if (B == nullptr || Xsol == nullptr) return fail(GP_ERR_ARG, "B and Xsol must be non-NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0 &&
@@ -1434,12 +1549,22 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
     return s;
   if (opts->prec != GP_PREC_FP32 && opts->refine_rtol > 0)
     return refine_solve(prob, B, w, Xsol, nullptr, opts, iters, relres, ws, ws_bytes, st);
+  const int kmax = precond_kmax(prob, opts->precond_rank);
+  const size_t base = solve_bytes(prob, w, opts->prec);
+  if (kmax > 0 && (s = check_ws(ws, ws_bytes, gp_workspace_bytes(GP_OP_PCG, prob, w, opts))) != GP_OK)
+    return s;
   SolveSetup ss;
   if ((s = setup_solve(prob, w, false, opts->prec, 0, opts->prec, ws, ws_bytes, st, ss)) != GP_OK)
     return s;
+  Precond pcond;
+  if (kmax > 0) {
+    pcond = carve_precond(static_cast<char*>(ws) + align256(base), ss.pc.nr_pad, prob->d, kmax,
+                          ss.pc.w_pad);
+    if ((s = build_precond(prob, kmax, opts->precond_tol, pcond, st)) != GP_OK) return s;
+  }
   GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
   const int maxit = effective_maxit(prob, opts);
-  s = run_cg(prob, ss.pc, opts->prec, ss.W, w, maxit, opts->cg_rtol, st);
+  s = run_cg(prob, ss.pc, opts->prec, ss.W, w, maxit, opts->cg_rtol, st, kmax > 0 ? &pcond : nullptr);
   if (s != GP_OK) return s;
   GP_CUDA(launch_unpad_block(ss.W.X, prob->n, w, ss.pc.w_pad, Xsol, w, 0, st));
   HostCg h;
@@ -1457,12 +1582,47 @@ gp_status gp_pcg_solve_refined(const gp_problem* prob, const float* B, int32_t w
   gp_status s;
   if ((s = check_problem(prob)) != GP_OK) return s;
   if ((s = check_width(w)) != GP_OK) return s;
-  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if ((s = check_opts(opts, false, true)) != GP_OK) return s;
   if (B == nullptr || X64 == nullptr) return fail(GP_ERR_ARG, "B and X64 must be non-NULL");
   if (!(opts->refine_rtol > 0)) return fail(GP_ERR_ARG, "refine_rtol must be > 0");
   if ((s = no_ard(prob, "iterative refinement")) != GP_OK) return s;
   return refine_solve(prob, B, w, nullptr, X64, opts, iters, relres, ws, ws_bytes,
                       static_cast<cudaStream_t>(stream));
+}
+
+gp_status gp_nystrom_apply(const gp_problem* prob, int32_t k, double tol, const float* V, int32_t w,
+                           float* Z, float* L, int64_t* piv, int32_t* rank, void* ws,
+                           size_t ws_bytes, void* stream) {
+  gp_status s;
+  if ((s = check_problem(prob)) != GP_OK) return s;
+  if ((s = check_width(w)) != GP_OK) return s;
+  if (k < 1 || k > GP_MAX_PRECOND_RANK) return fail(GP_ERR_ARG, "k must be in [1, 4096]");
+  if (!(tol <= 1.0) && !(tol > 1.0)) return fail(GP_ERR_ARG, "tol is NaN");
+  if (V == nullptr || Z == nullptr || rank == nullptr)
+    return fail(GP_ERR_ARG, "V, Z and rank must be non-NULL");
+  const int kmax = precond_kmax(prob, k);
+  if ((s = check_ws(ws, ws_bytes, nystrom_entry_bytes(prob, w, kmax))) != GP_OK) return s;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t n = prob->n;
+  const int64_t n_pad = round_up(n, kPad);
+  const int w_pad = static_cast<int>(round_up(w, 4));
+  float* Vp = static_cast<float*>(ws);
+  Precond pc = carve_precond(static_cast<char*>(ws) +
+                                 align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad),
+                             n_pad, prob->d, kmax, w_pad);
+  GP_CUDA(cudaMemsetAsync(Vp, 0, sizeof(float) * static_cast<size_t>(n_pad) * w_pad, st));
+  GP_CUDA(launch_pad_block(V, n, w, w, Vp, n_pad, w_pad, 0, st));
+  if ((s = build_precond(prob, kmax, tol, pc, st)) != GP_OK) return s;
+  GP_CUDA(nys_apply(pc.ws, pc.rank, n, pc.s, Vp, pc.Z, nullptr, st));
+  GP_CUDA(launch_unpad_block(pc.Z, n, w, w_pad, Z, w, 0, st));
+  if (L != nullptr)
+    GP_CUDA(cudaMemcpy2DAsync(L, sizeof(float) * n, pc.ws.Lt, sizeof(float) * n_pad, sizeof(float) * n,
+                              pc.rank, cudaMemcpyDeviceToDevice, st));
+  if (piv != nullptr)
+    GP_CUDA(cudaMemcpyAsync(piv, pc.ws.piv, sizeof(int64_t) * pc.rank, cudaMemcpyDeviceToHost, st));
+  GP_CUDA(cudaStreamSynchronize(st));
+  *rank = pc.rank;
+  return GP_OK;
 }
 
 gp_status gp_true_residual(const gp_problem* prob, const float* B, const float* X, int32_t w,

@@ -1,0 +1,695 @@
+// Nystrom preconditioner M = s I + L L^T (see nystrom.cuh): the partial
+// pivoted Cholesky factor L of f^2 K, the Gram matrix C = s I + L^T L, C's FP64
+// Cholesky factorisation and inverse, and the application M^-1 V by the
+// Woodbury identity.
+//
+// Accurate dot products: acc_prod is the Dot2 scheme of Ogita, Rump and Oishi
+// ("Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005): the
+// exact product a b = p + e (TwoProd), TwoSum of p into the running high part,
+// and the two rounding errors summed into the low part.  The result carries the
+// error of a dot product computed in twice the working precision.
+#include <math.h>
+
+#include <algorithm>
+#include <climits>
+
+#include "nystrom.cuh"
+
+namespace gp {
+
+namespace {
+
+constexpr int kStepThreads = 256;
+constexpr int kStepRows = 4;                      // rows per thread (one float4 per column of L)
+constexpr int kStepRowsPerBlock = kStepThreads * kStepRows;
+constexpr int kGT = 64;                           // Gram tile (columns of L)
+constexpr int kGK = 32;                           // Gram rows per shared-memory slab
+constexpr int kLtvChunk = 4096;                   // rows per block of L^T V
+constexpr int kZTile = 512;                       // rows of T staged per pass of the Z kernel
+constexpr int kInvWarps = 2;                      // columns of C^-1 per block
+
+__device__ __forceinline__ void acc_prod(pa::fpair& acc, float a, float b) {
+  const pa::fpair p = pa::two_prod(a, b);
+  const pa::fpair s = pa::two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = pa::add(acc.lo, pa::add(s.lo, p.lo));
+}
+
+// acc += a (thi + tlo): the product with the high part exact, the low part's
+// product folded into the error term.
+__device__ __forceinline__ void acc_prod_pair(pa::fpair& acc, float a, float thi, float tlo) {
+  const pa::fpair p = pa::two_prod(a, thi);
+  const pa::fpair s = pa::two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = pa::add(acc.lo, pa::add(s.lo, pa::fma_(a, tlo, p.lo)));
+}
+
+__device__ __forceinline__ void renorm(pa::fpair& a) { a = pa::fast_two_sum(a.hi, a.lo); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ pa::fpair warp_sum_pair(pa::fpair v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const pa::fpair w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = pa::add(v, w);
+  }
+  return v;
+}
+
+// (v, i) <- the better of (v, i) and (v2, i2): larger value, then smaller index.
+__device__ __forceinline__ void better(double& v, long long& i, double v2, long long i2) {
+  if (v2 > v || (v2 == v && i2 < i)) {
+    v = v2;
+    i = i2;
+  }
+}
+
+__device__ __forceinline__ void warp_argmax(double& v, long long& i) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double v2 = __shfl_xor_sync(0xffffffffu, v, o);
+    const long long i2 = __shfl_xor_sync(0xffffffffu, i, o);
+    better(v, i, v2, i2);
+  }
+}
+
+// True in exactly one block: the last to arrive (its reads see every block's writes).
+__device__ __forceinline__ bool last_block(unsigned* ticket) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(ticket, 1u);
+    am_last = (t == gridDim.x * gridDim.y * gridDim.z - 1);
+    if (am_last) *ticket = 0u;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+struct StageScales {
+  float v[GP_MAX_DIM];
+};
+
+// ----------------------------------------------------------- factor steps --
+
+// xs = scaled points; dg = f^2 (the diagonal of f^2 K, k(0) = 1); state reset
+// with the first pivot 0 (every diagonal entry is equal, and ties go to the
+// smallest index).
+__global__ void nys_init_kernel(const float* X, int64_t n, int d, const StageScales sc,
+                                int64_t n_pad, double f2, float* xs, double* dg, NysState* S) {
+  for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_pad;
+       i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    for (int t = 0; t < d; ++t) xs[i * d + t] = i < n ? X[i * d + t] * sc.v[t] : 0.0f;
+    dg[i] = i < n ? f2 : 0.0;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->rank = 0;
+    S->stop = 0;
+    S->err = 0;
+    S->pivot = 0;
+    S->dp = f2;
+    S->ticket = 0u;
+  }
+}
+
+struct StepArgs {
+  const float* xs;
+  int64_t n, n_pad;
+  int d, kernel;
+  pa::fpair kc;
+  double f2, tol_abs;
+  int kmax;
+  float* Lt;
+  double* dg;
+  float* prow;
+  long long* piv;
+  double* amax_v;
+  long long* amax_i;
+  NysState* S;
+};
+
+// Step j: with p the current pivot and d_p its residual diagonal,
+//   L[i][j] = (f^2 k(x_i, x_p) - sum_{m<j} L[i][m] L[p][m]) / sqrt(d_p),
+//   d_i -= L[i][j]^2 (d_p = 0), and the next pivot = argmax_i d_i.
+// The kernel entry is the pair exponential of the compensated residual and
+// the dot product is Dot2, so the column is exact for the stored (FP32)
+// earlier columns up to its final rounding; d is kept in FP64 as the exact
+// residual diagonal of the stored factor.
+template <int DMAX>
+__global__ void __launch_bounds__(kStepThreads)
+    nys_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ pa::ExpConsts C, int j) {
+  extern __shared__ float sp[];   // row p of L, columns < j
+  NysState* S = a.S;
+  if (S->stop) return;
+  const long long p = S->pivot;
+  const double dp = S->dp;
+  for (int m = threadIdx.x; m < j; m += blockDim.x) sp[m] = a.prow[m];
+  float xp[DMAX];
+#pragma unroll
+  for (int t = 0; t < DMAX; ++t) xp[t] = t < a.d ? a.xs[p * a.d + t] : 0.0f;
+  __syncthreads();
+  const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x) * kStepRows;
+  double best = -INFINITY;
+  long long besti = LLONG_MAX;
+  if (i0 < a.n_pad) {
+    pa::fpair acc[kStepRows] = {};
+    const float* col = a.Lt + i0;
+    for (int m = 0; m < j; ++m) {
+      const float4 l = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m) * a.n_pad);
+      const float b = sp[m];
+      acc_prod(acc[0], l.x, b);
+      acc_prod(acc[1], l.y, b);
+      acc_prod(acc[2], l.z, b);
+      acc_prod(acc[3], l.w, b);
+    }
+    const double inv = 1.0 / sqrt(dp);
+    float out[kStepRows];
+#pragma unroll
+    for (int q = 0; q < kStepRows; ++q) {
+      const int64_t i = i0 + q;
+      float c = 0.0f;
+      if (i < a.n) {
+        const pa::fpair r2 = pa::sqdist<DMAX>(a.xs + i * a.d, xp, a.d);
+        const pa::fpair k = pa::kernel_entry(r2, a.kernel, a.kc, C);
+        c = static_cast<float>((a.f2 * pa::to_double(k) - pa::to_double(acc[q])) * inv);
+        double dn = a.dg[i] - static_cast<double>(c) * c;
+        if (i == p) dn = 0.0;
+        a.dg[i] = dn;
+        better(best, besti, dn, i);
+      }
+      out[q] = c;
+    }
+    *reinterpret_cast<float4*>(a.Lt + static_cast<int64_t>(j) * a.n_pad + i0) =
+        make_float4(out[0], out[1], out[2], out[3]);
+  }
+  // Block argmax, then the last block picks the next pivot.
+  __shared__ double wv[kStepThreads / 32];
+  __shared__ long long wi[kStepThreads / 32];
+  warp_argmax(best, besti);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (lane == 0) {
+    wv[warp] = best;
+    wi[warp] = besti;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = -INFINITY;
+    long long ix = LLONG_MAX;
+    for (int w = 0; w < kStepThreads / 32; ++w) better(v, ix, wv[w], wi[w]);
+    a.amax_v[blockIdx.x] = v;
+    a.amax_i[blockIdx.x] = ix;
+  }
+  if (!last_block(&S->ticket)) return;
+  __shared__ int go_on;
+  __shared__ long long next;
+  if (warp == 0) {
+    double v = -INFINITY;
+    long long ix = LLONG_MAX;
+    for (unsigned b = lane; b < gridDim.x; b += 32) better(v, ix, a.amax_v[b], a.amax_i[b]);
+    warp_argmax(v, ix);
+    if (lane == 0) {
+      a.piv[j] = p;
+      S->rank = j + 1;
+      const bool cont = (v > a.tol_abs) && (j + 1 < a.kmax) && ix < a.n;
+      S->stop = cont ? 0 : 1;
+      S->pivot = cont ? ix : 0;
+      S->dp = v;
+      go_on = cont ? 1 : 0;
+      next = ix;
+    }
+  }
+  __syncthreads();
+  if (go_on) {
+    for (int m = threadIdx.x; m <= j; m += blockDim.x)
+      a.prow[m] = a.Lt[static_cast<int64_t>(m) * a.n_pad + next];
+  }
+}
+
+// ------------------------------------------------------------------- Gram --
+
+// Partial sums of L^T L over one chunk of rows, for one 64 x 64 tile pair
+// (ta >= tb) of the lower triangle.  Dot2 accumulation, renormalised per slab.
+__global__ void __launch_bounds__(256)
+    nys_gram_kernel(const float* __restrict__ Lt, int64_t n_pad, int r, int64_t rows_per_chunk,
+                    int pairs, double* gpart) {
+  __shared__ __align__(16) float As[kGK][kGT + 4];
+  __shared__ __align__(16) float Bs[kGK][kGT + 4];
+  const int t = blockIdx.x;
+  int ta = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+  while (ta * (ta + 1) / 2 > t) --ta;
+  while ((ta + 1) * (ta + 2) / 2 <= t) ++ta;
+  const int tb = t - ta * (ta + 1) / 2;
+  const int64_t i_begin = static_cast<int64_t>(blockIdx.y) * rows_per_chunk;
+  const int64_t i_end = i_begin + rows_per_chunk < n_pad ? i_begin + rows_per_chunk : n_pad;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  pa::fpair acc[4][4] = {};
+  for (int64_t i0 = i_begin; i0 < i_end; i0 += kGK) {
+    for (int q = threadIdx.x; q < kGT * (kGK / 4); q += blockDim.x) {
+      const int aa = q / (kGK / 4), part = q % (kGK / 4);
+      const int ra = ta * kGT + aa, rb = tb * kGT + aa;
+      float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
+      if (ra < r) va = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(ra) * n_pad + i0 + part * 4);
+      if (rb < r) vb = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(rb) * n_pad + i0 + part * 4);
+      As[part * 4 + 0][aa] = va.x;
+      As[part * 4 + 1][aa] = va.y;
+      As[part * 4 + 2][aa] = va.z;
+      As[part * 4 + 3][aa] = va.w;
+      Bs[part * 4 + 0][aa] = vb.x;
+      Bs[part * 4 + 1][aa] = vb.y;
+      Bs[part * 4 + 2][aa] = vb.z;
+      Bs[part * 4 + 3][aa] = vb.w;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int ii = 0; ii < kGK; ++ii) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[ii][ty * 4]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[ii][tx * 4]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w};
+      const float bv[4] = {b4.x, b4.y, b4.z, b4.w};
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc_prod(acc[p][q], av[p], bv[q]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) renorm(acc[p][q]);
+    __syncthreads();
+  }
+  double* out = gpart + (static_cast<int64_t>(blockIdx.y) * pairs + t) * (kGT * kGT);
+#pragma unroll
+  for (int p = 0; p < 4; ++p)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) out[(ty * 4 + p) * kGT + tx * 4 + q] = pa::to_double(acc[p][q]);
+}
+
+// C[a][b] = sum over chunks (fixed order) + s [a == b] for a >= b; 0 above.
+__global__ void nys_gram_reduce_kernel(const double* gpart, int r, int pairs, int chunks, double s,
+                                       double* C) {
+  const int64_t total = static_cast<int64_t>(r) * r;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int a = static_cast<int>(e / r), b = static_cast<int>(e % r);
+    if (b > a) {
+      C[e] = 0.0;
+      continue;
+    }
+    const int ta = a / kGT, tb = b / kGT;
+    const int t = ta * (ta + 1) / 2 + tb;
+    const int64_t off = static_cast<int64_t>(t) * (kGT * kGT) + (a % kGT) * kGT + (b % kGT);
+    double v = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) v += gpart[static_cast<int64_t>(ch) * pairs * (kGT * kGT) + off];
+    C[e] = a == b ? v + s : v;
+  }
+}
+
+// ------------------------------------------------------- C's factorisation --
+
+// Right-looking step j of the outer-product Cholesky without scaling:
+// a_il -= a_ij a_lj / a_jj for j < l <= i < r (column j itself is read only).
+__global__ void nys_chol_step_kernel(double* C, int r, int j, NysState* S) {
+  const double ajj = C[static_cast<int64_t>(j) * r + j];
+  if (!(ajj > 0.0)) {
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) S->err = kDevNumeric;
+    return;
+  }
+  if (blockIdx.x > blockIdx.y) return;   // tile entirely above the diagonal
+  __shared__ double ci[16], cl[16];
+  const int base = j + 1;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  if (threadIdx.x < 16) {
+    const int i = base + blockIdx.y * 16 + threadIdx.x;
+    ci[threadIdx.x] = i < r ? C[static_cast<int64_t>(i) * r + j] : 0.0;
+  } else if (threadIdx.x < 32) {
+    const int l = base + blockIdx.x * 16 + threadIdx.x - 16;
+    cl[threadIdx.x - 16] = l < r ? C[static_cast<int64_t>(l) * r + j] / ajj : 0.0;
+  }
+  __syncthreads();
+  const int i = base + blockIdx.y * 16 + ty, l = base + blockIdx.x * 16 + tx;
+  if (i < r && l <= i) C[static_cast<int64_t>(i) * r + l] -= ci[ty] * cl[tx];
+}
+
+__global__ void nys_chol_diag_kernel(const double* C, int r, double* cdiag) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < r; j += gridDim.x * blockDim.x)
+    cdiag[j] = sqrt(C[static_cast<int64_t>(j) * r + j]);
+}
+
+// Factor entries L_C[i][j] = a_ij / sqrt(a_jj) (i >= j), mirrored above the diagonal.
+__global__ void nys_chol_scale_kernel(double* C, int r, const double* cdiag) {
+  const int64_t total = static_cast<int64_t>(r) * r;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int i = static_cast<int>(e / r), j = static_cast<int>(e % r);
+    if (j > i) continue;
+    if (i == j) {
+      C[e] = cdiag[j];
+    } else {
+      const double v = C[e] / cdiag[j];
+      C[e] = v;
+      C[static_cast<int64_t>(j) * r + i] = v;
+    }
+  }
+}
+
+// Column c of C^-1 (= row c, C symmetric): forward substitution L_C y = e_c,
+// then back substitution L_C^T x = y, one warp per column, FP64.
+__global__ void nys_inverse_kernel(const double* C, int r, double* Winv) {
+  extern __shared__ double ysh[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c = blockIdx.x * kInvWarps + warp;
+  if (c >= r) return;
+  double* y = ysh + static_cast<int64_t>(warp) * r;
+  for (int m = lane; m < c; m += 32) y[m] = 0.0;
+  __syncwarp();
+  for (int jj = c; jj < r; ++jj) {
+    const double* row = C + static_cast<int64_t>(jj) * r;
+    double part = 0.0;
+    for (int m = c + lane; m < jj; m += 32) part += row[m] * y[m];
+    part = warp_sum(part);
+    if (lane == 0) y[jj] = ((jj == c ? 1.0 : 0.0) - part) / row[jj];
+    __syncwarp();
+  }
+  for (int jj = r - 1; jj >= 0; --jj) {
+    const double* row = C + static_cast<int64_t>(jj) * r;   // upper part: L_C^T row jj
+    double part = 0.0;
+    for (int m = jj + 1 + lane; m < r; m += 32) part += row[m] * y[m];
+    part = warp_sum(part);
+    if (lane == 0) y[jj] = (y[jj] - part) / row[jj];
+    __syncwarp();
+  }
+  double* out = Winv + static_cast<int64_t>(c) * r;
+  for (int m = lane; m < r; m += 32) out[m] = y[m];
+}
+
+// ------------------------------------------------------------------ apply --
+
+// Partial sums of U = L^T V over a chunk of rows: warp w of block (x, y, z)
+// covers columns m0 .. m0 + 7 of L (m0 = 64 y + 8 w) and the four V columns
+// 4 z .. 4 z + 3; lanes stride the rows.
+__global__ void __launch_bounds__(256)
+    nys_ltv_kernel(const float* __restrict__ Lt, int64_t n_pad, int r, const float* __restrict__ V,
+                   int w_pad, double* upart, const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * 64 + warp * 8;
+  if (m0 >= r) return;
+  const int c0 = blockIdx.z * 4;
+  const int64_t i_begin = static_cast<int64_t>(blockIdx.x) * kLtvChunk;
+  const int64_t i_end = i_begin + kLtvChunk < n_pad ? i_begin + kLtvChunk : n_pad;
+  pa::fpair acc[8][4] = {};
+  for (int64_t i = i_begin + lane; i < i_end; i += 32) {
+    const float4 v = *reinterpret_cast<const float4*>(V + i * w_pad + c0);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      if (m0 + q < r) {
+        const float l = Lt[static_cast<int64_t>(m0 + q) * n_pad + i];
+        acc_prod(acc[q][0], l, v.x);
+        acc_prod(acc[q][1], l, v.y);
+        acc_prod(acc[q][2], l, v.z);
+        acc_prod(acc[q][3], l, v.w);
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      const pa::fpair s = warp_sum_pair(acc[q][cc]);
+      if (lane == 0 && m0 + q < r)
+        upart[(static_cast<int64_t>(blockIdx.x) * r + m0 + q) * w_pad + c0 + cc] = pa::to_double(s);
+    }
+}
+
+__global__ void nys_u_reduce_kernel(const double* upart, int chunks, int r, int w_pad, double* U,
+                                    const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t total = static_cast<int64_t>(r) * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    double v = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) v += upart[static_cast<int64_t>(ch) * total + e];
+    U[e] = v;
+  }
+}
+
+// T = C^-1 U (FP64), stored as FP32 pairs; one warp per (row m, 4 columns).
+__global__ void nys_wu_kernel(const double* Winv, const double* U, int r, int w_pad, float* Tp,
+                              const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m = blockIdx.x * (blockDim.x >> 5) + warp;
+  if (m >= r) return;
+  const int c0 = blockIdx.y * 4;
+  const double* row = Winv + static_cast<int64_t>(m) * r;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int q = lane; q < r; q += 32) {
+    const double wq = row[q];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) acc[cc] += wq * U[static_cast<int64_t>(q) * w_pad + c0 + cc];
+  }
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    const double t = warp_sum(acc[cc]);
+    if (lane == 0) {
+      const pa::fpair p = pa::from_double(t);
+      float* o = Tp + (static_cast<int64_t>(m) * w_pad + c0 + cc) * 2;
+      o[0] = p.hi;
+      o[1] = p.lo;
+    }
+  }
+}
+
+// Z = (V - L T) / s for the four columns 4 y .. 4 y + 3; one row per thread.
+__global__ void __launch_bounds__(256)
+    nys_z_kernel(const float* __restrict__ Lt, int64_t n_pad, int64_t n, int r, const float* Tp,
+                 const float* __restrict__ V, float* Z, int w_pad, double s, const int* active) {
+  if (active != nullptr && *active == 0) return;
+  __shared__ float sT[kZTile][8];
+  const int c0 = blockIdx.y * 4;
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  pa::fpair acc[4] = {};
+  for (int mt = 0; mt < r; mt += kZTile) {
+    const int mcount = r - mt < kZTile ? r - mt : kZTile;
+    __syncthreads();
+    for (int q = threadIdx.x; q < kZTile * 4; q += blockDim.x) {
+      const int mm = q >> 2, cc = q & 3;
+      float hi = 0.0f, lo = 0.0f;
+      if (mm < mcount) {
+        const float* t = Tp + (static_cast<int64_t>(mt + mm) * w_pad + c0 + cc) * 2;
+        hi = t[0];
+        lo = t[1];
+      }
+      sT[mm][2 * cc] = hi;
+      sT[mm][2 * cc + 1] = lo;
+    }
+    __syncthreads();
+    if (i < n) {
+      const float* col = Lt + static_cast<int64_t>(mt) * n_pad + i;
+      for (int mm = 0; mm < mcount; ++mm) {
+        const float l = col[static_cast<int64_t>(mm) * n_pad];
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc_prod_pair(acc[cc], l, sT[mm][2 * cc], sT[mm][2 * cc + 1]);
+      }
+#pragma unroll
+      for (int cc = 0; cc < 4; ++cc) renorm(acc[cc]);
+    }
+  }
+  if (i >= n_pad) return;
+#pragma unroll
+  for (int cc = 0; cc < 4; ++cc) {
+    float z = 0.0f;
+    if (i < n) z = static_cast<float>((static_cast<double>(V[i * w_pad + c0 + cc]) - pa::to_double(acc[cc])) / s);
+    Z[i * w_pad + c0 + cc] = z;
+  }
+}
+
+int grid_for(int64_t total, int threads, int cap = 152 * 16) {
+  int64_t b = (total + threads - 1) / threads;
+  if (b > cap) b = cap;
+  return static_cast<int>(b < 1 ? 1 : b);
+}
+
+int gram_chunks(int pairs) { return std::max(1, std::min(16, (608 + pairs - 1) / pairs)); }
+
+// Tile slots of the Gram partial sums for any rank up to kmax (chunks x pairs
+// is not monotone in the rank).
+size_t gram_slots(int kmax) {
+  const int tiles = (kmax + kGT - 1) / kGT;
+  size_t most = 0;
+  for (int t = 1; t <= tiles; ++t) {
+    const int pairs = t * (t + 1) / 2;
+    most = std::max(most, static_cast<size_t>(gram_chunks(pairs)) * pairs);
+  }
+  return most;
+}
+
+int64_t round_up64(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct NysCarve {
+  char* base;
+  size_t off = 0;
+  explicit NysCarve(void* b) : base(static_cast<char*>(b)) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~static_cast<size_t>(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+}  // namespace
+
+NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad) {
+  NysCarve c(base);
+  NysWs w;
+  const int step_blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
+  const int64_t chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
+  w.xs = c.take<float>(static_cast<size_t>(n_pad) * d);
+  w.Lt = c.take<float>(static_cast<size_t>(kmax) * n_pad);
+  w.dg = c.take<double>(n_pad);
+  w.prow = c.take<float>(kmax);
+  w.piv = c.take<long long>(kmax);
+  w.amax_v = c.take<double>(step_blocks);
+  w.amax_i = c.take<long long>(step_blocks);
+  w.S = c.take<NysState>(1);
+  w.C = c.take<double>(static_cast<size_t>(kmax) * kmax);
+  w.cdiag = c.take<double>(kmax);
+  w.Winv = c.take<double>(static_cast<size_t>(kmax) * kmax);
+  w.gpart = c.take<double>(gram_slots(kmax) * kGT * kGT);
+  w.upart = c.take<double>(static_cast<size_t>(chunks) * kmax * w_pad);
+  w.U = c.take<double>(static_cast<size_t>(kmax) * w_pad);
+  w.Tp = c.take<float>(static_cast<size_t>(kmax) * w_pad * 2);
+  w.n_pad = n_pad;
+  w.kmax = kmax;
+  w.w_pad = w_pad;
+  w.d = d;
+  w.bytes = c.off + 256;
+  return w;
+}
+
+size_t nys_bytes(int64_t n_pad, int d, int kmax, int w_pad) {
+  return carve_nys(nullptr, n_pad, d, kmax, w_pad).bytes;
+}
+
+cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_abs, int* rank,
+                      int* dev_err, cudaStream_t st) {
+  *rank = 0;
+  *dev_err = 0;
+  if (kmax < 1 || kmax > W.kmax || P.d > GP_MAX_DIM || P.d != W.d) return cudaErrorInvalidValue;
+  const int64_t n_pad = W.n_pad;
+  const double f2 = P.f * P.f;
+  StageScales sc;
+  for (int t = 0; t < GP_MAX_DIM; ++t) sc.v[t] = 1.0f;
+  double kl = P.l;
+  if (P.ls != nullptr) {
+    for (int t = 0; t < P.d; ++t) sc.v[t] = static_cast<float>(1.0 / P.ls[t]);
+    kl = 1.0;
+  }
+  nys_init_kernel<<<grid_for(n_pad, 256), 256, 0, st>>>(P.X, P.n, P.d, sc, n_pad, f2, W.xs, W.dg, W.S);
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  static pa::ExpConsts consts = [] {
+    pa::ExpConsts c;
+    pa::make_exp_consts(c);
+    return c;
+  }();
+  StepArgs a{};
+  a.xs = W.xs;
+  a.n = P.n;
+  a.n_pad = n_pad;
+  a.d = P.d;
+  a.kernel = P.kernel;
+  a.kc = pa::kernel_pair_const(P.kernel, kl);
+  a.f2 = f2;
+  a.tol_abs = tol_abs;
+  a.kmax = kmax;
+  a.Lt = W.Lt;
+  a.dg = W.dg;
+  a.prow = W.prow;
+  a.piv = W.piv;
+  a.amax_v = W.amax_v;
+  a.amax_i = W.amax_i;
+  a.S = W.S;
+  const int blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
+  const size_t smem = static_cast<size_t>(kmax) * sizeof(float);
+  for (int j = 0; j < kmax; ++j) {
+    nys_step_kernel<GP_MAX_DIM><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  NysState hs;
+  if ((e = cudaMemcpyAsync(&hs, W.S, sizeof hs, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  const int r = hs.rank;
+  *rank = r;
+  if (r < 1) return cudaErrorInvalidValue;
+  // C = s I + L^T L.
+  const int tiles = (r + kGT - 1) / kGT;
+  const int pairs = tiles * (tiles + 1) / 2;
+  const int G = gram_chunks(pairs);
+  const int64_t rows_per_chunk = round_up64((n_pad + G - 1) / G, kGK);
+  nys_gram_kernel<<<dim3(pairs, G), 256, 0, st>>>(W.Lt, n_pad, r, rows_per_chunk, pairs, W.gpart);
+  count_launch();
+  nys_gram_reduce_kernel<<<grid_for(static_cast<int64_t>(r) * r, 256), 256, 0, st>>>(W.gpart, r, pairs,
+                                                                                     G, P.s, W.C);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // Cholesky factorisation of C, then C^-1.
+  for (int j = 0; j + 1 < r; ++j) {
+    const int t = (r - j - 1 + 15) / 16;
+    nys_chol_step_kernel<<<dim3(t, t), 256, 0, st>>>(W.C, r, j, W.S);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  nys_chol_diag_kernel<<<grid_for(r, 256), 256, 0, st>>>(W.C, r, W.cdiag);
+  count_launch();
+  nys_chol_scale_kernel<<<grid_for(static_cast<int64_t>(r) * r, 256), 256, 0, st>>>(W.C, r, W.cdiag);
+  count_launch();
+  const size_t ismem = static_cast<size_t>(kInvWarps) * r * sizeof(double);
+  if ((e = cudaFuncSetAttribute(nys_inverse_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                static_cast<int>(ismem))) != cudaSuccess)
+    return e;
+  nys_inverse_kernel<<<(r + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, ismem, st>>>(W.C, r, W.Winv);
+  count_launch();
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = cudaMemcpyAsync(&hs, W.S, sizeof hs, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+  if (hs.err != 0) {
+    *dev_err = hs.err;
+    return cudaErrorInvalidValue;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
+                      const int* active, cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
+  const int cg = w_pad / 4;
+  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
+  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, cg), 256, 0, st>>>(W.Lt, n_pad, rank, V, w_pad,
+                                                                      W.upart, active);
+  count_launch();
+  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
+      W.upart, chunks, rank, w_pad, W.U, active);
+  count_launch();
+  nys_wu_kernel<<<dim3((rank + 3) / 4, cg), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp, active);
+  count_launch();
+  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(
+      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, s, active);
+  count_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace gp

@@ -1,0 +1,87 @@
+// Nystrom preconditioner for the CG solves: M = s I + L L^T, where L (n x r)
+// is the rank-r partial Cholesky factor of f^2 K with greedy diagonal pivoting
+// (each step takes the point with the largest residual diagonal, so the
+// pivots are landmark points spread over the data).  The paper's PCG
+// (§Gaussian Processes) leaves M open and its own choice, AFN, also starts
+// from a Nystrom factor on chosen landmarks; this is that factor alone, used
+// for the solves.  M^-1 V = (V - L C^-1 L^T V) / s with C = s I + L^T L (the
+// Woodbury identity); C^-1 is formed once in FP64.
+//
+// Arithmetic.  L is stored in FP32.  Every sum that the Woodbury form
+// cancels (the dot products of the factor steps, the Gram matrix L^T L,
+// L^T V and L T) is taken with exact FP32 products and FP32-pair sums, so
+// the preconditioner applied is the exact inverse of s I + L L^T for the
+// stored L up to the final rounding of M^-1 V to FP32: in the directions of
+// L's large singular values sigma the result is s / (s + sigma^2) times the
+// input, and a plain FP32 sum there would carry a relative error of about
+// u sigma^2 / s (1e-1 at sigma^2 = 1.6e4, s = 1e-2).
+#pragma once
+
+#include "gp_internal.cuh"
+#include "pair_arith.cuh"
+
+namespace gp {
+
+constexpr int kNysMaxRank = GP_MAX_PRECOND_RANK;
+
+// Scalar state of the factorisation (device).
+struct NysState {
+  int rank;           // columns built
+  int stop;           // the factor has stopped (tolerance or rank reached)
+  int err;            // DevErr of the factor or of C's Cholesky factorisation
+  int pad0;
+  long long pivot;    // pivot of the next step
+  double dp;          // its residual diagonal
+  unsigned ticket;    // last-block counter
+  unsigned pad1;
+};
+
+// Inputs of the factor: the problem's points and kernel.
+struct NysProblem {
+  const float* X;     // device, n x d row-major
+  int64_t n;
+  int d;
+  int kernel;
+  double f, l, s;
+  const double* ls;   // host per-dimension length-scales (NULL: isotropic l)
+};
+
+// Workspace layout (all sizes for the largest rank kmax and width w_pad).
+struct NysWs {
+  float* xs;          // [n_pad][d] points, divided by l_t under per-dimension scales
+  float* Lt;          // [kmax][n_pad]: column j of L is row j
+  double* dg;         // [n_pad] residual diagonal
+  float* prow;        // [kmax] row of L at the next pivot
+  long long* piv;     // [kmax] pivots
+  double* amax_v;     // [step blocks] block maxima of the residual diagonal
+  long long* amax_i;  // [step blocks] their indices
+  NysState* S;
+  double* C;          // [kmax][kmax]: s I + L^T L, then its Cholesky factor (lower)
+                      // with the transposed factor in the upper triangle
+  double* cdiag;      // [kmax] sqrt of the pivots of C's factorisation
+  double* Winv;       // [kmax][kmax]: C^-1
+  double* gpart;      // Gram partial sums
+  double* upart;      // [chunks][kmax][w_pad] partial sums of L^T V
+  double* U;          // [kmax][w_pad] L^T V
+  float* Tp;          // [kmax][w_pad][2] C^-1 L^T V as FP32 pairs
+  int64_t n_pad;
+  int kmax, w_pad, d;
+  size_t bytes;
+};
+
+size_t nys_bytes(int64_t n_pad, int d, int kmax, int w_pad);
+NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad);
+
+// Builds L (at most kmax columns; stops early when the largest residual
+// diagonal is <= tol_abs), C = s I + L^T L, its FP64 Cholesky factor and C^-1.
+// Synchronises `st`; *rank = columns built; returns cudaErrorInvalidValue with
+// *dev_err != 0 if C's factorisation met a non-positive pivot.
+cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_abs, int* rank,
+                      int* dev_err, cudaStream_t st);
+
+// Z = M^-1 V on padded [n_pad][w_pad] blocks (rows >= n of Z are zero).  If
+// `active` is non-NULL and *active == 0 the kernels exit (converged solves).
+cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
+                      const int* active, cudaStream_t st);
+
+}  // namespace gp

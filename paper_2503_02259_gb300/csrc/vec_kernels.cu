@@ -393,6 +393,92 @@ __global__ void cg_update_kernel(CgState* S, float* X, float* R, const float* P,
   }
 }
 
+// Preconditioned CG (z = M^-1 r): X += alpha P; R -= alpha Q; ||R||^2 gives the
+// relative residual and the stop test.  The recurrence scalar r^T z and beta
+// come from pcg_rz_kernel after the preconditioner has been applied.
+__global__ void pcg_update_kernel(CgState* S, float* X, float* R, const float* P, const float* Q,
+                                  int64_t n_pad, int w_pad, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live) {
+    const int act = S->active[L.c];
+    const float al = static_cast<float>(S->alpha[L.c]);
+    if (act) {
+      for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+        const int64_t idx = r * w_pad + L.c;
+        X[idx] = fmaf(al, P[idx], X[idx]);
+        const float rn = fmaf(-al, Q[idx], R[idx]);
+        R[idx] = rn;
+        acc[0] += static_cast<double>(rn) * rn;
+      }
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    if (S->active[c]) {
+      const int it = S->iters[c];
+      S->iters[c] = it + 1;
+      const double rel = sqrt(tot[c] / S->bn2[c]);
+      S->relres[c] = rel;
+      if (!(rel > S->rtol) || it + 1 >= S->maxit || !isfinite(rel)) {
+        S->active[c] = 0;
+      } else {
+        atomicAdd(&cnt, 1);
+      }
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    S->n_active = cnt;
+    S->iter = S->iter + 1;
+  }
+}
+
+// rz_c = R_c^T Z_c; beta_c = rz_c / (previous rz_c) (0 when `first`); the
+// previous value is replaced (S->rr holds r^T z in preconditioned CG, the
+// numerator of alpha).  A non-positive or non-finite rz is a breakdown.
+__global__ void pcg_rz_kernel(CgState* S, const float* R, const float* Z, int64_t n_pad, int w_pad,
+                              int first, double* red) {
+  if (S->n_active == 0) return;
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live) {
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      acc[0] += static_cast<double>(R[idx]) * Z[idx];
+    }
+  }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  if (threadIdx.x < w_pad) {
+    const int c = threadIdx.x;
+    double be = 0.0;
+    if (S->active[c]) {
+      const double rz = tot[c];
+      if (!(rz > 0.0) || !isfinite(rz)) {
+        S->err = kDevBreakdown;
+        S->active[c] = 0;
+      } else {
+        be = first ? 0.0 : rz / S->rr[c];
+        S->rr[c] = rz;
+      }
+    }
+    S->beta[c] = be;
+  }
+}
+
 __global__ void cg_pupdate_kernel(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad) {
   if (S->n_active == 0) return;
   const int64_t total = n_pad * w_pad;
@@ -1091,6 +1177,20 @@ cudaError_t launch_cg_update(CgState* S, float* X, float* R, const float* P, con
 cudaError_t launch_cg_pupdate(CgState* S, const float* R, float* P, int64_t n_pad, int w_pad,
                               cudaStream_t st) {
   cg_pupdate_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, R, P, n_pad, w_pad);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_update(CgState* S, float* X, float* R, const float* P, const float* Q,
+                              int64_t n_pad, int w_pad, double* red, cudaStream_t st) {
+  pcg_update_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, X, R, P, Q, n_pad, w_pad, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_rz(CgState* S, const float* R, const float* Z, int64_t n_pad, int w_pad,
+                          bool first, double* red, cudaStream_t st) {
+  pcg_rz_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, R, Z, n_pad, w_pad, first ? 1 : 0, red);
   count_launch();
   return cudaGetLastError();
 }

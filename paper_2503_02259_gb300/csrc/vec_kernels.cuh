@@ -103,6 +103,13 @@ bool cg_step_fits(int64_t n_pad);
 cudaError_t launch_cg_step(CgState* S, const float* part_k, int split, float* X, float* R, float* P,
                            float* Q, int64_t n_pad, int64_t n, int w_pad, double f2, double snoise,
                            double* red, cudaStream_t st);
+// Preconditioned CG: X += alpha P; R -= alpha Q; relres from ||R|| (no beta).
+cudaError_t launch_pcg_update(CgState* S, float* X, float* R, const float* P, const float* Q,
+                              int64_t n_pad, int w_pad, double* red, cudaStream_t st);
+// Preconditioned CG: rz = R^T Z per column, beta = rz / rz_prev (0 if first), S->rr = rz.
+// Then launch_cg_pupdate with Z in place of R gives P = Z + beta P.
+cudaError_t launch_pcg_rz(CgState* S, const float* R, const float* Z, int64_t n_pad, int w_pad,
+                          bool first, double* red, cudaStream_t st);
 
 // Lanczos with full reorthogonalisation, one independent process per column of
 // a padded [n_pad][w_pad] block (columns [col0, col0 + p) active).

@@ -87,6 +87,37 @@ def test_argument_errors_need_no_gpu(L):
     assert st == B.GP_ERR_OOM
 
 
+def test_preconditioner_arguments_need_no_gpu(L):
+    from paper_2503_02259_gb300 import _binding as B
+    prob = B.gp_problem(256, 1000, 3, 0, B.gp_theta(0.1, 1.0, 0.3))
+    opts = B.gp_solve_opts(nprobe=4, nlanczos=10, precond_rank=50)
+    # The loss, SLQ and prediction calls do not take the preconditioner.
+    assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) == 0
+    assert b"Nystrom" in L.gp_last_error()
+    st = L.gp_loss_and_grad(ctypes.byref(prob), 256, ctypes.byref(opts), None, None, None, 256, 1 << 20,
+                            None)
+    assert st == B.GP_ERR_UNIMPLEMENTED
+    # The solve's workspace holds at least the factor's FP32 columns.
+    base = L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1,
+                                ctypes.byref(B.gp_solve_opts(nlanczos=10)))
+    withp = L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1, ctypes.byref(opts))
+    assert base > 0 and withp - base >= 4 * 1024 * 50
+    # Rank beyond n is taken as n.
+    opts.precond_rank = 4000
+    big = L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1, ctypes.byref(opts))
+    opts.precond_rank = 1000
+    assert L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1, ctypes.byref(opts)) == big
+    for bad in (-1, B.MAX_PRECOND_RANK + 1):
+        opts.precond_rank = bad
+        assert L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1, ctypes.byref(opts)) == 0
+    opts.precond_rank = 0
+    assert L.gp_workspace_bytes(B.OP_NYSTROM, ctypes.byref(prob), 1, ctypes.byref(opts)) == 0
+    rank = ctypes.c_int32()
+    st = L.gp_nystrom_apply(ctypes.byref(prob), 0, 0.0, 256, 1, 512, None, None, ctypes.byref(rank),
+                            1024, 1 << 20, None)
+    assert st == B.GP_ERR_ARG and b"k must be" in L.gp_last_error()
+
+
 def test_workspace_grows_with_problem(L):
     from paper_2503_02259_gb300 import _binding as B
     a = B.gp_problem(256, 1000, 3, 1, B.gp_theta(0.1, 1.0, 0.3))

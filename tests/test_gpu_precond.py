@@ -1,0 +1,191 @@
+"""Nystrom-preconditioned CG: the pivoted partial Cholesky factor, M^-1 V by the
+Woodbury identity, and the preconditioned solves (plain and refined).
+
+Bounds, from the arithmetic:
+ - the factor: the GPU stores each column in FP32 and computes the next one
+   exactly for the stored columns (pair kernel entry, Dot2 sums), so column j
+   differs from the FP64 oracle's (on the same pivots) by the propagated
+   storage rounding, a few u f^2 / sqrt(d_{p_j}) (u = 2^-24), checked with a
+   factor 64 of slack; a pivot is valid when its oracle residual diagonal is
+   within 64 u f^2 of the largest, and must equal the oracle's argmax when the
+   top two are further apart than that;
+ - M^-1 V: exact for the stored factor up to the final rounding to FP32 and
+   the FP64 inverse of C (kappa(C) 2^-53): 1e-6 of ||M^-1 V_c|| per column;
+ - solves: the FP32 true-residual floor u ||Kh|| ||x|| / ||b|| (times 64) on
+   top of cg_rtol; refined solves: 1e-6 recomputed by the FP64 oracle.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle as O
+from paper_2503_02259_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+U32 = 2.0 ** -24
+
+
+@pytest.fixture(scope="module")
+def api():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2503_02259_gb300 import build
+    build.build()
+    from paper_2503_02259_gb300 import api as A
+    return A
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _fK(prob, theta=None):
+    s, f, l = prob.theta if theta is None else theta
+    return f * f * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, l)
+
+
+def _check_pivots(A, piv, f2):
+    """Each GPU pivot is an argmax of the oracle's residual diagonal on the
+    GPU's earlier pivots (exactly the argmax where it is unique to 64 u f^2)."""
+    tol = 64 * U32 * f2
+    L, _, _ = O.pivoted_cholesky(A, len(piv), pivots=piv)
+    assert piv[0] == 0
+    for j, p in enumerate(piv):
+        dj = np.diag(A) - np.sum(L[:, :j] ** 2, axis=1)
+        dj[np.asarray(piv[:j], dtype=int)] = -np.inf
+        order = np.argsort(-dj, kind="stable")
+        assert dj[p] >= dj[order[0]] - tol, (j, p, dj[p], dj[order[0]])
+        if dj[order[0]] - dj[order[1]] > 2 * tol:
+            assert p == order[0], (j, p, order[0])
+    return L
+
+
+@pytest.mark.parametrize("kind,n,k,w", [(0, 701, 60, 5), (1, 1000, 120, 1), (0, 257, 16, 8)])
+def test_factor_and_apply_match_the_oracle(api, kind, n, k, w):
+    prob = inputs.uniform_problem(n, 3, kind, (0.1, 1.3, 0.3), seed=31)
+    V = inputs.gaussian_block(n, w, seed=32).astype(np.float32)
+    Z, Lg, piv, rank = api.gp_nystrom_apply(_dev(prob.X), _dev(V), kind, prob.theta, k, want_L=True)
+    assert rank == k and len(piv) == k
+    A = _fK(prob)
+    f2 = prob.theta[1] ** 2
+    Lo = _check_pivots(A, piv, f2)
+    Lg = Lg.cpu().numpy().astype(np.float64)
+    for j in range(k):
+        dp = Lo[piv[j], j] ** 2
+        err = np.abs(Lg[:, j] - Lo[:, j]).max()
+        assert err <= 64 * U32 * (f2 / np.sqrt(dp) + np.abs(Lo[:, j]).max()), (j, err, dp)
+    # M^-1 V for the stored factor, by the oracle's Woodbury solve (itself
+    # pinned against a dense solve).
+    ref = O.nystrom_apply_inverse(Lg, prob.theta[0], V.astype(np.float64))
+    Zg = Z.cpu().numpy().astype(np.float64)
+    rel = np.linalg.norm(Zg - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    assert rel.max() <= 1e-6, rel
+
+
+def test_rank_one_factor_is_the_first_kernel_column(api):
+    prob = inputs.uniform_problem(300, 2, 1, (0.05, 0.7, 0.2), seed=33)
+    V = np.ones((300, 1), dtype=np.float32)
+    _, Lg, piv, rank = api.gp_nystrom_apply(_dev(prob.X), _dev(V), 1, prob.theta, 1, want_L=True)
+    assert rank == 1 and piv == [0]
+    col = _fK(prob)[:, 0] / prob.theta[1]
+    np.testing.assert_allclose(Lg.cpu().numpy()[:, 0], col, rtol=4 * U32, atol=4 * U32)
+
+
+def test_exact_rank_stops_the_factor(api):
+    # Three clusters of identical points: f^2 K has rank 3 (Gaussian kernel,
+    # distinct centres), so the factor stops after three pivots, one per cluster.
+    X = np.repeat(np.array([[0.1, 0.2], [0.7, 0.4], [0.3, 0.9]], dtype=np.float32), 40, axis=0)
+    V = inputs.gaussian_block(120, 2, seed=34).astype(np.float32)
+    theta = (0.2, 1.0, 0.3)
+    Z, Lg, piv, rank = api.gp_nystrom_apply(_dev(X), _dev(V), 0, theta, 10, tol=1e-5, want_L=True)
+    assert rank == 3
+    assert sorted(p // 40 for p in piv) == [0, 1, 2]
+    Lg = Lg.cpu().numpy().astype(np.float64)
+    A = O.kernel_value(O.sqdist(X, X), O.GAUSSIAN, 0.3)
+    np.testing.assert_allclose(Lg @ Lg.T, A, atol=1e-6)
+    ref = np.linalg.solve(theta[0] * np.eye(120) + Lg @ Lg.T, V.astype(np.float64))
+    Zg = Z.cpu().numpy()
+    assert np.linalg.norm(Zg - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def _true_relres(Kh, Bm, Xg):
+    return np.linalg.norm(Bm - Kh @ Xg, axis=0) / np.linalg.norm(Bm, axis=0)
+
+
+def _fp32_floor(Kh, Bm, Xg):
+    nK = np.linalg.norm(Kh, 2)
+    return 64 * U32 * nK * np.linalg.norm(Xg, axis=0) / np.linalg.norm(Bm, axis=0)
+
+
+def test_preconditioned_cg_matches_the_oracle_and_cuts_iterations(api):
+    # The oracle's pinned case: n = 1500 points of the precision problem's
+    # kernel (d = 2, Gaussian l = 0.05, s = 0.01), rank 600.
+    prob = inputs.precision_problem(seed=25, n=1500)
+    Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 2, seed=35)]).astype(np.float32)
+    rtol = 1e-5
+    opts = api.solve_opts(cg_rtol=rtol, cg_maxit=5000, precond_rank=600)
+    Xs, it, rel, st = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts)
+    assert st == 0 and max(rel) <= rtol
+    opts0 = api.solve_opts(cg_rtol=rtol, cg_maxit=5000)
+    _, it0, _, st0 = api.gp_pcg_solve(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts0)
+    assert st0 == 0
+    assert max(it) * 5 < min(it0), (it, it0)
+    # The oracle's PCG with the GPU's own factor takes about as many steps.
+    _, Lg, _, rank = api.gp_nystrom_apply(_dev(prob.X), _dev(Bm[:, :1]), prob.kind, prob.theta, 600,
+                                          want_L=True)
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    Lg = Lg.cpu().numpy().astype(np.float64)
+    _, ito, _ = O.pcg(Kh, Bm.astype(np.float64),
+                      lambda V: O.nystrom_apply_inverse(Lg, prob.theta[0], V), rtol, 5000)
+    assert np.all(np.abs(np.asarray(it) - ito) <= 2), (it, ito)
+    Xg = Xs.cpu().numpy().astype(np.float64)
+    tr = _true_relres(Kh, Bm.astype(np.float64), Xg)
+    assert np.all(tr <= 2 * rtol + _fp32_floor(Kh, Bm, Xg)), tr
+
+
+def test_full_rank_preconditioner_solves_in_a_few_steps(api):
+    # k >= n: M = s I + L L^T reproduces Kh up to the factor's rounding.
+    prob = inputs.uniform_problem(300, 3, 1, (0.1, 1.0, 0.4), seed=36)
+    opts = api.solve_opts(cg_rtol=1e-6, cg_maxit=300, precond_rank=4096)
+    Xs, it, rel, st = api.gp_pcg_solve(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    assert st == 0 and it[0] <= 4, it
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    ref = sla.cho_solve(sla.cho_factor(Kh), prob.y.astype(np.float64))
+    assert np.linalg.norm(Xs.cpu().numpy()[:, 0] - ref) <= 1e-4 * np.linalg.norm(ref)
+
+
+def test_preconditioner_with_per_dimension_length_scales(api):
+    prob = inputs.uniform_problem(1200, 3, 0, (0.01, 1.0, 1.0), seed=37)
+    ls = [0.15, 0.3, 0.6]
+    rtol = 1e-5
+    opts = api.solve_opts(cg_rtol=rtol, cg_maxit=5000, precond_rank=300)
+    Xs, it, rel, st = api.gp_pcg_solve(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts, ls=ls)
+    assert st == 0
+    _, it0, _, _ = api.gp_pcg_solve(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta,
+                                    api.solve_opts(cg_rtol=rtol, cg_maxit=5000), ls=ls)
+    assert it[0] * 3 < it0[0], (it, it0)
+    Kh = O.khat_dense_ard(prob.X, prob.kind, prob.theta[0], prob.theta[1], np.asarray(ls))
+    Xg = Xs.cpu().numpy().astype(np.float64)
+    y = prob.y.astype(np.float64)[:, None]
+    assert _true_relres(Kh, y, Xg)[0] <= 2 * rtol + _fp32_floor(Kh, y, Xg)[0]
+
+
+@pytest.mark.parametrize("prec", [0, 4])
+def test_refinement_with_the_preconditioner_reaches_1e6(api, prec):
+    # kappa ~ 1e5: n = 3000 points of the precision problem's kernel.
+    prob = inputs.precision_problem(seed=38, n=3000)
+    Bm = np.column_stack([prob.y, inputs.gaussian_block(prob.n, 1, seed=39)]).astype(np.float32)
+    opts = api.solve_opts(cg_rtol=1e-3, cg_maxit=2000, prec=prec, refine_rtol=1e-7, refine_maxit=20,
+                          precond_rank=900)
+    X64, it, rel, st = api.gp_pcg_solve_refined(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts)
+    assert st == 0 and max(rel) <= 1e-7
+    Kh = O.khat_dense(prob.X, prob.kind, prob.theta)
+    tr = _true_relres(Kh, Bm.astype(np.float64), X64.cpu().numpy())
+    assert tr.max() <= 1e-6, tr
+    opts0 = api.solve_opts(cg_rtol=1e-3, cg_maxit=5000, prec=prec, refine_rtol=1e-7,
+                           refine_maxit=20)
+    _, it0, rel0, st0 = api.gp_pcg_solve_refined(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts0)
+    assert st0 == 0
+    assert max(it) * 5 < min(it0), (it, it0)

@@ -525,6 +525,24 @@ def test_pivoted_cholesky_greedy_rule_and_trace():
         assert piv[j] == int(np.argmax(dj))
 
 
+def test_pivoted_cholesky_on_given_pivots_interpolates_their_columns():
+    # Any pivot sequence: L L^T reproduces A on the pivot columns (the Nystrom
+    # interpolation property) and L restricted to the pivot rows is lower
+    # triangular; the greedy sequence given back reproduces the greedy factor.
+    prob = inputs.small_problem(seed=26, n=150)
+    A = prob.theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, prob.theta[2])
+    piv = np.random.default_rng(27).permutation(150)[:12]
+    L, got, _ = O.pivoted_cholesky(A, 12, pivots=piv)
+    assert got.tolist() == piv.tolist()
+    np.testing.assert_allclose((L @ L.T)[:, piv], A[:, piv], rtol=0, atol=1e-12)
+    assert np.allclose(np.triu(L[piv, :], 1), 0.0)
+    L0, p0, d0 = O.pivoted_cholesky(A, 12)
+    L1, p1, d1 = O.pivoted_cholesky(A, 12, pivots=p0)
+    assert p1.tolist() == p0.tolist()
+    np.testing.assert_array_equal(L1, L0)
+    np.testing.assert_array_equal(d1, d0)
+
+
 def test_pivoted_cholesky_stops_at_the_exact_rank():
     # Points in 3 identical clusters: f^2 K has rank 3 (Gaussian, distinct
     # cluster centres), so the greedy factor stops after 3 steps.
