@@ -332,8 +332,11 @@ def precision_config(api, B, torch, dev) -> dict:
 def refinement(api, torch, n: int = 20_000) -> dict:
     """Time to a true residual of 1e-6 on the precision problem's kernel at n = 2e4
     (d = 2, Gaussian f = 1, l = 0.05, s = 0.01; kappa ~ 3e4): plain FP32 CG against
-    mixed-precision iterative refinement (split-BF16 inner CG to 1e-2, FP64 outer
-    residual).  True residuals are the library's FP64 gp_true_residual."""
+    mixed-precision iterative refinement (split-BF16 or split-TF32 inner CG to 1e-2;
+    FP32 inner CG preconditioned by a rank-1000 Nystrom factor), each with the
+    compensated FP32-pair outer residual over all rows.  The FP32 solve's true
+    residual is the library's FP64 gp_true_residual; a refined solve's is its own
+    outer residual."""
     from paper_2503_02259_gb300 import inputs
     prob = inputs.precision_problem(seed=0, n=n)
     X = torch.from_numpy(prob.X).cuda()
@@ -360,30 +363,40 @@ def refinement(api, torch, n: int = 20_000) -> dict:
         torch.cuda.synchronize()
         out[f"refined_{name}"] = {"s": time.perf_counter() - t0, "inner_iterations": it[0],
                                   "true_relres": rr[0], "status": st}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, it, rr, st = api.gp_pcg_solve_refined(
+        X, y, prob.kind, prob.theta,
+        api.solve_opts(cg_rtol=1e-2, refine_rtol=1e-7, refine_maxit=40, precond_rank=1000),
+        raise_not_converged=False)
+    torch.cuda.synchronize()
+    out["refined_fp32_nystrom1000"] = {"s": time.perf_counter() - t0, "inner_iterations": it[0],
+                                       "true_relres": rr[0], "status": st}
     return out
 
 
-def precision_refinement(api, B, torch, cap_inner: int = 25, cap_outer: int = 2,
-                         nsample: int = 1000) -> dict:
-    """Refinement on the precision problem itself (n = 1e6, d = 2 uniform, Gaussian
-    f = 1, l = 0.05, s = 0.01; kappa ~ 1.6e6), with a stated iteration cap: FP32 CG
-    for cap_inner * cap_outer iterations against mixed-precision refinement
-    (split-BF16 inner CG capped at cap_inner iterations, cap_outer outer steps,
-    compensated FP32-pair outer residual).  Reported: wall time, the achieved
-    residual (the refinement's own pair residual over all n rows, and the FP64
-    residual on nsample sampled rows for both solvers), how far the pair residual
-    rows are from the FP64 ones, and the time of the two residual arithmetics."""
+def precision_refinement(api, B, torch, rank: int = 1500, cap_plain: int = 20,
+                         nsample: int = 1000, n: int = 1_000_000) -> dict:
+    """The precision problem itself (n = 1e6, d = 2 uniform, Gaussian f = 1,
+    l = 0.05, s = 0.01; kappa ~ 1.6e6) solved to the 1e-6 target:
+    mixed-precision iterative refinement (compensated FP32-pair outer residual
+    over all rows) whose inner solves are FP32 CG preconditioned by the rank-1500
+    Nystrom factor, for two inner tolerances; the preconditioned FP32 solve
+    without refinement; and, for contrast, unpreconditioned FP32 CG at a
+    cap_plain-iteration cap.  Residuals: the refinement's own pair residual over
+    all n rows, and the FP64 residual on nsample sampled rows (gp_residual_rows)
+    for every solver; then how far the pair residual rows are from the FP64 ones
+    and the time of both arithmetics."""
     from paper_2503_02259_gb300 import inputs
-    prob = inputs.precision_problem(seed=0)
-    n = prob.n
+    prob = inputs.precision_problem(seed=0, n=n)
     X = torch.from_numpy(prob.X).cuda()
     y = torch.from_numpy(prob.y).cuda()
     rows = np.sort(np.random.default_rng(5).choice(n, nsample, replace=False)).astype(np.int64)
     rows_d = torch.from_numpy(rows).cuda()
     ws = api.workspace(B.OP_RESIDUAL, api.problem(X, prob.kind, prob.theta)[0], 1, None, X.device)
     out = {"workload": f"n={n} d=2 uniform[0,1]^2, Gaussian f=1 l=0.05 s=0.01, B = y (w = 1); "
-                       f"iteration cap {cap_inner * cap_outer} CG iterations per solver; residuals "
-                       f"on {nsample} sampled rows in FP64 (gp_residual_rows)",
+                       f"Nystrom preconditioner of rank {rank}; residuals on {nsample} sampled rows "
+                       "in FP64 (gp_residual_rows)",
            "target_true_relres": 1e-6}
 
     def timed(fn):
@@ -393,35 +406,56 @@ def precision_refinement(api, B, torch, cap_inner: int = 25, cap_outer: int = 2,
         torch.cuda.synchronize()
         return r, time.perf_counter() - t0
 
-    (x32, it32, rr32, _), t32 = timed(lambda: api.gp_pcg_solve(
-        X, y, prob.kind, prob.theta, api.solve_opts(cg_rtol=1e-12, cg_maxit=cap_inner * cap_outer),
+    def fp64_rows(x64):
+        return api.gp_residual_rows(X, y, x64, prob.kind, prob.theta, rows=rows_d,
+                                    arith=B.RESIDUAL_FP64, ws=ws, want_rows=False)[1][0]
+
+    (_, _, piv, rk), tf = timed(lambda: api.gp_nystrom_apply(X, y, prob.kind, prob.theta, rank))
+    out["nystrom_factor"] = {"s_factor_and_one_apply": tf, "rank": rk}
+    best = None
+    for rtol_in in (1e-2, 1e-5):
+        opts = api.solve_opts(cg_rtol=rtol_in, cg_maxit=200, refine_rtol=1e-6, refine_maxit=10,
+                              precond_rank=rank)
+        (x64, it, rr, st), t = timed(lambda: api.gp_pcg_solve_refined(
+            X, y, prob.kind, prob.theta, opts, raise_not_converged=False))
+        rec = {"s": t, "inner_iterations": it[0], "status": st, "relres_pair_all_rows": rr[0],
+               "relres_fp64_sampled_rows": fp64_rows(x64)}
+        out[f"refined_fp32_nystrom_inner{rtol_in:g}"] = rec
+        if st == 0 and (best is None or t < best[1]["s"]):
+            best = (x64, rec)
+    (x32, it32, rr32, st32), t32 = timed(lambda: api.gp_pcg_solve(
+        X, y, prob.kind, prob.theta, api.solve_opts(cg_rtol=1e-6, cg_maxit=200, precond_rank=rank),
         raise_not_converged=False))
-    _, rel32 = api.gp_residual_rows(X, y, x32.double(), prob.kind, prob.theta, rows=rows_d,
-                                    arith=B.RESIDUAL_FP64, ws=ws, want_rows=False)
-    out["fp32_cg"] = {"s": t32, "iterations": it32[0], "recurrence_relres": rr32[0],
-                      "relres_fp64_sampled_rows": rel32[0]}
-    (x64, itr, rrr, st), tr = timed(lambda: api.gp_pcg_solve_refined(
-        X, y, prob.kind, prob.theta,
-        api.solve_opts(cg_rtol=1e-12, cg_maxit=cap_inner, prec=B.PREC_BF16X3, refine_rtol=1e-6,
-                       refine_maxit=cap_outer), raise_not_converged=False))
-    (Rf, relf), tf = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
-                                                        rows=rows_d, arith=B.RESIDUAL_FP64, ws=ws))
-    (Rp, relp), tp = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
-                                                        rows=rows_d, arith=B.RESIDUAL_PAIR, ws=ws))
-    (_, relall), tall = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
-                                                           arith=B.RESIDUAL_PAIR, ws=ws,
-                                                           want_rows=False))
-    bn = float(torch.linalg.vector_norm(y[rows_d].double()))
-    out["refined_bf16x3"] = {
-        "s": tr, "inner_iterations": itr[0], "outer_steps_cap": cap_outer, "status": st,
-        "relres_pair_all_rows": rrr[0], "relres_fp64_sampled_rows": relf[0],
-        "relres_pair_sampled_rows": relp[0]}
-    out["residual_arithmetics"] = {
-        "pair_minus_fp64_rows_over_norm_B_rows": float(torch.linalg.vector_norm(Rp - Rf)) / bn,
-        "s_fp64_sampled_rows": tf, "s_pair_sampled_rows": tp, "fp64_over_pair_time": tf / tp,
-        "s_pair_all_rows": tall, "relres_pair_all_rows_recomputed": relall[0],
-        "pair_entries_per_s": float(n) * n / tall}
-    out["target_met"] = bool(relf[0] <= 1e-6)
+    out["fp32_pcg_nystrom"] = {"s": t32, "iterations": it32[0], "recurrence_relres": rr32[0],
+                               "status": st32, "relres_fp64_sampled_rows": fp64_rows(x32.double())}
+    (xc, itc, rrc, _), tc = timed(lambda: api.gp_pcg_solve(
+        X, y, prob.kind, prob.theta, api.solve_opts(cg_rtol=1e-12, cg_maxit=cap_plain),
+        raise_not_converged=False))
+    out["fp32_cg_unpreconditioned"] = {"s": tc, "iterations": itc[0], "recurrence_relres": rrc[0],
+                                       "relres_fp64_sampled_rows": fp64_rows(xc.double())}
+    if best is not None:
+        x64 = best[0]
+        (Rf, relf), tfr = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
+                                                             rows=rows_d, arith=B.RESIDUAL_FP64,
+                                                             ws=ws))
+        (Rp, relp), tp = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
+                                                            rows=rows_d, arith=B.RESIDUAL_PAIR,
+                                                            ws=ws))
+        (_, relall), tall = timed(lambda: api.gp_residual_rows(X, y, x64, prob.kind, prob.theta,
+                                                               arith=B.RESIDUAL_PAIR, ws=ws,
+                                                               want_rows=False))
+        bn = float(torch.linalg.vector_norm(y[rows_d].double()))
+        out["residual_arithmetics"] = {
+            "pair_minus_fp64_rows_over_norm_B_rows": float(torch.linalg.vector_norm(Rp - Rf)) / bn,
+            "s_fp64_sampled_rows": tfr, "s_pair_sampled_rows": tp, "fp64_over_pair_time": tfr / tp,
+            "s_pair_all_rows": tall, "relres_pair_all_rows_recomputed": relall[0],
+            "relres_pair_sampled_rows": relp[0], "relres_fp64_sampled_rows": relf[0],
+            "pair_entries_per_s": float(n) * n / tall}
+        out["best_s_to_target"] = best[1]["s"]
+        out["target_met"] = bool(best[1]["relres_fp64_sampled_rows"] <= 1e-6
+                                 and best[1]["relres_pair_all_rows"] <= 1e-6)
+    else:
+        out["target_met"] = False
     return out
 
 
@@ -660,7 +694,7 @@ def run_leg(args) -> int:
     elif args.leg == "refinement":
         out = refinement(api, torch)
     elif args.leg == "precision_refinement":
-        out = precision_refinement(api, B, torch)
+        out = precision_refinement(api, B, torch, n=args.precision_n)
     elif args.leg == "loss_grad_mixed_vs_fp32":
         out = loss_grad_mixed_vs_fp32(api, torch, rates)
     elif args.leg == "serving_accuracy":
@@ -685,6 +719,9 @@ def main() -> int:
                     help="requests replayed by the serving leg (the full stream is 512)")
     ap.add_argument("--serving-all-arms", action="store_true",
                     help="also replay the stream with batched FP32 requests and in split TF32")
+    ap.add_argument("--precision-n", type=int, default=1_000_000,
+                    help="points of the precision_refinement leg when run alone (smaller n for "
+                         "profiling; the full run always uses 1e6)")
     ap.add_argument("--leg", default=None,
                     choices=["loss_grad", "precision_modes", "precision_config", "refinement",
                              "precision_refinement",

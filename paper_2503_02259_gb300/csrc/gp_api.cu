@@ -1120,9 +1120,13 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   std::vector<int> total_iters(w, 0);
   HostCg hr;
   for (int outer = 0;; ++outer) {
-    if ((s = residual_into(prob, Bp, ss.pc.w_pad, x64, ss.pc.w_pad, w, nullptr, n, arith, part, rerr,
-                           r64, ss.pc.w_pad, nullptr, st)) != GP_OK)
+    if (outer == 0) {
+      // x = 0: the residual is B itself (no O(n^2) pass).
+      GP_CUDA(launch_widen(Bp, r64, static_cast<int64_t>(plane), st));
+    } else if ((s = residual_into(prob, Bp, ss.pc.w_pad, x64, ss.pc.w_pad, w, nullptr, n, arith, part,
+                                  rerr, r64, ss.pc.w_pad, nullptr, st)) != GP_OK) {
       return s;
+    }
     GP_CUDA(launch_refine_norms(ss.W.S2, r64, Bp, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, w, ss.W.red, st));
     if ((s = read_cg(ss.W.S2, hr, st)) != GP_OK) return s;
     bool done = true;

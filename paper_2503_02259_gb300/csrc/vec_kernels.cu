@@ -987,6 +987,12 @@ __global__ void copy_col0_kernel(const float* X, float* V, int64_t n_pad, int w_
 // ------------------------------------------------------------ refinement --
 // Norms of the outer residual of iterative refinement, the FP64 solution update
 // and its FP32 copy.  (The residual itself is in residual.cuh.)
+__global__ void widen_kernel(const float* a, double* b, int64_t total) {
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x)
+    b[e] = static_cast<double>(a[e]);
+}
+
 __global__ void refine_norms_kernel(CgState* S, const double* r64, const float* B, float* rf,
                                     int64_t n_pad, int w_pad, int w, double* red) {
   const RedLayout L = red_layout(w_pad);
@@ -1306,6 +1312,12 @@ cudaError_t launch_yalpha(CgState* S, const float* B, const float* X, int64_t n_
 
 cudaError_t launch_assemble(CgState* S, int64_t n, int p, cudaStream_t st) {
   assemble_kernel<<<1, 32, 0, st>>>(S, n, p);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_widen(const float* a, double* b, int64_t total, cudaStream_t st) {
+  widen_kernel<<<elt_blocks(total), kEltThreads, 0, st>>>(a, b, total);
   count_launch();
   return cudaGetLastError();
 }

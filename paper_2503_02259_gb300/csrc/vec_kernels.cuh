@@ -163,6 +163,8 @@ cudaError_t launch_pred_var(CgState* S, const float* B, const float* U, int64_t 
 // S->rr[c] = ||r64_c||^2, S->bn2[c] = ||B_c||^2, S->relres[c] = sqrt(rr/bn2); rf = r64 as FP32.
 cudaError_t launch_refine_norms(CgState* S, const double* r64, const float* B, float* rf,
                                 int64_t n_pad, int w_pad, int w, double* red, cudaStream_t st);
+// b = a widened to FP64 (total elements).
+cudaError_t launch_widen(const float* a, double* b, int64_t total, cudaStream_t st);
 // x64 += X (FP32 correction) for columns c < w.
 cudaError_t launch_refine_update(double* x64, const float* X, int64_t n_pad, int w_pad, int w,
                                  cudaStream_t st);
