@@ -22,6 +22,7 @@ namespace {
 constexpr int kStepThreads = 256;
 constexpr int kStepRows = 4;                      // rows per thread (one float4 per column of L)
 constexpr int kStepRowsPerBlock = kStepThreads * kStepRows;
+constexpr int kStepBatch = 8;                     // columns of L loaded ahead per thread
 constexpr int kGT = 64;                           // Gram tile (columns of L)
 constexpr int kGK = 32;                           // Gram rows per shared-memory slab
 constexpr int kLtvChunk = 4096;                   // rows per block of L^T V
@@ -161,7 +162,25 @@ __global__ void __launch_bounds__(kStepThreads)
   if (i0 < a.n_pad) {
     pa::fpair acc[kStepRows] = {};
     const float* col = a.Lt + i0;
-    for (int m = 0; m < j; ++m) {
+    // Batches of kStepBatch columns: all loads of a batch are issued before
+    // the first is used, so that enough bytes are in flight to stream L at
+    // the memory's rate when few blocks share an SM.
+    int m = 0;
+    for (; m + kStepBatch <= j; m += kStepBatch) {
+      float4 l[kStepBatch];
+#pragma unroll
+      for (int u = 0; u < kStepBatch; ++u)
+        l[u] = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m + u) * a.n_pad);
+#pragma unroll
+      for (int u = 0; u < kStepBatch; ++u) {
+        const float b = sp[m + u];
+        acc_prod(acc[0], l[u].x, b);
+        acc_prod(acc[1], l[u].y, b);
+        acc_prod(acc[2], l[u].z, b);
+        acc_prod(acc[3], l[u].w, b);
+      }
+    }
+    for (; m < j; ++m) {
       const float4 l = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m) * a.n_pad);
       const float b = sp[m];
       acc_prod(acc[0], l.x, b);
@@ -493,7 +512,18 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (i < n) {
       const float* col = Lt + static_cast<int64_t>(mt) * n_pad + i;
-      for (int mm = 0; mm < mcount; ++mm) {
+      int mm = 0;
+      for (; mm + kStepBatch <= mcount; mm += kStepBatch) {
+        float l[kStepBatch];
+#pragma unroll
+        for (int u = 0; u < kStepBatch; ++u) l[u] = col[static_cast<int64_t>(mm + u) * n_pad];
+#pragma unroll
+        for (int u = 0; u < kStepBatch; ++u)
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc)
+            acc_prod_pair(acc[cc], l[u], sT[mm + u][2 * cc], sT[mm + u][2 * cc + 1]);
+      }
+      for (; mm < mcount; ++mm) {
         const float l = col[static_cast<int64_t>(mm) * n_pad];
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) acc_prod_pair(acc[cc], l, sT[mm][2 * cc], sT[mm][2 * cc + 1]);
