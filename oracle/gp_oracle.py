@@ -21,6 +21,10 @@ Paper passages followed (HiGP, arXiv 2503.02259):
   * Eq. (1) / Eq. (2) with M = I: log|M| = 0 and tr(M^-1 dM) = 0; the
     remainders are estimated by stochastic Lanczos quadrature (Ubaru et al.
     2017) and the Hutchinson estimator.
+  * Eq. (1) / Eq. (2) with a Nystrom preconditioner M = s I + B W^-1 B^T on a
+    fixed pivot set (``nystrom_precond``, ``est_nll_precond``): log|M| and
+    tr(M^-1 dM/dtheta) exactly, the remainders by SLQ on M^-1/2 Kh M^-1/2 and
+    by the Hutchinson estimator, with probes z ~ N(0, M).
   * §Statement of Need: the on-the-fly MatVec evaluates kernel blocks and
     uses them immediately; semantically it is the dense product Kh @ V.
 
@@ -32,7 +36,11 @@ regularised matrix are not printed in the paper):
   * Matern-3/2 kernel      k(r) = (1 + sqrt(3) r / l) exp(-sqrt(3) r / l).
   * l is one isotropic length-scale; gradients are w.r.t. raw (s, f, l).
   * Probes are Rademacher +-1, unnormalised (||z||^2 = n), drawn by the
-    counter-based rule in ``rademacher_probes``.
+    counter-based rule in ``rademacher_probes``; the preconditioned estimator
+    takes standard normal e1, e2 (``gaussian_probes``: the same hash, then the
+    Box-Muller transform) and forms z = L e1 + sqrt(s) e2 ~ N(0, M).
+  * The preconditioner's derivatives are taken with its pivot set held fixed
+    (the greedy pivot choice is piecewise constant in Theta).
 
 Parity status per function (pins live in tests/test_oracle_pins.py):
   every public function below is pinned against a closed form, a brute-force
@@ -94,6 +102,25 @@ def rademacher_probes(n: int, p: int, seed: int) -> np.ndarray:
             z = z ^ (z >> np.uint64(31))
             Z[:, c] = np.where((z >> np.uint64(63)) == 0, 1.0, -1.0)
     return Z
+
+
+def gaussian_probes(rows: int, p: int, seed: int) -> np.ndarray:
+    """Standard normal values G (rows x p) from the same counter-based hash:
+    for row i and column c, h1 = probe_hash(seed ^ 2^39, c, 2i) and
+    h2 = probe_hash(seed ^ 2^39, c, 2i + 1) (bit 39 of the key keeps these keys
+    apart from the Rademacher ones); u1 = (h1 // 2^11 + 1) 2^-53 in (0, 1],
+    u2 = (h2 // 2^11) 2^-53 in [0, 1); G_ic = sqrt(-2 ln u1) cos(2 pi u2)
+    (the Box-Muller transform, Box & Muller 1958)."""
+    G = np.empty((rows, p))
+    tag = (seed ^ (1 << 39)) & _M64
+    for c in range(p):
+        for i in range(rows):
+            h1 = probe_hash(tag, c, 2 * i)
+            h2 = probe_hash(tag, c, 2 * i + 1)
+            u1 = ((h1 >> 11) + 1) * 2.0 ** -53
+            u2 = (h2 >> 11) * 2.0 ** -53
+            G[i, c] = math.sqrt(-2.0 * math.log(u1)) * math.cos(2.0 * math.pi * u2)
+    return G
 
 
 # ---------------------------------------------------------------------------
@@ -582,3 +609,78 @@ def pcg(A: np.ndarray, B: np.ndarray, apply_minv, rtol: float, maxit: int):
         iters[c] = it
         relres[c] = np.linalg.norm(r) / bn if bn > 0 else 0.0
     return Xs, iters, relres
+
+
+# ---------------------------------------------------------------------------
+# Eq. (1) / Eq. (2) with a Nystrom preconditioner on a fixed pivot set.
+# ---------------------------------------------------------------------------
+
+def nystrom_precond(X, kind: int, theta, piv):
+    """M = s I + B W^-1 B^T, the Nystrom preconditioner on the pivot set P:
+    A = f^2 K, B = A[:, P], W = A[P, P].  With P held fixed its derivatives are
+      dM/ds = I,   dM/df = (2/f) B W^-1 B^T,
+      dM/dl = B' W^-1 B^T + B W^-1 B'^T - B W^-1 W' W^-1 B^T,
+    with B' = dB/dl and W' = dW/dl (f^2 times the dk/dl entries).
+    Returns (M, [dM/ds, dM/df, dM/dl])."""
+    s, f, l = theta
+    X = np.asarray(X, dtype=np.float64)
+    P = np.asarray(piv, dtype=int)
+    n = X.shape[0]
+    R2 = sqdist(X, X[P])
+    B = f * f * kernel_value(R2, kind, l)
+    Bd = f * f * kernel_dl(R2, kind, l)
+    W = B[P, :]
+    Wd = Bd[P, :]
+    G = np.linalg.solve(W, B.T)          # W^-1 B^T
+    N = B @ G
+    N = 0.5 * (N + N.T)
+    T = Bd @ G
+    dl = T + T.T - G.T @ Wd @ G
+    return s * np.eye(n) + N, [np.eye(n), (2.0 / f) * N, 0.5 * (dl + dl.T)]
+
+
+def _inv_sqrt_spd(M: np.ndarray) -> np.ndarray:
+    lam, U = np.linalg.eigh(M)
+    return (U / np.sqrt(lam)) @ U.T
+
+
+def est_nll_precond(X, y, kind: int, theta, piv, E1: np.ndarray, E2: np.ndarray, k: int) -> dict:
+    """The preconditioned estimator: Eq. (1) and Eq. (2) with the Nystrom M on
+    the pivots piv, exact solves, and probes z_i = L e1_i + sqrt(s) e2_i
+    (L the partial Cholesky factor on piv, so L L^T = B W^-1 B^T and z_i ~ N(0, M)
+    for standard normal e1 (r x p) and e2 (n x p)):
+      log|Kh| ~ log|M| + mean_i ||zh_i||^2 e1^T log(T_i) e1,
+        zh_i = M^-1/2 z_i, T_i from k Lanczos steps on M^-1/2 Kh M^-1/2 from zh_i;
+      tr(Kh^-1 dKh) ~ tr(M^-1 dM) + mean_i [(Kh^-1 z_i)^T dKh (M^-1 z_i)
+                                             - (M^-1 z_i)^T dM (M^-1 z_i)],
+    the second an unbiased estimate of tr(Kh^-1 dKh - M^-1 dM) because
+    E[z z^T] = M.  Loss and gradient then as in est_nll."""
+    s, f, l = theta
+    y = np.asarray(y, dtype=np.float64)
+    n = y.size
+    Kh = khat_dense(X, kind, theta)
+    dKs = dkhat_dense(X, kind, theta)
+    A = f * f * kernel_value(sqdist(X, X), kind, l)
+    L, _, _ = pivoted_cholesky(A, len(piv), pivots=piv)
+    Z = L @ np.asarray(E1, dtype=np.float64) + math.sqrt(s) * np.asarray(E2, dtype=np.float64)
+    M, dMs = nystrom_precond(X, kind, theta, piv)
+    logdet_M = float(np.linalg.slogdet(M)[1])
+    trM = np.array([np.trace(np.linalg.solve(M, dM)) for dM in dMs])
+    Mis = _inv_sqrt_spd(M)
+    Ah = Mis @ Kh @ Mis
+    Zh = Mis @ Z
+    ld_vals = np.array([gauss_quadrature_log(*lanczos(Ah, Zh[:, i], k), Zh[:, i] @ Zh[:, i])
+                        for i in range(Z.shape[1])])
+    C = sla.cho_factor(Kh, lower=True)
+    alpha = sla.cho_solve(C, y)
+    U = sla.cho_solve(C, Z)
+    V = np.linalg.solve(M, Z)
+    corr = np.array([np.sum(U * (dK @ V), axis=0) - np.sum(V * (dM @ V), axis=0)
+                     for dK, dM in zip(dKs, dMs)])
+    tr = trM + corr.mean(axis=1)
+    quad = np.array([alpha @ (dK @ alpha) for dK in dKs])
+    logdet = logdet_M + float(ld_vals.mean())
+    loss = 0.5 * (y @ alpha + logdet + n * math.log(2.0 * math.pi))
+    return {"loss": loss, "grad": 0.5 * (-quad + tr), "logdet": logdet, "logdet_M": logdet_M,
+            "logdet_probes": ld_vals, "trace": tr, "trace_M": trM, "trace_corr": corr,
+            "quad": quad, "yalpha": float(y @ alpha), "Z": Z, "L": L}

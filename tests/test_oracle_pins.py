@@ -685,3 +685,124 @@ def test_planted_wrong_woodbury_sign_is_caught(monkeypatch):
     monkeypatch.setattr(O, "nystrom_apply_inverse", wrong)
     with pytest.raises(AssertionError):
         test_nystrom_woodbury_inverse_matches_dense_solve()
+
+
+# ------------------------------------- Eq. 1 / Eq. 2 with a Nystrom M --
+
+def _precond_case(n=60, seed=41, kind=1, theta=(0.05, 1.2, 0.3)):
+    prob = inputs.uniform_problem(n, 3, kind, theta, seed=seed)
+    return prob, prob.theta
+
+
+def test_nystrom_precond_derivatives_match_central_differences():
+    prob, theta = _precond_case()
+    A = theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, theta[2])
+    _, piv, _ = O.pivoted_cholesky(A, 8)
+    M, dMs = O.nystrom_precond(prob.X, prob.kind, theta, piv)
+    for t in range(3):
+        h = 1e-5 * theta[t]
+        tp = list(theta); tp[t] += h
+        tm = list(theta); tm[t] -= h
+        Mp, _ = O.nystrom_precond(prob.X, prob.kind, tp, piv)
+        Mm, _ = O.nystrom_precond(prob.X, prob.kind, tm, piv)
+        fd = (Mp - Mm) / (2 * h)
+        np.testing.assert_allclose(dMs[t], fd, rtol=0, atol=1e-6 * np.abs(fd).max() + 1e-12)
+
+
+def test_nystrom_precond_logdet_by_the_determinant_identity():
+    # |s I_n + L L^T| = s^(n-r) |s I_r + L^T L| (Sylvester), with L the partial
+    # Cholesky factor on the same pivots (L L^T = B W^-1 B^T).
+    prob, theta = _precond_case()
+    s = theta[0]
+    A = theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, theta[2])
+    L, piv, _ = O.pivoted_cholesky(A, 10)
+    M, _ = O.nystrom_precond(prob.X, prob.kind, theta, piv)
+    n, r = L.shape
+    ref = (n - r) * math.log(s) + np.linalg.slogdet(s * np.eye(r) + L.T @ L)[1]
+    assert abs(np.linalg.slogdet(M)[1] - ref) <= 1e-9 * abs(ref)
+    np.testing.assert_allclose(M, s * np.eye(n) + L @ L.T, atol=1e-12)
+
+
+def test_precond_estimator_is_exact_when_m_is_kh():
+    # Every point a pivot: M = Kh, so log|M| = log|Kh|, M^-1/2 Kh M^-1/2 = I
+    # (its SLQ term is log 1 = 0 for any probe) and each Hutchinson term is
+    # zero: the estimator is the exact loss and gradient whatever the probes.
+    prob, theta = _precond_case(n=50)
+    A = theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, theta[2])
+    _, piv, _ = O.pivoted_cholesky(A, 50)
+    rng = np.random.default_rng(42)
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, theta, piv, rng.standard_normal((50, 3)),
+                            rng.standard_normal((50, 3)), 4)
+    ex = O.exact_nll(prob.X, prob.y, prob.kind, theta)
+    assert abs(est["loss"] - ex["loss"]) <= 1e-8 * abs(ex["loss"])
+    np.testing.assert_allclose(est["grad"], ex["grad"], rtol=1e-7, atol=1e-9)
+    assert np.abs(est["logdet_probes"]).max() <= 1e-9
+    assert np.abs(est["trace_corr"]).max() <= 1e-7
+
+
+def test_precond_slq_term_is_exact_at_full_krylov_dimension():
+    prob, theta = _precond_case(n=40)
+    A = theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, theta[2])
+    _, piv, _ = O.pivoted_cholesky(A, 6)
+    rng = np.random.default_rng(43)
+    E1, E2 = rng.standard_normal((6, 2)), rng.standard_normal((40, 2))
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, theta, piv, E1, E2, 40)
+    M, _ = O.nystrom_precond(prob.X, prob.kind, theta, piv)
+    lam, U = np.linalg.eigh(M)
+    Mis = (U / np.sqrt(lam)) @ U.T
+    Ah = Mis @ O.khat_dense(prob.X, prob.kind, theta) @ Mis
+    la, Ua = np.linalg.eigh(Ah)
+    logA = (Ua * np.log(la)) @ Ua.T
+    Zh = Mis @ est["Z"]
+    ref = np.array([Zh[:, i] @ logA @ Zh[:, i] for i in range(2)])
+    np.testing.assert_allclose(est["logdet_probes"], ref, rtol=1e-8)
+
+
+def test_precond_trace_estimator_is_unbiased_with_lower_variance():
+    # z ~ N(0, M): the mean of the Eq. 2 terms converges to tr(Kh^-1 dKh).  When
+    # the factor covers the eigenvalues of f^2 K above s (16 here; rank 25), the
+    # split off tr(M^-1 dM) leaves a far smaller variance than Gaussian probes
+    # with M = I (z ~ N(0, I), tr ~ (Kh^-1 z)^T dKh z).
+    prob = inputs.uniform_problem(120, 2, O.GAUSSIAN, (0.02, 1.0, 0.4), seed=41)
+    theta = prob.theta
+    A = theta[1] ** 2 * O.kernel_value(O.sqdist(prob.X, prob.X), prob.kind, theta[2])
+    _, piv, _ = O.pivoted_cholesky(A, 25)
+    rng = np.random.default_rng(44)
+    p = 1500
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, theta, piv, rng.standard_normal((25, p)),
+                            rng.standard_normal((120, p)), 3)
+    Kh = O.khat_dense(prob.X, prob.kind, theta)
+    dKs = O.dkhat_dense(prob.X, prob.kind, theta)
+    exact_tr = np.array([np.trace(np.linalg.solve(Kh, dK)) for dK in dKs])
+    vals = est["trace_M"][:, None] + est["trace_corr"]
+    se = vals.std(axis=1, ddof=1) / math.sqrt(p)
+    assert np.all(np.abs(vals.mean(axis=1) - exact_tr) <= 4 * se + 1e-12)
+    G = rng.standard_normal((120, p))
+    plain = np.array([np.sum(np.linalg.solve(Kh, G) * (dK @ G), axis=0) for dK in dKs])
+    assert np.all(vals.std(axis=1) < 0.2 * plain.std(axis=1))
+
+
+def test_gaussian_probes_are_standard_normal():
+    G = O.gaussian_probes(4000, 2, seed=7)
+    assert abs(G.mean()) <= 4 / math.sqrt(G.size)
+    assert abs(G.var() - 1.0) <= 4 * math.sqrt(2.0 / G.size)
+    from scipy import stats
+    assert stats.kstest(G.ravel(), "norm").pvalue > 1e-3
+    # Columns and seeds give different streams; rows are not shifted copies.
+    assert not np.allclose(G[:, 0], G[:, 1])
+    assert not np.allclose(O.gaussian_probes(50, 1, 8)[:, 0], G[:50, 0])
+    assert not np.allclose(G[1:51, 0], G[:50, 0])
+
+
+def test_planted_mistakes_in_the_preconditioned_estimator_are_caught(monkeypatch):
+    good = O.gp_oracle.nystrom_precond
+
+    def wrong_sign(X, kind, theta, piv):
+        M, d = good(X, kind, theta, piv)
+        return M, [d[0], d[1], -d[2]]
+    monkeypatch.setattr(O.gp_oracle, "nystrom_precond", wrong_sign)
+    monkeypatch.setattr(O, "nystrom_precond", wrong_sign)
+    with pytest.raises(AssertionError):
+        test_nystrom_precond_derivatives_match_central_differences()
+    with pytest.raises(AssertionError):
+        test_precond_estimator_is_exact_when_m_is_kh()
