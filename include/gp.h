@@ -155,9 +155,10 @@ typedef struct {
  *  precond_rank: 0 = no preconditioner (M = I); k in [1, GP_MAX_PRECOND_RANK]
  *              = the Nystrom preconditioner M = s I + L L^T with L the
  *              rank-k pivoted partial Cholesky factor of f^2 K (see
- *              gp_nystrom_apply), used by gp_pcg_solve and
- *              gp_pcg_solve_refined (in the refinement's inner solves); the
- *              other calls reject it (GP_ERR_UNIMPLEMENTED).
+ *              gp_nystrom_apply), used by gp_pcg_solve,
+ *              gp_pcg_solve_refined (in the refinement's inner solves) and
+ *              gp_loss_and_grad (Eq. 1 / Eq. 2 with this M); the other calls
+ *              reject it (GP_ERR_UNIMPLEMENTED).
  *  precond_tol: the factor stops before k columns once the largest residual
  *              diagonal is <= precond_tol * f^2 (<= 0: only when it is <= 0). */
 typedef struct {
@@ -200,6 +201,8 @@ typedef struct {
   int32_t refine_steps;    /* outer refinement steps taken (0 for FP32) */
   double relres_y;         /* final recurrence relres of the y column */
   double relres_max;       /* largest final relres over all columns */
+  double logdet_m;         /* log|M| of the preconditioner (0 for M = I; included in logdet) */
+  double trace_m[3];       /* tr(M^-1 dM/dtheta) (0 for M = I; included in trace) */
 } gp_loss_info;
 
 /* Library version string (static storage). */
@@ -360,7 +363,23 @@ gp_status gp_slq_logdet(const gp_problem* prob, const gp_solve_opts* opts, doubl
  * their d derivatives with alpha alpha^T and U Z^T / p (no derivative
  * product is formed); 1 + nprobe <= 48 then, info->quad/trace hold s and f
  * in [0..1] and NaN in [2], and no trace standard errors are formed.
- * Synchronises `stream`. */
+ * With opts->precond_rank > 0 (isotropic l only) the terms of Eq. 1 and
+ * Eq. 2 are taken with the Nystrom preconditioner M = s I + L L^T, its pivots
+ * held fixed for the derivatives:
+ *   log|Kh| = log|M| + log|M^-1/2 Kh M^-1/2|, log|M| = (n - r) log s + log|C|
+ *   (C = s I + L^T L), the second term by SLQ on M^-1/2 Kh M^-1/2 (Lanczos in
+ *   the M-inner product, weight z^T M^-1 z);
+ *   tr(Kh^-1 dKh) = tr(M^-1 dM) + tr(Kh^-1 dKh - M^-1 dM): the first in closed
+ *   form ((n - r)/s + tr(C^-1), (2/f)(r - s tr(C^-1)), 2 tr(C^-1 L^T dL/dl),
+ *   with dL/dl the forward derivative of the factor's column steps), the
+ *   second by the Hutchinson terms (Kh^-1 z)^T dKh (M^-1 z) - (M^-1 z)^T dM (M^-1 z);
+ * with probes z = L e1 + sqrt(s) e2 ~ N(0, M) for standard normal e1, e2:
+ * opts->probes, if given, is then a device (n + precond_rank) x nprobe
+ * float32 row-major block holding e2 in rows [0, n) and e1 in the rows after
+ * (only the first r of those are used), else e is generated from opts->seed
+ * (Box-Muller on the probe hash with bit 39 of the key set).  The CG solves
+ * run preconditioned.  info->logdet_m and info->trace_m give the closed-form
+ * terms.  Synchronises `stream`. */
 gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solve_opts* opts,
                            double* loss, double* grad, gp_loss_info* info, void* ws,
                            size_t ws_bytes, void* stream);

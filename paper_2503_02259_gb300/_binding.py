@@ -75,14 +75,15 @@ class gp_loss_info(ctypes.Structure):
     _fields_ = [("yalpha", c_double), ("logdet", c_double), ("logdet_stderr", c_double),
                 ("quad", c_double * 3), ("trace", c_double * 3), ("trace_stderr", c_double * 3),
                 ("cg_iters", c_int32), ("refine_steps", c_int32), ("relres_y", c_double),
-                ("relres_max", c_double)]
+                ("relres_max", c_double), ("logdet_m", c_double), ("trace_m", c_double * 3)]
 
     def as_dict(self) -> dict:
         return {"yalpha": self.yalpha, "logdet": self.logdet, "logdet_stderr": self.logdet_stderr,
                 "quad": list(self.quad), "trace": list(self.trace),
                 "trace_stderr": list(self.trace_stderr), "cg_iters": self.cg_iters,
                 "refine_steps": self.refine_steps, "relres_y": self.relres_y,
-                "relres_max": self.relres_max}
+                "relres_max": self.relres_max, "logdet_m": self.logdet_m,
+                "trace_m": list(self.trace_m)}
 
 
 class gp_request(ctypes.Structure):

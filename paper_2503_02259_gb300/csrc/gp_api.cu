@@ -568,24 +568,37 @@ namespace gp {
 
 struct Precond {
   NysWs ws;
-  float* Z = nullptr;   // [n_pad][w_pad]
+  float* Z = nullptr;   // [n_pad][w_pad]: z = M^-1 r in PCG; M^-1 of the probe block in the loss
+  float* U = nullptr;   // [n_pad][w_pad]: preconditioned Lanczos work vector (loss only)
+  float* Lp = nullptr;  // lz_k planes [n_pad][w_pad]: M-images of the Lanczos basis (loss only)
   int rank = 0;
   double s = 0.0;
 };
 
 static size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-static size_t precond_bytes(int64_t n_pad, int d, int kmax, int w_pad) {
-  return align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad) +
-         nys_bytes(n_pad, d, kmax, w_pad) + 256;
+// The preconditioner's planes, then its factor workspace.  lz_k > 0 adds the
+// Lanczos work plane and lz_k M-image planes; deriv adds dL/dl (the loss).
+static size_t precond_bytes(int64_t n_pad, int d, int kmax, int w_pad, int lz_k = 0,
+                            bool deriv = false) {
+  const size_t plane = align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad);
+  const size_t planes = 1 + (lz_k > 0 ? 1 + static_cast<size_t>(lz_k) : 0);
+  return planes * plane + nys_bytes(n_pad, d, kmax, w_pad, deriv) + 256;
 }
 
-static Precond carve_precond(void* base, int64_t n_pad, int d, int kmax, int w_pad) {
+static Precond carve_precond(void* base, int64_t n_pad, int d, int kmax, int w_pad, int lz_k = 0,
+                             bool deriv = false) {
   Precond pc;
   char* b = static_cast<char*>(base);
+  const size_t plane = align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad);
   pc.Z = reinterpret_cast<float*>(b);
-  pc.ws = carve_nys(b + align256(sizeof(float) * static_cast<size_t>(n_pad) * w_pad), n_pad, d, kmax,
-                    w_pad);
+  size_t off = plane;
+  if (lz_k > 0) {
+    pc.U = reinterpret_cast<float*>(b + off);
+    pc.Lp = reinterpret_cast<float*>(b + off + plane);
+    off += (1 + static_cast<size_t>(lz_k)) * plane;
+  }
+  pc.ws = carve_nys(b + off, n_pad, d, kmax, w_pad, deriv);
   return pc;
 }
 
@@ -807,6 +820,39 @@ gp_status run_lanczos(const gp_problem* prob, const SimtPlan& p, int prec, Solve
   return GP_OK;
 }
 
+// SLQ on M^-1/2 Kh M^-1/2 (Eq. 1's second term) for columns [col0, col0 + p)
+// of the probe block W.B, with pc.Z = M^-1 W.B: Lanczos in the variables
+// q = M^-1/2 qh with the M-images P = M Q kept beside the basis (pc.Lp), so
+// each step applies M^-1 once and M never: W = Kh q_j, alpha_j = q_j^T W,
+// u = M^-1 W - alpha_j q_j - beta q_{j-1}, M u = W - alpha_j p_j - beta p_{j-1},
+// two reorthogonalisation passes in the M-inner product, beta_j = sqrt(u^T M u).
+// The quadrature weight is ||zh||^2 = z^T M^-1 z.
+gp_status run_lanczos_m(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W,
+                        const Precond& pc, int col0, int np, int k, cudaStream_t st) {
+  const int64_t n = prob->n;
+  const double f2 = prob->theta.f * prob->theta.f;
+  const int64_t plane = p.nr_pad * p.w_pad;
+  CgState* S = W.S2;
+  GP_CUDA(cudaMemsetAsync(S, 0, sizeof(CgState), st));
+  GP_CUDA(launch_lz_init_m(S, W.B, pc.Z, W.Lq, pc.Lp, p.nr_pad, p.w_pad, col0, np, W.red, st));
+  for (int j = 0; j < k; ++j) {
+    const float* Qj = W.Lq + j * plane;
+    gp_status s = run_product(p, prob->kernel, false, prec, W.xs, W.xs, Qj, W.vt, W.part, nullptr,
+                              &S->n_active, &S->err, st);
+    if (s != GP_OK) return s;
+    GP_CUDA(launch_lz_epi_alpha(S, W.part, p.split, Qj, W.R, p.nr_pad, n, p.w_pad, f2,
+                                prob->theta.s, j, W.red, st));
+    GP_CUDA(nys_apply(pc.ws, pc.rank, n, pc.s, W.R, pc.U, &S->n_active, st));
+    GP_CUDA(launch_lz_three_term(S, pc.U, W.Lq, p.nr_pad, p.w_pad, j, st));
+    GP_CUDA(launch_lz_three_term(S, W.R, pc.Lp, p.nr_pad, p.w_pad, j, st));
+    GP_CUDA(launch_lz_reorth_m(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, W.red, st));
+    GP_CUDA(launch_lz_reorth_m(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, W.red, st));
+    GP_CUDA(launch_lz_mnorm_next(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, k, W.red, st));
+  }
+  GP_CUDA(launch_slq(S, col0, np, k, st));
+  return GP_OK;
+}
+
 }  // namespace gp
 
 struct HostCg {
@@ -827,6 +873,8 @@ struct SolveSetup {
   int slq_prec;
   SolveWs W;
   KernelConsts kc;
+  bool precond = false;   // Eq. 1 / Eq. 2 with the Nystrom preconditioner
+  Precond pcd;
 };
 
 static gp_status setup_solve_plans(const gp_problem* prob, const SolvePlans& P, bool with_grad,
@@ -878,7 +926,24 @@ static int effective_maxit(const gp_problem* prob, const gp_solve_opts* o) {
   return static_cast<int>(m);
 }
 
+// Bytes of the loss workspace: the solver's, then (precond_rank > 0) the
+// preconditioner's planes and factor with its derivative dL/dl.
+static size_t loss_bytes(const gp_problem* prob, const gp_solve_opts* o, bool with_grad) {
+  const int ww = 1 + o->nprobe;
+  const int lz_k = o->nprobe > 0 ? o->nlanczos : 0;
+  const int sp = slq_prec_of(o);
+  const SolvePlans P = solve_plans(prob, ww, o->prec, lz_k, sp);
+  const size_t base = carve_solve(nullptr, P.pc, P.pg, P.pl, with_grad, lz_k, o->prec, sp).bytes;
+  if (o->precond_rank <= 0) return base;
+  return align256(base) + precond_bytes(P.pc.nr_pad, prob->d, precond_kmax(prob, o->precond_rank),
+                                        P.pc.w_pad, lz_k, with_grad);
+}
+
 // Forward: CG on [y | Z], SLQ, y^T alpha, loss assembly.  Leaves X = Kh^-1 B.
+// With the preconditioner (Eq. 1 / Eq. 2): the factor with dL/dl and the
+// closed-form terms first, probes z = L e1 + sqrt(s) e2 ~ N(0, M), PCG, M^-1 of
+// the probe block (kept for the gradient pass), SLQ on M^-1/2 Kh M^-1/2 and
+// log|M| added to the log-determinant.
 static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_solve_opts* o,
                               bool with_grad, void* ws, size_t ws_bytes, cudaStream_t st,
                               SolveSetup& ss, gp_status& cg_status) {
@@ -886,18 +951,43 @@ static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_s
   const int p = o->nprobe;
   const int w = 1 + p;
   const int lz_k = p > 0 ? o->nlanczos : 0;
+  const bool precond = o->precond_rank > 0;
+  if (precond && (s = check_ws(ws, ws_bytes, loss_bytes(prob, o, with_grad))) != GP_OK) return s;
   if ((s = setup_solve(prob, w, with_grad, o->prec, lz_k, slq_prec_of(o), ws, ws_bytes, st, ss)) !=
       GP_OK)
     return s;
   SolveWs& W = ss.W;
-  GP_CUDA(launch_pad_block(y, prob->n, 1, 1, W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
-  if ((s = fill_probes(prob, o, W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) return s;
-  s = run_cg(prob, ss.pc, o->prec, W, w, effective_maxit(prob, o), o->cg_rtol, st);
+  const int64_t n = prob->n;
+  ss.precond = precond;
+  if (precond) {
+    const int kmax = precond_kmax(prob, o->precond_rank);
+    ss.pcd = carve_precond(static_cast<char*>(ws) + align256(W.bytes), ss.pc.nr_pad, prob->d, kmax,
+                           ss.pc.w_pad, lz_k, with_grad);
+    if ((s = build_precond(prob, kmax, o->precond_tol, ss.pcd, st)) != GP_OK) return s;
+    GP_CUDA(nys_closed_terms(ss.pcd.ws, ss.pcd.rank, n, prob->theta.s, prob->theta.f,
+                             &W.S->logdet_m, W.S->trm, st));
+  }
+  GP_CUDA(launch_pad_block(y, n, 1, 1, W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));
+  if (precond) {
+    if (p > 0)
+      GP_CUDA(nys_probes(ss.pcd.ws, ss.pcd.rank, n, prob->theta.s, o->probes, o->seed, p, W.B, 1, st));
+  } else if ((s = fill_probes(prob, o, W.B, ss.pc.nr_pad, ss.pc.w_pad, 1, st)) != GP_OK) {
+    return s;
+  }
+  s = run_cg(prob, ss.pc, o->prec, W, w, effective_maxit(prob, o), o->cg_rtol, st,
+             precond ? &ss.pcd : nullptr);
   if (s != GP_OK) return s;
   if (p > 0) {
-    if ((s = run_lanczos(prob, ss.pl, ss.slq_prec, W, 1, p, o->nlanczos, st)) != GP_OK) return s;
+    if (precond) {
+      GP_CUDA(nys_apply(ss.pcd.ws, ss.pcd.rank, n, ss.pcd.s, W.B, ss.pcd.Z, nullptr, st));
+      if ((s = run_lanczos_m(prob, ss.pl, ss.slq_prec, W, ss.pcd, 1, p, o->nlanczos, st)) != GP_OK)
+        return s;
+    } else if ((s = run_lanczos(prob, ss.pl, ss.slq_prec, W, 1, p, o->nlanczos, st)) != GP_OK) {
+      return s;
+    }
     GP_CUDA(cudaMemcpyAsync(W.S->out, W.S2->out, 2 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
+  if (precond) GP_CUDA(launch_add_logdet_m(W.S, st));
   GP_CUDA(launch_yalpha(W.S, W.B, W.X, ss.pc.nr_pad, ss.pc.w_pad, W.red, st));
   GP_CUDA(launch_assemble(W.S, prob->n, p, st));
   cg_status = GP_OK;
@@ -912,8 +1002,10 @@ static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, S
   const int p = o->nprobe;
   const int w = 1 + p;
   const SimtPlan& pg = ss.pg;
-  // V = B with column 0 replaced by alpha (reuse Q as V).
-  GP_CUDA(cudaMemcpyAsync(W.Q, W.B, sizeof(float) * pg.nr_pad * pg.w_pad, cudaMemcpyDeviceToDevice, st));
+  // V = B with column 0 replaced by alpha (reuse Q as V); with the
+  // preconditioner, V = [alpha | M^-1 Z] (Eq. 2's Hutchinson terms with z ~ N(0, M)).
+  GP_CUDA(cudaMemcpyAsync(W.Q, ss.precond ? ss.pcd.Z : W.B, sizeof(float) * pg.nr_pad * pg.w_pad,
+                          cudaMemcpyDeviceToDevice, st));
   GP_CUDA(launch_copy_col0(W.X, W.Q, pg.nr_pad, pg.w_pad, st));
   if (ss.kc.ard) {
     // Per-dimension length-scales: the s terms from column dot products, the f
@@ -938,6 +1030,13 @@ static gp_status backward_impl(const gp_problem* prob, const gp_solve_opts* o, S
   const double f = prob->theta.f;
   GP_CUDA(launch_grad_dots(W.S, part_k, part_d, pg.split, W.Q, W.X, pg.nr_pad, pg.w_pad, w, 2.0 * f,
                            f * f * ss.kc.cD, W.red, st));
+  if (ss.precond && p > 0) {
+    // Subtract v^T (dM/dtheta) v, v = M^-1 z: v^T v, (2/f) |L^T v|^2, 2 (L^T v).(dL^T v).
+    GP_CUDA(launch_plane_dots(W.S, W.Q, W.Q, pg.nr_pad, pg.w_pad, W.S->vv, W.red, st));
+    GP_CUDA(nys_lt_times(ss.pcd.ws, ss.pcd.rank, false, W.Q, ss.pcd.ws.U, st));
+    GP_CUDA(nys_lt_times(ss.pcd.ws, ss.pcd.rank, true, W.Q, ss.pcd.ws.U2, st));
+    GP_CUDA(launch_precond_corr(W.S, ss.pcd.ws.U, ss.pcd.ws.U2, ss.pcd.rank, pg.w_pad, p, f, st));
+  }
   GP_CUDA(launch_assemble(W.S, prob->n, p, st));
   return GP_OK;
 }
@@ -948,6 +1047,8 @@ static gp_status read_outputs(const CgState* S, const CgState* S2, int w, double
   gp_status s;
   if ((s = read_cg(S, h, st)) != GP_OK) return s;
   GP_CUDA(cudaMemcpyAsync(out, S->out, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double mterms[4];
+  GP_CUDA(cudaMemcpyAsync(mterms, &S->logdet_m, sizeof(mterms), cudaMemcpyDeviceToHost, st));
   int err = 0, err2 = 0;
   GP_CUDA(cudaMemcpyAsync(&err, &S->err, sizeof(int), cudaMemcpyDeviceToHost, st));
   if (S2 != nullptr)
@@ -973,6 +1074,8 @@ static gp_status read_outputs(const CgState* S, const CgState* S2, int w, double
     info->refine_steps = 0;
     info->relres_y = h.relres[0];
     info->relres_max = rmax;
+    info->logdet_m = mterms[0];
+    for (int t = 0; t < 3; ++t) info->trace_m[t] = mterms[1 + t];
   }
   if (err == kDevTimeout) return fail(GP_ERR_TIMEOUT, "a bounded device wait gave up");
   if (err == kDevBreakdown) return fail(GP_ERR_BREAKDOWN, "CG breakdown");
@@ -1516,7 +1619,8 @@ size_t gp_workspace_bytes(gp_op op, const gp_problem* prob, int32_t w, const gp_
     }
     case GP_OP_SLQ:
     case GP_OP_LOSS_GRAD: {
-      if (check_opts(opts, op == GP_OP_SLQ) != GP_OK) return 0;
+      if (check_opts(opts, op == GP_OP_SLQ, op == GP_OP_LOSS_GRAD) != GP_OK) return 0;
+      if (op == GP_OP_LOSS_GRAD) return loss_bytes(prob, opts, true);
       const int ww = op == GP_OP_SLQ ? opts->nprobe : 1 + opts->nprobe;
       const int lz_k = opts->nprobe > 0 ? opts->nlanczos : 0;
       const int sp = slq_prec_of(opts);
@@ -1764,7 +1868,8 @@ gp_status gp_loss_and_grad(const gp_problem* prob, const float* y, const gp_solv
                            void* stream) {
   gp_status s;
   if ((s = check_problem(prob)) != GP_OK) return s;
-  if ((s = check_opts(opts, false)) != GP_OK) return s;
+  if ((s = check_opts(opts, false, true)) != GP_OK) return s;
+  if (opts->precond_rank > 0 && (s = no_ard(prob, "the preconditioned loss")) != GP_OK) return s;
   if (y == nullptr) return fail(GP_ERR_ARG, "y is NULL");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   SolveSetup ss;

@@ -28,6 +28,7 @@ constexpr int kGK = 32;                           // Gram rows per shared-memory
 constexpr int kLtvChunk = 4096;                   // rows per block of L^T V
 constexpr int kZTile = 512;                       // rows of T staged per pass of the Z kernel
 constexpr int kInvWarps = 2;                      // columns of C^-1 per block
+constexpr int kRedCap = 152 * 16;                 // blocks of a grid_for reduction
 
 __device__ __forceinline__ void acc_prod(pa::fpair& acc, float a, float b) {
   const pa::fpair p = pa::two_prod(a, b);
@@ -116,6 +117,7 @@ __global__ void nys_init_kernel(const float* X, int64_t n, int d, const StageSca
     S->err = 0;
     S->pivot = 0;
     S->dp = f2;
+    S->ddp = 0.0;
     S->ticket = 0u;
   }
 }
@@ -124,7 +126,8 @@ struct StepArgs {
   const float* xs;
   int64_t n, n_pad;
   int d, kernel;
-  pa::fpair kc;
+  pa::fpair kc;       // kernel constant (kernel_pair_const)
+  pa::fpair dlc;      // derivative constant: 1/l^3 (Gaussian) or 1/l (Matern-3/2)
   double f2, tol_abs;
   int kmax;
   float* Lt;
@@ -134,7 +137,25 @@ struct StepArgs {
   double* amax_v;
   long long* amax_i;
   NysState* S;
+  float* Ldt;         // derivative factor (DERIV only)
+  float* dprow;
 };
+
+// k(r) and dk/dl from r^2 in pair arithmetic (isotropic l):
+// Gaussian k = exp(-r^2 kc), dk/dl = k r^2 / l^3; Matern-3/2 with a = r kc:
+// k = (1 + a) e^-a, dk/dl = a^2 e^-a / l.
+__device__ __forceinline__ void kernel_and_dl(pa::fpair r2, int kernel, pa::fpair kc, pa::fpair dlc,
+                                              const pa::ExpConsts& C, pa::fpair& k, pa::fpair& dk) {
+  if (kernel == 0) {
+    k = pa::exp(pa::neg(pa::mul(r2, kc)), C);
+    dk = pa::mul(pa::mul(k, r2), dlc);
+  } else {
+    const pa::fpair a = pa::mul(pa::sqrt(r2), kc);
+    const pa::fpair e = pa::exp(pa::neg(a), C);
+    k = pa::mul(pa::add_f(a, 1.0f), e);
+    dk = pa::mul(pa::mul(pa::mul(a, a), e), dlc);
+  }
+}
 
 // Step j: with p the current pivot and d_p its residual diagonal,
 //   L[i][j] = (f^2 k(x_i, x_p) - sum_{m<j} L[i][m] L[p][m]) / sqrt(d_p),
@@ -142,16 +163,26 @@ struct StepArgs {
 // The kernel entry is the pair exponential of the compensated residual and
 // the dot product is Dot2, so the column is exact for the stored (FP32)
 // earlier columns up to its final rounding; d is kept in FP64 as the exact
-// residual diagonal of the stored factor.
-template <int DMAX>
+// residual diagonal of the stored factor.  With DERIV the same step also
+// forms column j of dL/dl (pivots fixed):
+//   dS_i = f^2 dk/dl(x_i, x_p) - sum_{m<j} (dL[i][m] L[p][m] + L[i][m] dL[p][m]),
+//   dL[i][j] = (dS_i - L[i][j] dd_p / 2 / sqrt(d_p)) / sqrt(d_p),
+// with dd_p = -2 sum_m L[p][m] dL[p][m] (dk/dl = 0 at r = 0), formed by the
+// previous step's last block.
+template <int DMAX, bool DERIV>
 __global__ void __launch_bounds__(kStepThreads)
     nys_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ pa::ExpConsts C, int j) {
-  extern __shared__ float sp[];   // row p of L, columns < j
+  extern __shared__ float sp[];   // row p of L, then (DERIV) row p of dL/dl; columns < j
   NysState* S = a.S;
   if (S->stop) return;
   const long long p = S->pivot;
   const double dp = S->dp;
-  for (int m = threadIdx.x; m < j; m += blockDim.x) sp[m] = a.prow[m];
+  const double ddp = DERIV ? S->ddp : 0.0;
+  float* sdp = sp + a.kmax;
+  for (int m = threadIdx.x; m < j; m += blockDim.x) {
+    sp[m] = a.prow[m];
+    if constexpr (DERIV) sdp[m] = a.dprow[m];
+  }
   float xp[DMAX];
 #pragma unroll
   for (int t = 0; t < DMAX; ++t) xp[t] = t < a.d ? a.xs[p * a.d + t] : 0.0f;
@@ -161,23 +192,40 @@ __global__ void __launch_bounds__(kStepThreads)
   long long besti = LLONG_MAX;
   if (i0 < a.n_pad) {
     pa::fpair acc[kStepRows] = {};
+    pa::fpair dacc[kStepRows] = {};
     const float* col = a.Lt + i0;
-    // Batches of kStepBatch columns: all loads of a batch are issued before
-    // the first is used, so that enough bytes are in flight to stream L at
-    // the memory's rate when few blocks share an SM.
+    const float* dcol = DERIV ? a.Ldt + i0 : nullptr;
+    // Batches of columns: all loads of a batch are issued before the first
+    // is used, so that enough bytes are in flight to stream L at the memory's
+    // rate when few blocks share an SM.
+    constexpr int kB = DERIV ? kStepBatch / 2 : kStepBatch;
     int m = 0;
-    for (; m + kStepBatch <= j; m += kStepBatch) {
-      float4 l[kStepBatch];
+    for (; m + kB <= j; m += kB) {
+      float4 l[kB], dl[kB];
 #pragma unroll
-      for (int u = 0; u < kStepBatch; ++u)
+      for (int u = 0; u < kB; ++u) {
         l[u] = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m + u) * a.n_pad);
+        if constexpr (DERIV)
+          dl[u] = *reinterpret_cast<const float4*>(dcol + static_cast<int64_t>(m + u) * a.n_pad);
+      }
 #pragma unroll
-      for (int u = 0; u < kStepBatch; ++u) {
+      for (int u = 0; u < kB; ++u) {
         const float b = sp[m + u];
         acc_prod(acc[0], l[u].x, b);
         acc_prod(acc[1], l[u].y, b);
         acc_prod(acc[2], l[u].z, b);
         acc_prod(acc[3], l[u].w, b);
+        if constexpr (DERIV) {
+          const float db = sdp[m + u];
+          acc_prod(dacc[0], dl[u].x, b);
+          acc_prod(dacc[1], dl[u].y, b);
+          acc_prod(dacc[2], dl[u].z, b);
+          acc_prod(dacc[3], dl[u].w, b);
+          acc_prod(dacc[0], l[u].x, db);
+          acc_prod(dacc[1], l[u].y, db);
+          acc_prod(dacc[2], l[u].z, db);
+          acc_prod(dacc[3], l[u].w, db);
+        }
       }
     }
     for (; m < j; ++m) {
@@ -187,26 +235,52 @@ __global__ void __launch_bounds__(kStepThreads)
       acc_prod(acc[1], l.y, b);
       acc_prod(acc[2], l.z, b);
       acc_prod(acc[3], l.w, b);
+      if constexpr (DERIV) {
+        const float4 dl = *reinterpret_cast<const float4*>(dcol + static_cast<int64_t>(m) * a.n_pad);
+        const float db = sdp[m];
+        acc_prod(dacc[0], dl.x, b);
+        acc_prod(dacc[1], dl.y, b);
+        acc_prod(dacc[2], dl.z, b);
+        acc_prod(dacc[3], dl.w, b);
+        acc_prod(dacc[0], l.x, db);
+        acc_prod(dacc[1], l.y, db);
+        acc_prod(dacc[2], l.z, db);
+        acc_prod(dacc[3], l.w, db);
+      }
     }
     const double inv = 1.0 / sqrt(dp);
-    float out[kStepRows];
+    float out[kStepRows], dout[kStepRows];
 #pragma unroll
     for (int q = 0; q < kStepRows; ++q) {
       const int64_t i = i0 + q;
-      float c = 0.0f;
+      float c = 0.0f, dc = 0.0f;
       if (i < a.n) {
         const pa::fpair r2 = pa::sqdist<DMAX>(a.xs + i * a.d, xp, a.d);
-        const pa::fpair k = pa::kernel_entry(r2, a.kernel, a.kc, C);
-        c = static_cast<float>((a.f2 * pa::to_double(k) - pa::to_double(acc[q])) * inv);
+        pa::fpair k, dk;
+        if constexpr (DERIV) {
+          kernel_and_dl(r2, a.kernel, a.kc, a.dlc, C, k, dk);
+        } else {
+          k = pa::kernel_entry(r2, a.kernel, a.kc, C);
+        }
+        const double v = (a.f2 * pa::to_double(k) - pa::to_double(acc[q])) * inv;
+        c = static_cast<float>(v);
+        if constexpr (DERIV) {
+          const double dS = a.f2 * pa::to_double(dk) - pa::to_double(dacc[q]);
+          dc = static_cast<float>((dS - v * ddp * 0.5 * inv) * inv);
+        }
         double dn = a.dg[i] - static_cast<double>(c) * c;
         if (i == p) dn = 0.0;
         a.dg[i] = dn;
         better(best, besti, dn, i);
       }
       out[q] = c;
+      dout[q] = dc;
     }
     *reinterpret_cast<float4*>(a.Lt + static_cast<int64_t>(j) * a.n_pad + i0) =
         make_float4(out[0], out[1], out[2], out[3]);
+    if constexpr (DERIV)
+      *reinterpret_cast<float4*>(a.Ldt + static_cast<int64_t>(j) * a.n_pad + i0) =
+          make_float4(dout[0], dout[1], dout[2], dout[3]);
   }
   // Block argmax, then the last block picks the next pivot.
   __shared__ double wv[kStepThreads / 32];
@@ -246,25 +320,54 @@ __global__ void __launch_bounds__(kStepThreads)
   }
   __syncthreads();
   if (go_on) {
-    for (int m = threadIdx.x; m <= j; m += blockDim.x)
-      a.prow[m] = a.Lt[static_cast<int64_t>(m) * a.n_pad + next];
+    double part = 0.0;
+    for (int m = threadIdx.x; m <= j; m += blockDim.x) {
+      const float lv = a.Lt[static_cast<int64_t>(m) * a.n_pad + next];
+      a.prow[m] = lv;
+      if constexpr (DERIV) {
+        const float dv = a.Ldt[static_cast<int64_t>(m) * a.n_pad + next];
+        a.dprow[m] = dv;
+        part += static_cast<double>(lv) * dv;
+      }
+    }
+    if constexpr (DERIV) {
+      // dd_p of the next pivot, summed in a fixed order.
+      __shared__ double red[kStepThreads];
+      red[threadIdx.x] = part;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int q = 0; q < kStepThreads; ++q) t += red[q];
+        S->ddp = -2.0 * t;
+      }
+    }
   }
 }
 
 // ------------------------------------------------------------------- Gram --
 
 // Partial sums of L^T L over one chunk of rows, for one 64 x 64 tile pair
-// (ta >= tb) of the lower triangle.  Dot2 accumulation, renormalised per slab.
+// (ta >= tb) of the lower triangle; with TWO, of L^T Bm (Bm = dL/dl) for every
+// tile pair (ta, tb), t = ta * tiles + tb.  Dot2 accumulation, renormalised
+// per slab.
+template <bool TWO>
 __global__ void __launch_bounds__(256)
-    nys_gram_kernel(const float* __restrict__ Lt, int64_t n_pad, int r, int64_t rows_per_chunk,
-                    int pairs, double* gpart) {
+    nys_gram_kernel(const float* __restrict__ Lt, const float* __restrict__ Bm, int64_t n_pad, int r,
+                    int64_t rows_per_chunk, int pairs, int tiles, double* gpart) {
   __shared__ __align__(16) float As[kGK][kGT + 4];
   __shared__ __align__(16) float Bs[kGK][kGT + 4];
   const int t = blockIdx.x;
-  int ta = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
-  while (ta * (ta + 1) / 2 > t) --ta;
-  while ((ta + 1) * (ta + 2) / 2 <= t) ++ta;
-  const int tb = t - ta * (ta + 1) / 2;
+  int ta, tb;
+  if constexpr (TWO) {
+    ta = t / tiles;
+    tb = t - ta * tiles;
+  } else {
+    ta = static_cast<int>((sqrtf(8.0f * t + 1.0f) - 1.0f) * 0.5f);
+    while (ta * (ta + 1) / 2 > t) --ta;
+    while ((ta + 1) * (ta + 2) / 2 <= t) ++ta;
+    tb = t - ta * (ta + 1) / 2;
+  }
+  const float* Bsrc = TWO ? Bm : Lt;
   const int64_t i_begin = static_cast<int64_t>(blockIdx.y) * rows_per_chunk;
   const int64_t i_end = i_begin + rows_per_chunk < n_pad ? i_begin + rows_per_chunk : n_pad;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -275,7 +378,7 @@ __global__ void __launch_bounds__(256)
       const int ra = ta * kGT + aa, rb = tb * kGT + aa;
       float4 va = make_float4(0.f, 0.f, 0.f, 0.f), vb = va;
       if (ra < r) va = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(ra) * n_pad + i0 + part * 4);
-      if (rb < r) vb = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(rb) * n_pad + i0 + part * 4);
+      if (rb < r) vb = *reinterpret_cast<const float4*>(Bsrc + static_cast<int64_t>(rb) * n_pad + i0 + part * 4);
       As[part * 4 + 0][aa] = va.x;
       As[part * 4 + 1][aa] = va.y;
       As[part * 4 + 2][aa] = va.z;
@@ -327,6 +430,123 @@ __global__ void nys_gram_reduce_kernel(const double* gpart, int r, int pairs, in
     double v = 0.0;
     for (int ch = 0; ch < chunks; ++ch) v += gpart[static_cast<int64_t>(ch) * pairs * (kGT * kGT) + off];
     C[e] = a == b ? v + s : v;
+  }
+}
+
+// <C^-1, H> = sum_{a,b < r} Winv[a][b] H[a][b] with H = sum over chunks of the
+// TWO Gram partials; per-block FP64 partials in a fixed order, summed by the
+// last block into S->tr_wh.
+__global__ void nys_trwh_kernel(const double* gpart2, int chunks, int tiles, int r,
+                                const double* Winv, double* red, NysState* S) {
+  const int64_t total = static_cast<int64_t>(r) * r;
+  const int64_t slot = static_cast<int64_t>(tiles) * tiles * (kGT * kGT);
+  double acc = 0.0;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int a = static_cast<int>(e / r), b = static_cast<int>(e % r);
+    const int64_t off = (static_cast<int64_t>(a / kGT) * tiles + b / kGT) * (kGT * kGT) +
+                        (a % kGT) * kGT + (b % kGT);
+    double h = 0.0;
+    for (int ch = 0; ch < chunks; ++ch) h += gpart2[ch * slot + off];
+    acc += Winv[e] * h;
+  }
+  __shared__ double sm[256];
+  sm[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) t += sm[q];
+    red[blockIdx.x] = t;
+  }
+  if (!last_block(&S->ticket)) return;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (unsigned q = 0; q < gridDim.x; ++q) t += red[q];
+    S->tr_wh = t;
+  }
+}
+
+// log|C| = 2 sum log cdiag and tr(C^-1), one block, fixed order.
+__global__ void nys_scalars_kernel(const double* cdiag, const double* Winv, int r, NysState* S) {
+  __shared__ double s1[256], s2[256];
+  double a = 0.0, b = 0.0;
+  for (int j = threadIdx.x; j < r; j += blockDim.x) {
+    a += log(cdiag[j]);
+    b += Winv[static_cast<int64_t>(j) * r + j];
+  }
+  s1[threadIdx.x] = a;
+  s2[threadIdx.x] = b;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tb = 0.0;
+    for (int q = 0; q < blockDim.x; ++q) {
+      ta += s1[q];
+      tb += s2[q];
+    }
+    S->logdet_c = 2.0 * ta;
+    S->tr_w = tb;
+  }
+}
+
+__global__ void nys_terms_kernel(const NysState* S, int64_t n, int r, double s, double f,
+                                 double* logdet_m, double* trm) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double nr = static_cast<double>(n - r);
+  logdet_m[0] = nr * log(s) + S->logdet_c;
+  trm[0] = nr / s + S->tr_w;
+  trm[1] = (2.0 / f) * (static_cast<double>(r) - s * S->tr_w);
+  trm[2] = 2.0 * S->tr_wh;
+}
+
+// ------------------------------------------------------------------ probes --
+
+__device__ __forceinline__ uint64_t splitmix64_hash(uint64_t key) {
+  uint64_t z = key + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// Standard normal value of (row i, column c): Box-Muller on two hashed uniforms.
+__device__ __forceinline__ double gauss_eps(uint64_t tag, int c, int64_t i) {
+  const uint64_t base = tag ^ (static_cast<uint64_t>(c) << 40);
+  const uint64_t h1 = splitmix64_hash(base ^ static_cast<uint64_t>(2 * i));
+  const uint64_t h2 = splitmix64_hash(base ^ static_cast<uint64_t>(2 * i + 1));
+  const double u1 = static_cast<double>((h1 >> 11) + 1) * 0x1.0p-53;
+  const double u2 = static_cast<double>(h2 >> 11) * 0x1.0p-53;
+  return sqrt(-2.0 * log(u1)) * cos(2.0 * 3.14159265358979323846 * u2);
+}
+
+// B[i][col0 + c] = sqrt(s) e2[i][c] (i < n; 0 below), Tp[m][col0 + c] = -e1[m][c]
+// as pairs (m < r; every other Tp entry 0), so that the Z kernel with scale 1
+// turns B into sqrt(s) e2 + L e1.
+__global__ void nys_eps_kernel(const float* eps, uint64_t tag, int64_t n, int64_t n_pad, int r,
+                               int p, int col0, int w_pad, double sqrt_s, float* B, float* Tp) {
+  const int64_t total = (n_pad + r) * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const int64_t row = e / w_pad;
+    const int col = static_cast<int>(e - row * w_pad);
+    const int c = col - col0;
+    const bool live = c >= 0 && c < p;
+    if (row < n_pad) {
+      if (!live) continue;
+      float v = 0.0f;
+      if (row < n) {
+        const double g = eps != nullptr ? static_cast<double>(eps[row * p + c]) : gauss_eps(tag, c, row);
+        v = static_cast<float>(sqrt_s * g);
+      }
+      B[row * w_pad + col] = v;
+    } else {
+      const int64_t m = row - n_pad;
+      float v = 0.0f;
+      if (live) {
+        const int64_t erow = n + m;
+        v = eps != nullptr ? eps[erow * p + c] : static_cast<float>(gauss_eps(tag, c, erow));
+      }
+      Tp[(m * w_pad + col) * 2] = -v;
+      Tp[(m * w_pad + col) * 2 + 1] = 0.0f;
+    }
   }
 }
 
@@ -486,10 +706,12 @@ __global__ void nys_wu_kernel(const double* Winv, const double* U, int r, int w_
   }
 }
 
-// Z = (V - L T) / s for the four columns 4 y .. 4 y + 3; one row per thread.
+// Z = (V - L T) * scale for the four columns 4 y .. 4 y + 3; one row per
+// thread (V and Z may be the same block: each element is read, then written,
+// by one thread).
 __global__ void __launch_bounds__(256)
     nys_z_kernel(const float* __restrict__ Lt, int64_t n_pad, int64_t n, int r, const float* Tp,
-                 const float* __restrict__ V, float* Z, int w_pad, double s, const int* active) {
+                 const float* V, float* Z, int w_pad, double scale, const int* active) {
   if (active != nullptr && *active == 0) return;
   __shared__ float sT[kZTile][8];
   const int c0 = blockIdx.y * 4;
@@ -536,7 +758,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int cc = 0; cc < 4; ++cc) {
     float z = 0.0f;
-    if (i < n) z = static_cast<float>((static_cast<double>(V[i * w_pad + c0 + cc]) - pa::to_double(acc[cc])) / s);
+    if (i < n) z = static_cast<float>((static_cast<double>(V[i * w_pad + c0 + cc]) - pa::to_double(acc[cc])) * scale);
     Z[i * w_pad + c0 + cc] = z;
   }
 }
@@ -551,6 +773,15 @@ int gram_chunks(int pairs) { return std::max(1, std::min(16, (608 + pairs - 1) /
 
 // Tile slots of the Gram partial sums for any rank up to kmax (chunks x pairs
 // is not monotone in the rank).
+// Tile slots of the L^T dL/dl partial sums (all tile pairs) for any rank up to kmax.
+size_t gram2_slots(int kmax) {
+  const int tiles = (kmax + kGT - 1) / kGT;
+  size_t most = 0;
+  for (int t = 1; t <= tiles; ++t)
+    most = std::max(most, static_cast<size_t>(gram_chunks(t * t)) * t * t);
+  return most;
+}
+
 size_t gram_slots(int kmax) {
   const int tiles = (kmax + kGT - 1) / kGT;
   size_t most = 0;
@@ -578,9 +809,9 @@ struct NysCarve {
 
 }  // namespace
 
-NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad) {
+NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad, bool deriv) {
   NysCarve c(base);
-  NysWs w;
+  NysWs w{};
   const int step_blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
   const int64_t chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
   w.xs = c.take<float>(static_cast<size_t>(n_pad) * d);
@@ -598,16 +829,24 @@ NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad) {
   w.upart = c.take<double>(static_cast<size_t>(chunks) * kmax * w_pad);
   w.U = c.take<double>(static_cast<size_t>(kmax) * w_pad);
   w.Tp = c.take<float>(static_cast<size_t>(kmax) * w_pad * 2);
+  w.tred = c.take<double>(kRedCap);
+  if (deriv) {
+    w.Ldt = c.take<float>(static_cast<size_t>(kmax) * n_pad);
+    w.dprow = c.take<float>(kmax);
+    w.gpart2 = c.take<double>(gram2_slots(kmax) * kGT * kGT);
+    w.U2 = c.take<double>(static_cast<size_t>(kmax) * w_pad);
+  }
   w.n_pad = n_pad;
   w.kmax = kmax;
   w.w_pad = w_pad;
   w.d = d;
+  w.deriv = deriv;
   w.bytes = c.off + 256;
   return w;
 }
 
-size_t nys_bytes(int64_t n_pad, int d, int kmax, int w_pad) {
-  return carve_nys(nullptr, n_pad, d, kmax, w_pad).bytes;
+size_t nys_bytes(int64_t n_pad, int d, int kmax, int w_pad, bool deriv) {
+  return carve_nys(nullptr, n_pad, d, kmax, w_pad, deriv).bytes;
 }
 
 cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_abs, int* rank,
@@ -650,10 +889,18 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
   a.amax_v = W.amax_v;
   a.amax_i = W.amax_i;
   a.S = W.S;
+  a.Ldt = W.Ldt;
+  a.dprow = W.dprow;
+  a.dlc = pa::from_double(P.kernel == 0 ? 1.0 / (kl * kl * kl) : 1.0 / kl);
+  const bool deriv = W.deriv;
+  if (deriv && P.ls != nullptr) return cudaErrorInvalidValue;
   const int blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
-  const size_t smem = static_cast<size_t>(kmax) * sizeof(float);
+  const size_t smem = static_cast<size_t>(kmax) * sizeof(float) * (deriv ? 2 : 1);
   for (int j = 0; j < kmax; ++j) {
-    nys_step_kernel<GP_MAX_DIM><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+    if (deriv)
+      nys_step_kernel<GP_MAX_DIM, true><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+    else
+      nys_step_kernel<GP_MAX_DIM, false><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -668,7 +915,8 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
   const int pairs = tiles * (tiles + 1) / 2;
   const int G = gram_chunks(pairs);
   const int64_t rows_per_chunk = round_up64((n_pad + G - 1) / G, kGK);
-  nys_gram_kernel<<<dim3(pairs, G), 256, 0, st>>>(W.Lt, n_pad, r, rows_per_chunk, pairs, W.gpart);
+  nys_gram_kernel<false><<<dim3(pairs, G), 256, 0, st>>>(W.Lt, W.Lt, n_pad, r, rows_per_chunk, pairs,
+                                                         tiles, W.gpart);
   count_launch();
   nys_gram_reduce_kernel<<<grid_for(static_cast<int64_t>(r) * r, 256), 256, 0, st>>>(W.gpart, r, pairs,
                                                                                      G, P.s, W.C);
@@ -691,7 +939,22 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
     return e;
   nys_inverse_kernel<<<(r + kInvWarps - 1) / kInvWarps, 32 * kInvWarps, ismem, st>>>(W.C, r, W.Winv);
   count_launch();
+  nys_scalars_kernel<<<1, 256, 0, st>>>(W.cdiag, W.Winv, r, W.S);
+  count_launch();
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (deriv) {
+    // <C^-1, L^T dL/dl>.
+    const int t2 = tiles * tiles;
+    const int G2 = gram_chunks(t2);
+    const int64_t rpc2 = round_up64((n_pad + G2 - 1) / G2, kGK);
+    nys_gram_kernel<true><<<dim3(t2, G2), 256, 0, st>>>(W.Lt, W.Ldt, n_pad, r, rpc2, t2, tiles,
+                                                        W.gpart2);
+    count_launch();
+    nys_trwh_kernel<<<grid_for(static_cast<int64_t>(r) * r, 256, kRedCap), 256, 0, st>>>(
+        W.gpart2, G2, tiles, r, W.Winv, W.tred, W.S);
+    count_launch();
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   if ((e = cudaMemcpyAsync(&hs, W.S, sizeof hs, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
   if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
   if (hs.err != 0) {
@@ -699,6 +962,44 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
     return cudaErrorInvalidValue;
   }
   return cudaSuccess;
+}
+
+cudaError_t nys_closed_terms(const NysWs& W, int rank, int64_t n, double s, double f,
+                             double* logdet_m, double* trm, cudaStream_t st) {
+  nys_terms_kernel<<<1, 32, 0, st>>>(W.S, n, rank, s, f, logdet_m, trm);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t nys_probes(const NysWs& W, int rank, int64_t n, double s, const float* eps, uint64_t seed,
+                       int p, float* B, int col0, cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  if (rank < 1 || rank > W.kmax || col0 + p > w_pad || w_pad % 4 != 0) return cudaErrorInvalidValue;
+  const uint64_t tag = seed ^ (1ull << 39);
+  nys_eps_kernel<<<grid_for((n_pad + rank) * w_pad, 256), 256, 0, st>>>(
+      eps, tag, n, n_pad, rank, p, col0, w_pad, sqrt(s), B, W.Tp);
+  count_launch();
+  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), w_pad / 4), 256, 0, st>>>(
+      W.Lt, n_pad, n, rank, W.Tp, B, B, w_pad, 1.0, nullptr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const float* V, double* U,
+                         cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  if (rank < 1 || rank > W.kmax || w_pad % 4 != 0 || (deriv_matrix && !W.deriv))
+    return cudaErrorInvalidValue;
+  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
+  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, w_pad / 4), 256, 0, st>>>(
+      deriv_matrix ? W.Ldt : W.Lt, n_pad, rank, V, w_pad, W.upart, nullptr);
+  count_launch();
+  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
+      W.upart, chunks, rank, w_pad, U, nullptr);
+  count_launch();
+  return cudaGetLastError();
 }
 
 cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
@@ -717,7 +1018,7 @@ cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float
   nys_wu_kernel<<<dim3((rank + 3) / 4, cg), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp, active);
   count_launch();
   nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(
-      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, s, active);
+      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, 1.0 / s, active);
   count_launch();
   return cudaGetLastError();
 }

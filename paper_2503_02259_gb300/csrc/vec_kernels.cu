@@ -666,8 +666,10 @@ __global__ void __launch_bounds__(kRedThreads, 4)
 // reorthogonalisation by two classical Gram-Schmidt passes per step, the steps
 // of stochastic Lanczos quadrature (Ubaru et al. 2017) from q_0 = z/||z||.
 
-__global__ void lz_init_kernel(CgState* S, const float* B, int64_t n_pad, int w_pad, int col0, int p,
-                               double* red) {
+// bn2 = ||B_c||^2, or B_c^T B2_c when B2 is given (preconditioned Lanczos:
+// z^T M^-1 z with B2 = M^-1 B).
+__global__ void lz_init_kernel(CgState* S, const float* B, const float* B2, int64_t n_pad, int w_pad,
+                               int col0, int p, double* red) {
   const RedLayout L = red_layout(w_pad);
   int64_t r0, r1;
   block_rows(n_pad, r0, r1);
@@ -675,7 +677,7 @@ __global__ void lz_init_kernel(CgState* S, const float* B, int64_t n_pad, int w_
   if (L.live)
     for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
       const double b = B[r * w_pad + L.c];
-      acc[0] += b * b;
+      acc[0] += b * (B2 != nullptr ? static_cast<double>(B2[r * w_pad + L.c]) : b);
     }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
@@ -832,8 +834,10 @@ __global__ void lz_sub_kernel(const CgState* S, float* W, const float* Q, int64_
   }
 }
 
-__global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_pad, int j, int k,
-                               double* red) {
+// beta_j = ||W|| per column, or sqrt(W^T W2) when W2 is given (the M-norm of
+// the preconditioned Lanczos vector W with W2 = M W).
+__global__ void lz_norm_kernel(CgState* S, const float* W, const float* W2, int64_t n_pad, int w_pad,
+                               int j, int k, double* red) {
   if (S->n_active == 0) return;
   const RedLayout L = red_layout(w_pad);
   int64_t r0, r1;
@@ -842,7 +846,7 @@ __global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_
   if (L.live)
     for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
       const double v = W[r * w_pad + L.c];
-      acc[0] += v * v;
+      acc[0] += v * (W2 != nullptr ? static_cast<double>(W2[r * w_pad + L.c]) : v);
     }
   block_store<1>(acc, L, w_pad, red);
   if (!last_block(&S->ticket)) return;
@@ -853,7 +857,7 @@ __global__ void lz_norm_kernel(CgState* S, const float* W, int64_t n_pad, int w_
   if (threadIdx.x < w_pad) {
     const int c = threadIdx.x;
     if (S->active[c]) {
-      const double be = sqrt(tot[c]);
+      const double be = sqrt(fmax(tot[c], 0.0));
       const double bprev = j > 0 ? S->bhist[j - 1][c] : 0.0;
       const double tn = fmax(S->tnorm[c], fabs(S->ahist[j][c]) + be + bprev);
       S->tnorm[c] = tn;
@@ -971,11 +975,53 @@ __global__ void assemble_kernel(CgState* S, int64_t n, int p) {
     double var = 0.0;
     for (int i = 1; i <= p; ++i) var += (S->dots[t][i] - mean) * (S->dots[t][i] - mean);
     S->out[6 + t] = quad;
+    mean += S->trm[t];   // tr(M^-1 dM/dtheta) of a preconditioner (0 for M = I)
     S->out[9 + t] = mean;
     S->out[12 + t] = p > 1 ? sqrt(var / (p - 1) / p) : 0.0;
     S->out[3 + t] = 0.5 * (-quad + mean);
   }
   S->out[15] = ya;
+}
+
+// out[c] = sum_r A[r][c] B[r][c] (FP64, fixed order) for every column c < w_pad.
+__global__ void plane_dots_kernel(CgState* S, const float* A, const float* B, int64_t n_pad,
+                                  int w_pad, double* out, double* red) {
+  const RedLayout L = red_layout(w_pad);
+  int64_t r0, r1;
+  block_rows(n_pad, r0, r1);
+  double acc[1] = {0.0};
+  if (L.live)
+    for (int64_t r = r0 + L.rl; r < r1; r += L.nrl) {
+      const int64_t idx = r * w_pad + L.c;
+      acc[0] += static_cast<double>(A[idx]) * static_cast<double>(B[idx]);
+    }
+  block_store<1>(acc, L, w_pad, red);
+  if (!last_block(&S->ticket)) return;
+  const double* tot = final_sums(red, 1, w_pad);
+  if (threadIdx.x < w_pad) out[threadIdx.x] = tot[threadIdx.x];
+}
+
+// Eq. 2's Hutchinson terms with a preconditioner: for probe columns c in
+// [1, 1 + p) with v = M^-1 z_c, subtract v^T (dM/dtheta) v from the dots
+// W_c^T dKh V_c: s: v^T v (S->vv); f: (2/f) ||L^T v||^2; l: 2 (L^T v).(dL^T v),
+// with U = L^T V and U2 = (dL/dl)^T V ([r][w_pad], FP64).
+__global__ void precond_corr_kernel(CgState* S, const double* U, const double* U2, int r, int w_pad,
+                                    int p, double f) {
+  const int c = 1 + static_cast<int>(threadIdx.x);
+  if (c > p) return;
+  double uu = 0.0, ud = 0.0;
+  for (int m = 0; m < r; ++m) {
+    const double u = U[static_cast<int64_t>(m) * w_pad + c];
+    uu += u * u;
+    ud += u * U2[static_cast<int64_t>(m) * w_pad + c];
+  }
+  S->dots[0][c] -= S->vv[c];
+  S->dots[1][c] -= (2.0 / f) * uu;
+  S->dots[2][c] -= 2.0 * ud;
+}
+
+__global__ void add_logdet_m_kernel(CgState* S) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) S->out[0] += S->logdet_m;
 }
 
 __global__ void copy_col0_kernel(const float* X, float* V, int64_t n_pad, int w_pad) {
@@ -1235,7 +1281,7 @@ cudaError_t launch_cg_step(CgState* S, const float* part_k, int split, float* X,
 
 cudaError_t launch_lz_init(CgState* S, const float* B, float* Q0, int64_t n_pad, int w_pad, int col0,
                            int p, double* red, cudaStream_t st) {
-  lz_init_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, n_pad, w_pad, col0, p, red);
+  lz_init_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, B, nullptr, n_pad, w_pad, col0, p, red);
   count_launch();
   lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, B, Q0, n_pad, w_pad, -1);
   count_launch();
@@ -1271,13 +1317,69 @@ cudaError_t launch_lz_reorth(CgState* S, float* W, const float* Q, int64_t n_pad
 
 cudaError_t launch_lz_norm_next(CgState* S, const float* W, float* Q, int64_t n_pad, int w_pad,
                                 int j, int k, double* red, cudaStream_t st) {
-  lz_norm_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, W, n_pad, w_pad, j, k, red);
+  lz_norm_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, W, nullptr, n_pad, w_pad, j, k, red);
   count_launch();
   if (j + 1 < k) {
     float* Qn = Q + static_cast<int64_t>(j + 1) * n_pad * w_pad;
     lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, W, Qn, n_pad, w_pad, j);
     count_launch();
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_init_m(CgState* S, const float* Z, const float* V, float* Q0, float* P0,
+                             int64_t n_pad, int w_pad, int col0, int p, double* red, cudaStream_t st) {
+  lz_init_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, Z, V, n_pad, w_pad, col0, p, red);
+  count_launch();
+  lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, V, Q0, n_pad, w_pad, -1);
+  count_launch();
+  lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, Z, P0, n_pad, w_pad, -1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_reorth_m(CgState* S, float* U, float* MU, const float* Q, const float* P,
+                               int64_t n_pad, int w_pad, int j, double* red, cudaStream_t st) {
+  lz_dots_kernel<<<lz_dot_blocks(n_pad), kRedThreads, 0, st>>>(S, U, P, n_pad, w_pad, j + 1, red);
+  count_launch();
+  lz_sub_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, U, Q, n_pad, w_pad, j + 1);
+  count_launch();
+  lz_sub_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, MU, P, n_pad, w_pad, j + 1);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lz_mnorm_next(CgState* S, const float* U, const float* MU, float* Q, float* P,
+                                 int64_t n_pad, int w_pad, int j, int k, double* red, cudaStream_t st) {
+  lz_norm_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, U, MU, n_pad, w_pad, j, k, red);
+  count_launch();
+  if (j + 1 < k) {
+    const int64_t off = static_cast<int64_t>(j + 1) * n_pad * w_pad;
+    lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, U, Q + off, n_pad, w_pad, j);
+    count_launch();
+    lz_scale_kernel<<<elt_blocks(n_pad * w_pad), kEltThreads, 0, st>>>(S, MU, P + off, n_pad, w_pad, j);
+    count_launch();
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plane_dots(CgState* S, const float* A, const float* B, int64_t n_pad, int w_pad,
+                              double* out, double* red, cudaStream_t st) {
+  plane_dots_kernel<<<red_blocks(n_pad), kRedThreads, 0, st>>>(S, A, B, n_pad, w_pad, out, red);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_precond_corr(CgState* S, const double* U, const double* U2, int r, int w_pad, int p,
+                                double f, cudaStream_t st) {
+  precond_corr_kernel<<<1, kMaxW, 0, st>>>(S, U, U2, r, w_pad, p, f);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_add_logdet_m(CgState* S, cudaStream_t st) {
+  add_logdet_m_kernel<<<1, 32, 0, st>>>(S);
+  count_launch();
   return cudaGetLastError();
 }
 

@@ -40,6 +40,10 @@ struct CgState {
   double ard_quad[2 + GP_MAX_DIM];
   double ard_trace[2 + GP_MAX_DIM];
   double ard_grad[2 + GP_MAX_DIM];
+  // Eq. 1 / Eq. 2 terms of a preconditioner in closed form (zero for M = I):
+  double logdet_m;           // log|M|
+  double trm[3];             // tr(M^-1 dM/dtheta), theta = s, f, l
+  double vv[kMaxW];          // per-column v^T v of the preconditioned Hutchinson terms
   int group_counter;         // work counter of a grouped product (batched solves)
   unsigned bar_count;        // grid barrier of the fused CG step: arrivals
   unsigned bar_gen;          // grid barrier of the fused CG step: generation
@@ -129,6 +133,27 @@ cudaError_t launch_lz_reorth(CgState* S, float* W, const float* Q, int64_t n_pad
 // beta_j = ||W||; truncation; q_{j+1} = W / beta_j.
 cudaError_t launch_lz_norm_next(CgState* S, const float* W, float* Q, int64_t n_pad, int w_pad,
                                 int j, int k, double* red, cudaStream_t st);
+
+// Lanczos on M^-1/2 Kh M^-1/2 carried in the variables q = M^-1/2 qh, with the
+// M-images P = M Q kept beside the basis Q (so that M is never applied):
+// init: bn2 = z^T M^-1 z (Z = the probe block, V = M^-1 Z), q_0 = V / sqrt(bn2),
+// p_0 = Z / sqrt(bn2).
+cudaError_t launch_lz_init_m(CgState* S, const float* Z, const float* V, float* Q0, float* P0,
+                             int64_t n_pad, int w_pad, int col0, int p, double* red, cudaStream_t st);
+// One reorthogonalisation pass in the M-inner product: h = P^T U, U -= Q h, MU -= P h.
+cudaError_t launch_lz_reorth_m(CgState* S, float* U, float* MU, const float* Q, const float* P,
+                               int64_t n_pad, int w_pad, int j, double* red, cudaStream_t st);
+// beta_j = sqrt(U^T MU); q_{j+1} = U / beta_j, p_{j+1} = MU / beta_j.
+cudaError_t launch_lz_mnorm_next(CgState* S, const float* U, const float* MU, float* Q, float* P,
+                                 int64_t n_pad, int w_pad, int j, int k, double* red, cudaStream_t st);
+// out[c] = A_c^T B_c for every column (FP64, fixed order).
+cudaError_t launch_plane_dots(CgState* S, const float* A, const float* B, int64_t n_pad, int w_pad,
+                              double* out, double* red, cudaStream_t st);
+// Subtract v^T dM/dtheta v from the probe columns' dots (see vec_kernels.cu).
+cudaError_t launch_precond_corr(CgState* S, const double* U, const double* U2, int r, int w_pad, int p,
+                                double f, cudaStream_t st);
+// S->out[0] += S->logdet_m.
+cudaError_t launch_add_logdet_m(CgState* S, cudaStream_t st);
 
 // SLQ from the Lanczos coefficients of columns [col0, col0 + p): per-probe
 // values into S->slq_val and (mean, stderr) into S->out[0..1].

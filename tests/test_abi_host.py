@@ -91,12 +91,24 @@ def test_preconditioner_arguments_need_no_gpu(L):
     from paper_2503_02259_gb300 import _binding as B
     prob = B.gp_problem(256, 1000, 3, 0, B.gp_theta(0.1, 1.0, 0.3))
     opts = B.gp_solve_opts(nprobe=4, nlanczos=10, precond_rank=50)
-    # The loss, SLQ and prediction calls do not take the preconditioner.
-    assert L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts)) == 0
+    # SLQ alone and the split forward / backward calls do not take the preconditioner.
+    assert L.gp_workspace_bytes(B.OP_SLQ, ctypes.byref(prob), 0, ctypes.byref(opts)) == 0
     assert b"Nystrom" in L.gp_last_error()
+    st = L.gp_nll_forward(ctypes.byref(prob), 256, ctypes.byref(opts), 256, None, None, 256, 1 << 20,
+                          None)
+    assert st == B.GP_ERR_UNIMPLEMENTED
+    # The loss takes it (isotropic only): its workspace grows by the factor, its
+    # derivative, the Lanczos M-images and the work planes.
+    plain = B.gp_solve_opts(nprobe=4, nlanczos=10)
+    lb = L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(plain))
+    lp = L.gp_workspace_bytes(B.OP_LOSS_GRAD, ctypes.byref(prob), 0, ctypes.byref(opts))
+    assert lb > 0 and lp - lb >= 2 * 4 * 1024 * 50 + 11 * 4 * 1024 * 8
+    ls = (ctypes.c_double * 3)(0.3, 0.4, 0.5)
+    prob.ls = ctypes.cast(ls, ctypes.c_void_p)
     st = L.gp_loss_and_grad(ctypes.byref(prob), 256, ctypes.byref(opts), None, None, None, 256, 1 << 20,
                             None)
-    assert st == B.GP_ERR_UNIMPLEMENTED
+    assert st == B.GP_ERR_UNIMPLEMENTED and b"isotropic" in L.gp_last_error()
+    prob.ls = None
     # The solve's workspace holds at least the factor's FP32 columns.
     base = L.gp_workspace_bytes(B.OP_PCG, ctypes.byref(prob), 1,
                                 ctypes.byref(B.gp_solve_opts(nlanczos=10)))
