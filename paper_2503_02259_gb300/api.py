@@ -59,11 +59,13 @@ def solve_opts(nprobe: int = 0, nlanczos: int = 30, cg_maxit: int = 0, cg_rtol: 
     refinement's outer residual (B.RESIDUAL_PAIR or B.RESIDUAL_FP64);
     precond_rank > 0 selects the Nystrom preconditioner of that rank for the
     solves (precond_tol: its early stop, relative to f^2)."""
-    return B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
-                           float(refine_rtol), int(seed) & (2**64 - 1),
-                           0 if probes is None else probes.data_ptr(), int(refine_maxit),
-                           int(slq_prec), int(refine_residual), int(precond_rank),
-                           float(precond_tol))
+    o = B.gp_solve_opts(int(nprobe), int(nlanczos), int(cg_maxit), int(prec), float(cg_rtol),
+                        float(refine_rtol), int(seed) & (2**64 - 1),
+                        0 if probes is None else probes.data_ptr(), int(refine_maxit),
+                        int(slq_prec), int(refine_residual), int(precond_rank),
+                        float(precond_tol))
+    o._probes_keep = probes   # the struct holds only the address: keep the tensor alive with it
+    return o
 
 
 def workspace(op: int, prob: B.gp_problem, w: int, opts: B.gp_solve_opts | None, device) -> torch.Tensor:

@@ -822,11 +822,13 @@ gp_status run_lanczos(const gp_problem* prob, const SimtPlan& p, int prec, Solve
 
 // SLQ on M^-1/2 Kh M^-1/2 (Eq. 1's second term) for columns [col0, col0 + p)
 // of the probe block W.B, with pc.Z = M^-1 W.B: Lanczos in the variables
-// q = M^-1/2 qh with the M-images P = M Q kept beside the basis (pc.Lp), so
-// each step applies M^-1 once and M never: W = Kh q_j, alpha_j = q_j^T W,
-// u = M^-1 W - alpha_j q_j - beta q_{j-1}, M u = W - alpha_j p_j - beta p_{j-1},
-// two reorthogonalisation passes in the M-inner product, beta_j = sqrt(u^T M u).
-// The quadrature weight is ||zh||^2 = z^T M^-1 z.
+// q = M^-1/2 qh with the M-images P = M Q kept beside the basis (pc.Lp):
+// W = Kh q_j, alpha_j = q_j^T W, u = M^-1 W - alpha_j q_j - beta q_{j-1}, M u
+// formed explicitly (s u + L L^T u), two reorthogonalisation passes in the
+// M-inner product (h = P^T u), beta_j = sqrt(u^T M u).  (Carrying M u by the
+// three-term recurrence instead would divide its error by beta_j at every
+// step: with M close to Kh, beta_j is ~1e-4 and the images drift within a
+// few steps.)  The quadrature weight is ||zh||^2 = z^T M^-1 z.
 gp_status run_lanczos_m(const gp_problem* prob, const SimtPlan& p, int prec, SolveWs& W,
                         const Precond& pc, int col0, int np, int k, cudaStream_t st) {
   const int64_t n = prob->n;
@@ -844,7 +846,7 @@ gp_status run_lanczos_m(const gp_problem* prob, const SimtPlan& p, int prec, Sol
                                 prob->theta.s, j, W.red, st));
     GP_CUDA(nys_apply(pc.ws, pc.rank, n, pc.s, W.R, pc.U, &S->n_active, st));
     GP_CUDA(launch_lz_three_term(S, pc.U, W.Lq, p.nr_pad, p.w_pad, j, st));
-    GP_CUDA(launch_lz_three_term(S, W.R, pc.Lp, p.nr_pad, p.w_pad, j, st));
+    GP_CUDA(nys_apply_m(pc.ws, pc.rank, n, pc.s, pc.U, W.R, &S->n_active, st));
     GP_CUDA(launch_lz_reorth_m(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, W.red, st));
     GP_CUDA(launch_lz_reorth_m(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, W.red, st));
     GP_CUDA(launch_lz_mnorm_next(S, pc.U, W.R, W.Lq, pc.Lp, p.nr_pad, p.w_pad, j, k, W.red, st));

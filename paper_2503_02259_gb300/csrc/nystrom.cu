@@ -706,6 +706,19 @@ __global__ void nys_wu_kernel(const double* Winv, const double* U, int r, int w_
   }
 }
 
+// Tp = -U / s as pairs (so that the Z kernel with scale s gives s V + L U).
+__global__ void nys_mneg_kernel(const double* U, int r, int w_pad, double inv_s, float* Tp,
+                                const int* active) {
+  if (active != nullptr && *active == 0) return;
+  const int64_t total = static_cast<int64_t>(r) * w_pad;
+  for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+    const pa::fpair p = pa::from_double(-U[e] * inv_s);
+    Tp[2 * e] = p.hi;
+    Tp[2 * e + 1] = p.lo;
+  }
+}
+
 // Z = (V - L T) * scale for the four columns 4 y .. 4 y + 3; one row per
 // thread (V and Z may be the same block: each element is read, then written,
 // by one thread).
@@ -998,6 +1011,28 @@ cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const floa
   count_launch();
   nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
       W.upart, chunks, rank, w_pad, U, nullptr);
+  count_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t nys_apply_m(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
+                        const int* active, cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
+  const int cg = w_pad / 4;
+  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
+  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, cg), 256, 0, st>>>(W.Lt, n_pad, rank, V, w_pad,
+                                                                      W.upart, active);
+  count_launch();
+  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
+      W.upart, chunks, rank, w_pad, W.U, active);
+  count_launch();
+  nys_mneg_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
+      W.U, rank, w_pad, 1.0 / s, W.Tp, active);
+  count_launch();
+  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(
+      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, s, active);
   count_launch();
   return cudaGetLastError();
 }

@@ -118,6 +118,11 @@ cudaError_t nys_probes(const NysWs& W, int rank, int64_t n, double s, const floa
 cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const float* V, double* U,
                          cudaStream_t st);
 
+// Z = M V = s V + L (L^T V) (exact products and pair sums), same conventions
+// as nys_apply; V and Z may not alias.
+cudaError_t nys_apply_m(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
+                        const int* active, cudaStream_t st);
+
 // Z = M^-1 V on padded [n_pad][w_pad] blocks (rows >= n of Z are zero).  If
 // `active` is non-NULL and *active == 0 the kernels exit (converged solves).
 cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,

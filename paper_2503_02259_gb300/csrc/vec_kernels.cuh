@@ -135,7 +135,7 @@ cudaError_t launch_lz_norm_next(CgState* S, const float* W, float* Q, int64_t n_
                                 int j, int k, double* red, cudaStream_t st);
 
 // Lanczos on M^-1/2 Kh M^-1/2 carried in the variables q = M^-1/2 qh, with the
-// M-images P = M Q kept beside the basis Q (so that M is never applied):
+// M-images P = M Q kept beside the basis Q:
 // init: bn2 = z^T M^-1 z (Z = the probe block, V = M^-1 Z), q_0 = V / sqrt(bn2),
 // p_0 = Z / sqrt(bn2).
 cudaError_t launch_lz_init_m(CgState* S, const float* Z, const float* V, float* Q0, float* P0,

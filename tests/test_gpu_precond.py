@@ -189,3 +189,85 @@ def test_refinement_with_the_preconditioner_reaches_1e6(api, prec):
     _, it0, rel0, st0 = api.gp_pcg_solve_refined(_dev(prob.X), _dev(Bm), prob.kind, prob.theta, opts0)
     assert st0 == 0
     assert max(it) * 5 < min(it0), (it, it0)
+
+
+# ------------------------------------- the loss with the preconditioner --
+# Eq. 1 / Eq. 2 with M = s I + L L^T (pivots fixed).  Bounds: log|M| to 1e-7
+# relative (FP64 Cholesky of the exact-sum Gram of the stored factor against
+# the oracle's dense slogdet); tr(M^-1 dM) to 1e-5 relative (dL/dl stored in
+# FP32); loss and gradient to the 1e-4 bound of the unpreconditioned
+# estimator, against the oracle's estimator on the same pivots and normal values.
+
+def _loss_precond(api, prob, rank, p, k, eps=None, tol=0.0, seed=0):
+    # opts holds only the probe block's address: keep the tensor alive for the call.
+    eps_d = None if eps is None else _dev(eps)
+    opts = api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-8, cg_maxit=5000, precond_rank=rank,
+                          precond_tol=tol, probes=eps_d, seed=seed)
+    out = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    del eps_d
+    return out
+
+
+def _pivots(api, prob, rank, tol):
+    _, _, piv, _ = api.gp_nystrom_apply(_dev(prob.X), _dev(prob.y[:, None]), prob.kind, prob.theta,
+                                        rank, tol=tol)
+    return piv
+
+
+def _check_loss(loss, grad, ref_loss, ref_grad):
+    assert abs(loss - ref_loss) <= 1e-4 * abs(ref_loss), (loss, ref_loss)
+    g = np.asarray(grad)
+    scale = np.maximum(np.abs(ref_grad), 1e-3 * np.linalg.norm(ref_grad))
+    assert np.all(np.abs(g - ref_grad) / scale <= 1e-4), (g, ref_grad)
+
+
+@pytest.mark.parametrize("kind,n,d,theta,rank,tol", [
+    (0, 600, 2, (0.05, 1.0, 0.4), 80, 1e-6),
+    (1, 500, 3, (0.05, 1.2, 0.5), 120, 1e-5),
+])
+def test_preconditioned_loss_matches_the_oracle(api, kind, n, d, theta, rank, tol):
+    prob = inputs.uniform_problem(n, d, kind, theta, seed=51)
+    p, k = 8, 25
+    eps = np.random.default_rng(52).standard_normal((n + rank, p)).astype(np.float32)
+    loss, grad, info = _loss_precond(api, prob, rank, p, k, eps=eps, tol=tol)
+    piv = _pivots(api, prob, rank, tol)
+    r = len(piv)
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, prob.theta, piv,
+                            eps[n:n + r].astype(np.float64), eps[:n].astype(np.float64), k)
+    assert abs(info["logdet_m"] - est["logdet_M"]) <= 1e-7 * abs(est["logdet_M"])
+    np.testing.assert_allclose(info["trace_m"], est["trace_M"], rtol=1e-5)
+    _check_loss(loss, grad, est["loss"], est["grad"])
+
+
+def test_preconditioned_loss_with_every_point_a_pivot_is_exact(api):
+    # M = Kh up to the factor's rounding: the stochastic terms vanish for any
+    # probes (generated on the device here) and the estimate is the exact loss.
+    prob = inputs.uniform_problem(250, 3, 1, (0.05, 1.0, 0.3), seed=53)
+    loss, grad, info = _loss_precond(api, prob, 4096, 4, 10, seed=3)
+    ex = O.exact_nll(prob.X, prob.y, prob.kind, prob.theta)
+    _check_loss(loss, grad, ex["loss"], ex["grad"])
+
+
+def test_generated_gaussian_probes_match_the_oracle_generator(api):
+    prob = inputs.uniform_problem(300, 2, 0, (0.05, 1.0, 0.4), seed=54)
+    rank, p, k, seed, tol = 40, 4, 15, 11, 1e-6
+    loss, grad, _ = _loss_precond(api, prob, rank, p, k, tol=tol, seed=seed)
+    piv = _pivots(api, prob, rank, tol)
+    r = len(piv)
+    G = O.gaussian_probes(300 + r, p, seed)
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, prob.theta, piv, G[300:300 + r], G[:300], k)
+    _check_loss(loss, grad, est["loss"], est["grad"])
+
+
+def test_preconditioned_estimator_has_a_smaller_spread(api):
+    # With the spectrum above s covered by the factor, Eq. 1 / Eq. 2's split
+    # leaves stochastic terms with a far smaller spread than M = I, and the
+    # solves take fewer iterations.
+    prob = inputs.uniform_problem(600, 2, 0, (0.05, 1.0, 0.4), seed=51)
+    _, _, ip = _loss_precond(api, prob, 80, 16, 25, tol=1e-6, seed=5)
+    opts = api.solve_opts(nprobe=16, nlanczos=25, cg_rtol=1e-8, cg_maxit=5000, seed=5)
+    _, _, i0 = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    assert ip["logdet_stderr"] < i0["logdet_stderr"] / 3, (ip["logdet_stderr"], i0["logdet_stderr"])
+    for t in range(3):
+        assert ip["trace_stderr"][t] < i0["trace_stderr"][t] / 3, (t, ip["trace_stderr"], i0["trace_stderr"])
+    assert ip["cg_iters"] < i0["cg_iters"]
