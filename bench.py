@@ -512,6 +512,64 @@ def loss_grad_mixed_vs_fp32(api, torch, rates: dict, full_n: int = 200_000) -> d
     return out
 
 
+def loss_grad_precond(api, B, torch, rates: dict, full_n: int = 200_000, rank_sub: int = 800,
+                      rank_full: int = 1500, p: int = 16, k: int = 30, cap_plain: int = 300) -> dict:
+    """Eq. 1 / Eq. 2 with the Nystrom preconditioner on the precision problem's kernel
+    (d = 2 uniform, Gaussian f = 1, l = 0.05, s = 0.01).  On the n = 4000 subsample:
+    the error of the estimate (p probes x k Lanczos steps, CG to 1e-8) against the
+    exact L and dL/dTheta (Cholesky, stored FP64 values) for M = I (Rademacher
+    probes) and for the rank-rank_sub Nystrom M (Gaussian probes z ~ N(0, M)), with
+    the estimator's standard errors.  At n = full_n: the time per Theta with the
+    rank-rank_full preconditioner (CG to 1e-6), its CG iterations and standard
+    errors, against M = I with CG capped at cap_plain iterations (which does not
+    reach 1e-6 there)."""
+    from paper_2503_02259_gb300 import inputs
+    sub = inputs.precision_problem(seed=0, n=4000)
+    refs = _refs()
+    lref, gref = float(refs["preck_loss"]), np.asarray(refs["preck_grad"])
+    floor = 1e-3 * np.linalg.norm(gref)
+    out = {"workload": f"precision problem's kernel; accuracy vs the exact loss and gradient on the "
+                       f"n=4000 subsample ({p} probes x {k} Lanczos steps, CG 1e-8); time at "
+                       f"n={full_n} (CG 1e-6; M = I capped at {cap_plain} CG iterations)"}
+    Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
+    for name, extra in (("m_identity", {}), (f"nystrom_rank{rank_sub}", {"precond_rank": rank_sub})):
+        opts = api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-8, cg_maxit=20000, seed=0, **extra)
+        loss, grad, info = api.gp_loss_and_grad(Xs, ys, sub.kind, sub.theta, opts)
+        out[name] = {"relerr_loss_vs_exact_n4000": abs(loss - lref) / abs(lref),
+                     "relerr_grad_vs_exact_n4000": max(abs(g - r) / max(abs(r), floor)
+                                                       for g, r in zip(grad, gref)),
+                     "logdet_stderr": info["logdet_stderr"], "trace_stderr": info["trace_stderr"],
+                     "cg_iters": info["cg_iters"]}
+    full = inputs.precision_problem(seed=0, n=full_n)
+    Xf, yf = torch.from_numpy(full.X).cuda(), torch.from_numpy(full.y).cuda()
+
+    def timed(opts):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        try:
+            res, st = api.gp_loss_and_grad(Xf, yf, full.kind, full.theta, opts), 0
+        except B.GPError as exc:
+            res, st = None, exc.status
+        torch.cuda.synchronize()
+        return res, st, (time.perf_counter() - t0) * 1e3
+
+    res, st, ms = timed(api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-6, cg_maxit=2000, seed=0,
+                                       precond_rank=rank_full))
+    rec = {"ms_per_theta": ms, "status": st}
+    if res is not None:
+        loss, grad, info = res
+        rec.update({"loss": loss, "grad": grad, "cg_iters": info["cg_iters"],
+                    "relres_max": info["relres_max"], "logdet_stderr": info["logdet_stderr"],
+                    "trace_stderr": info["trace_stderr"], "logdet_m": info["logdet_m"],
+                    "products_roofline": lossgrad_roofline(full_n, 2, False, p, k, info["cg_iters"],
+                                                           ms, rates)})
+    out[f"nystrom_rank{rank_full}_n{full_n}"] = rec
+    _, st0, ms0 = timed(api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-6, cg_maxit=cap_plain, seed=0))
+    out[f"m_identity_n{full_n}_capped"] = {"ms_per_theta": ms0, "cg_iters": cap_plain,
+                                           "status": st0, "converged_to_1e-6": st0 == 0}
+    return out
+
+
 # (name, CG arithmetic, SLQ arithmetic, max_batch): max_batch > 1 runs compatible
 # loss + gradient requests as batches with one grouped product launch per step.
 SERVING_ARMS = (("fp32", 0, 0, 1), ("bf16x3_slq_tf32x3", 4, 3, 1))
@@ -697,6 +755,8 @@ def run_leg(args) -> int:
         out = precision_refinement(api, B, torch, n=args.precision_n)
     elif args.leg == "loss_grad_mixed_vs_fp32":
         out = loss_grad_mixed_vs_fp32(api, torch, rates)
+    elif args.leg == "loss_grad_precond":
+        out = loss_grad_precond(api, B, torch, rates)
     elif args.leg == "serving_accuracy":
         out = serving_accuracy(torch)
     else:
@@ -724,7 +784,7 @@ def main() -> int:
                          "profiling; the full run always uses 1e6)")
     ap.add_argument("--leg", default=None,
                     choices=["loss_grad", "precision_modes", "precision_config", "refinement",
-                             "precision_refinement",
+                             "precision_refinement", "loss_grad_precond",
                              "loss_grad_mixed_vs_fp32", "serving", "serving_accuracy"],
                     help="run one extra leg alone on cuda:0 and print its JSON (for profiling)")
     args = ap.parse_args()
@@ -839,6 +899,7 @@ def main() -> int:
                 ("refinement", lambda: refinement(api, torch)),
                 ("precision_refinement", lambda: precision_refinement(api, B, torch)),
                 ("loss_grad_mixed_vs_fp32", lambda: loss_grad_mixed_vs_fp32(api, torch, rates)),
+                ("loss_grad_precond", lambda: loss_grad_precond(api, B, torch, rates)),
                 ("serving", lambda: serving(torch, count=args.serving_requests,
                                             precs=SERVING_ARMS_ALL if args.serving_all_arms
                                             else SERVING_ARMS)),

@@ -19,7 +19,10 @@ Contents
       probes from seed 0, 20 Lanczos steps, exact solves) of the loss+grad
       requests and the posterior mean at the first 200 test points (exact
       solve) of the predictions; NaN where a field does not apply;
-      serving_kappa: the condition number of each request's Kh (eigvalsh).
+      serving_kappa: the condition number of each request's Kh (eigvalsh);
+  preck_loss, preck_grad: the exact L and dL/d(s, f, l) (Cholesky) on the
+      n = 4000 subsample of the precision problem (d = 2, Gaussian l = 0.05,
+      s = 0.01), for the preconditioned-loss leg.
 """
 import os
 import sys
@@ -56,6 +59,12 @@ def diff_refs():
     sub = inputs.diff_problem(seed=0, n=4000)
     est = O.est_nll(sub.X, sub.y, sub.kind, sub.theta, O.rademacher_probes(sub.n, 32, 77), 40)
     return float(est["loss"]), np.asarray(est["grad"], dtype=np.float64)
+
+
+def preck_refs():
+    sub = inputs.precision_problem(seed=0, n=4000)
+    ex = O.exact_nll(sub.X, sub.y, sub.kind, sub.theta)
+    return float(ex["loss"]), np.asarray(ex["grad"], dtype=np.float64)
 
 
 SERVING_NMAX = 3000
@@ -95,10 +104,11 @@ def main():
     pr, pY = precision_refs()
     dl, dg = diff_refs()
     si, sl, sg, smu, sk = serving_refs()
+    pl, pg = preck_refs()
     np.savez_compressed(OUT, matvec_rows=mr, matvec_Y=mY, matvec_L=mL, precision_rows=pr,
                         precision_Y=pY, diff_loss=np.float64(dl), diff_grad=dg, serving_idx=si,
                         serving_loss=sl, serving_grad=sg, serving_mu=smu,
-                        serving_kappa=sk)
+                        serving_kappa=sk, preck_loss=np.float64(pl), preck_grad=pg)
     print("wrote", OUT)
 
 

@@ -69,3 +69,11 @@ def test_serving_condition_numbers_are_the_oracles():
     p = reqs[int(refs["serving_idx"][k])].problem
     ev = np.linalg.eigvalsh(O.khat_dense(p.X, p.kind, p.theta))
     assert ev[-1] / ev[0] == pytest.approx(float(refs["serving_kappa"][k]), rel=1e-9)
+
+
+def test_precision_subsample_exact_loss_is_the_oracles():
+    refs = np.load(REFS)
+    sub = inputs.precision_problem(seed=0, n=4000)
+    ex = O.exact_nll(sub.X, sub.y, sub.kind, sub.theta)
+    assert abs(ex["loss"] - float(refs["preck_loss"])) <= 1e-9 * abs(ex["loss"])
+    np.testing.assert_allclose(ex["grad"], refs["preck_grad"], rtol=1e-9, atol=0)
