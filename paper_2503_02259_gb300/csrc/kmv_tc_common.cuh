@@ -69,6 +69,23 @@ struct TcGeom {
   static constexpr uint32_t A_BYTES = (kTcM / 8) * SBO;
 };
 
+// Split BF16 can keep the A operand (the evaluated kernel tile) in tensor
+// memory instead of shared memory: each eval thread writes its row's entries
+// with tcgen05.st, two BF16 values per 32-bit column (the lower K index in the
+// low half), and the MMA reads A from there, which removes the core-matrix
+// shared-memory stores of A.  It costs 128 tensor-memory columns per CTA (two
+// stages x K and D x hi and lo x 16), so the host takes it per launch only
+// where it keeps as many CTAs resident as the shared-memory form (measured at
+// n = 1e5, w = 32 with the gradient: 8.22 ms against 8.88).  Plain BF16 (three
+// CTAs per SM with A in shared memory: 5.83 ms, against 6.80 with A in tensor
+// memory and two CTAs) and the TF32 modes (4-byte elements) keep A in shared
+// memory.
+template <int MODE>
+struct TcATmem {
+  static constexpr bool ON = MODE == kTcBF16x3;
+  static constexpr int COLS = TcGeom<MODE>::BK / 2;   // columns per A matrix per stage
+};
+
 namespace tc {
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
@@ -78,6 +95,17 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint
   d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
   d |= static_cast<uint64_t>(1) << 46;  // descriptor version of tcgen05
   return d;                             // base offset 0, layout: no swizzle
+}
+
+// A in tensor memory: tcgen05.mma reads A from [atmem] (M rows = lanes 0..127).
+template <int MODE>
+__device__ __forceinline__ void mma_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc,
+                                       uint32_t acc) {
+  static_assert(TcTraits<MODE>::FMT == 1, "A from tensor memory: BF16 modes only");
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtmem),
+      "r"(atmem), "l"(bdesc), "r"(idesc), "r"(acc));
 }
 
 template <int MODE>
@@ -138,6 +166,12 @@ __device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16]) {
       "r"(r[15]));
 }
 
+__device__ __forceinline__ void st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]));
+}
+
 __device__ __forceinline__ void wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
@@ -185,6 +219,23 @@ __device__ __forceinline__ void store_group(unsigned char* hi, unsigned char* lo
   }
 }
 
+// BF16 packing of 8 entries (4 pairs) into 4 words of hi and, when SPLIT, 4
+// words of the rounded remainder lo (the arithmetic of store_group's BF16 path).
+template <bool SPLIT>
+__device__ __forceinline__ void pack_bf16(const float2 (&v)[4], uint32_t* h, uint32_t* l) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(v[u].x, v[u].y);
+    h[u] = *reinterpret_cast<const uint32_t*>(&p);
+    if constexpr (SPLIT) {
+      const float2 r = __ffma2_rn(__bfloat1622float2(p), m1, v[u]);
+      const __nv_bfloat162 q = __floats2bfloat162_rn(r.x, r.y);
+      l[u] = *reinterpret_cast<const uint32_t*>(&q);
+    }
+  }
+}
+
 }  // namespace tc
 
 // Shared-memory plan of one launch (host and device agree on it).
@@ -194,7 +245,7 @@ struct TcSmem {
 };
 
 template <int MODE, int DT>
-__host__ __device__ inline TcSmem tc_smem(int n, bool grad, int nbs) {
+__host__ __device__ inline TcSmem tc_smem(int n, bool grad, int nbs, bool atm = false) {
   using G = TcGeom<MODE>;
   constexpr int DP = DimTraits<DT>::DP;
   TcSmem s;
@@ -205,13 +256,21 @@ __host__ __device__ inline TcSmem tc_smem(int n, bool grad, int nbs) {
   s.sx = 128;
   s.sb = s.sx + ((nbs * s.xbytes + 127) / 128) * 128;
   s.sa = s.sb + nbs * TcTraits<MODE>::NSB * s.bbytes;
-  s.total = s.sa + kTcAStages * (grad ? 2 : 1) * TcTraits<MODE>::NSA * s.abytes;
+  s.total = s.sa + ((TcATmem<MODE>::ON && atm)
+                         ? 0u
+                         : kTcAStages * (grad ? 2 : 1) * TcTraits<MODE>::NSA * s.abytes);
   return s;
 }
 
-// Tensor-memory columns: accumulators [0, NMAT*n) and running sums [NMAT*n, 2*NMAT*n).
-__host__ __device__ inline uint32_t tc_tmem_cols(int n, bool grad) {
-  const int need = 2 * (grad ? 2 : 1) * n;
+// Tensor-memory columns: accumulators [0, NMAT*n), running sums [NMAT*n,
+// 2*NMAT*n), then (BF16 modes) the A stages, kTcAStages x NMAT x NSA matrices
+// of TcATmem::COLS columns.
+template <int MODE>
+__host__ __device__ inline uint32_t tc_tmem_cols(int n, bool grad, bool atm = false) {
+  const int nmat = grad ? 2 : 1;
+  int need = 2 * nmat * n;
+  if (TcATmem<MODE>::ON && atm)
+    need += kTcAStages * nmat * TcTraits<MODE>::NSA * TcATmem<MODE>::COLS;
   uint32_t c = 32;
   while (c < static_cast<uint32_t>(need)) c <<= 1;
   return c;

@@ -47,12 +47,14 @@ __global__ void tc_stage_v_kernel(const float* v, int n, int jtiles, unsigned ch
   }
 }
 
-template <int KIND, bool GRAD, int DT>
+// The instantiation with A in shared memory (ATM = false) or, for split BF16,
+// in tensor memory (ATM = true; other modes map it to the shared-memory one).
+template <int KIND, bool GRAD, int DT, bool ATM>
 auto kernel_ptr() {
-  return kmv_tc_kernel<KIND, GRAD, DT, MODE>;
+  return kmv_tc_kernel<KIND, GRAD, DT, MODE, ATM && TcATmem<MODE>::ON>;
 }
 
-template <int KIND, bool GRAD, int DT>
+template <int KIND, bool GRAD, int DT, bool ATM>
 cudaError_t ensure_attr() {
   static std::atomic<uint64_t> done{0};
   int dev = 0;
@@ -60,8 +62,8 @@ cudaError_t ensure_attr() {
   if (e != cudaSuccess) return e;
   const uint64_t bit = 1ull << (dev & 63);
   if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel_ptr<KIND, GRAD, DT>(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           227 * 1024);
+  e = cudaFuncSetAttribute(kernel_ptr<KIND, GRAD, DT, ATM>(),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
   return e;
 }
@@ -70,45 +72,55 @@ template <int KIND, bool GRAD, int DT>
 cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
   const int n = p.w_pad;
   if (n > 128 || n < 16 || (n & 15)) return cudaErrorNotSupported;
-  cudaError_t e = ensure_attr<KIND, GRAD, DT>();
+  cudaError_t e = ensure_attr<KIND, GRAD, DT, false>();
   if (e != cudaSuccess) return e;
-  const uint32_t cols = tc_tmem_cols(n, GRAD);
-  if (cols > 512) return cudaErrorNotSupported;
-  // Resident CTAs must fit the 512 tensor-memory columns of an SM.
-  const int max_ctas = static_cast<int>(512 / cols);
-  // Copy-ring depth: the one (2..kTcBStages stages) that lets the most CTAs
-  // reside on an SM, the deepest among those.  A tile's copies (points and one
-  // B slice, a few KB from L2) land within a fraction of the time the eval
-  // warps spend on one tile, so two stages suffice to hide them, while one
-  // more resident CTA adds eval warps to hide the evaluation's latencies.
+  if (TcATmem<MODE>::ON && (e = ensure_attr<KIND, GRAD, DT, true>()) != cudaSuccess) return e;
+  // Per form of the A operand (shared memory; for split BF16 also tensor
+  // memory) and copy-ring depth (2..kTcBStages stages): the resident CTAs per
+  // SM, bounded by the 512 tensor-memory columns.  The choice keeps the most
+  // resident CTAs, then A in tensor memory (fewer shared-memory stores), then
+  // the deepest ring.  A tile's copies (points and one B slice, a few KB from
+  // L2) land within a fraction of the time the eval warps spend on one tile,
+  // so two stages suffice to hide them, while one more resident CTA adds eval
+  // warps to hide the evaluation's latencies.
   int nbs = 0, best_occ = 0;
-  for (int b = kTcBStages; b >= 2; --b) {
-    const TcSmem Lb = tc_smem<MODE, DT>(n, GRAD, b);
-    if (Lb.total > 227u * 1024u) continue;
-    int occ_b = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, kernel_ptr<KIND, GRAD, DT>(),
-                                                      kTcThreads, Lb.total);
-    if (e != cudaSuccess) return e;
-    occ_b = std::min(occ_b, max_ctas);
-    if (occ_b > best_occ) {
-      best_occ = occ_b;
-      nbs = b;
+  bool atm = false;
+  uint32_t cols = 0;
+  for (int form = TcATmem<MODE>::ON ? 1 : 0; form >= 0; --form) {
+    const bool f_atm = form == 1;
+    const auto f_fn = f_atm ? kernel_ptr<KIND, GRAD, DT, true>() : kernel_ptr<KIND, GRAD, DT, false>();
+    const uint32_t f_cols = tc_tmem_cols<MODE>(n, GRAD, f_atm);
+    if (f_cols > 512) continue;
+    const int f_max = static_cast<int>(512 / f_cols);
+    for (int b = kTcBStages; b >= 2; --b) {
+      const TcSmem Lb = tc_smem<MODE, DT>(n, GRAD, b, f_atm);
+      if (Lb.total > 227u * 1024u) continue;
+      int occ_b = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_b, f_fn, kTcThreads, Lb.total);
+      if (e != cudaSuccess) return e;
+      occ_b = std::min(occ_b, f_max);
+      if (occ_b > best_occ) {
+        best_occ = occ_b;
+        nbs = b;
+        atm = f_atm;
+        cols = f_cols;
+      }
     }
   }
   if (nbs == 0) return cudaErrorNotSupported;
-  const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs);
+  const int max_ctas = static_cast<int>(512 / cols);
+  const auto fn = atm ? kernel_ptr<KIND, GRAD, DT, true>() : kernel_ptr<KIND, GRAD, DT, false>();
+  const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs, atm);
   // Reserve extra shared memory when the occupancy would otherwise exceed the
   // tensor-memory bound.
   size_t smem = L.total;
   int occ = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_ptr<KIND, GRAD, DT>(), kTcThreads,
-                                                    smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTcThreads, smem);
   if (e != cudaSuccess) return e;
   while (occ > max_ctas && smem < 227u * 1024u) {
     smem += 8 * 1024;
     if (smem > 227u * 1024u) smem = 227u * 1024u;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel_ptr<KIND, GRAD, DT>(), kTcThreads,
-                                                      smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTcThreads, smem);
     if (e != cudaSuccess) return e;
   }
   if (occ < 1 || occ > max_ctas) return cudaErrorNotSupported;
@@ -130,7 +142,6 @@ cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
                          (static_cast<uint32_t>(n >> 3) << 17) |
                          (static_cast<uint32_t>(kTcM >> 4) << 24);
   dim3 grid(p.row_tiles, p.split);
-  auto fn = kernel_ptr<KIND, GRAD, DT>();
   profile_product_begin(st);
   fn<<<grid, kTcThreads, smem, st>>>(a, n, p.nr_pad, p.jtiles, p.jt_per_split, idesc, cols, nbs);
   profile_product_end(st);

@@ -57,11 +57,11 @@ __device__ __forceinline__ void arrive(uint64_t* bar) {
 
 }  // namespace tc
 
-template <int KIND, bool GRAD, int DT, int MODE>
+template <int KIND, bool GRAD, int DT, int MODE, bool ATM_T>
 // Plain BF16 needs little shared memory, so it can keep three CTAs per SM if
 // the registers allow (<= 72 per thread at 288 threads); the other modes are
-// limited to one or two CTAs by shared memory and keep the compiler's own
-// register choice (each instantiation unit compiles one mode).
+// limited to one or two CTAs by shared or tensor memory and keep the
+// compiler's own register choice (each instantiation unit compiles one mode).
 #if defined(GP_TC_MODE) && GP_TC_MODE == 2
 #define GP_TC_BOUNDS __launch_bounds__(kTcThreads, 3)
 #else
@@ -71,7 +71,8 @@ __global__ void GP_TC_BOUNDS
     kmv_tc_kernel(TcArgs a, int n_cols, int64_t nr_pad, int jtiles, int jt_per_split,
                   uint32_t idesc, uint32_t tmem_cols, int nbs) {
   // nbs: stages of the point / B-operand ring, 2 <= nbs <= kTcBStages (host-chosen
-  // to fit shared memory).
+  // to fit shared memory).  ATM_T: A in tensor memory (split BF16 only; the host
+  // chooses the instantiation per launch).
   using G = TcGeom<MODE>;
   constexpr int DP = DimTraits<DT>::DP;
   constexpr int NSA = TcTraits<MODE>::NSA;
@@ -80,11 +81,13 @@ __global__ void GP_TC_BOUNDS
   constexpr int EPC = G::EPC;
   constexpr int NMAT = GRAD ? 2 : 1;
   constexpr int HALF_CK = G::CK / 2;
+  constexpr bool ATM = TcATmem<MODE>::ON && ATM_T;   // A operand in tensor memory
+  constexpr uint32_t ACOLS = TcATmem<MODE>::COLS;
 
   if (a.active != nullptr && *a.active == 0) return;
 
   extern __shared__ __align__(1024) unsigned char smem[];
-  const TcSmem L = tc_smem<MODE, DT>(n_cols, GRAD, nbs);
+  const TcSmem L = tc_smem<MODE, DT>(n_cols, GRAD, nbs, ATM);
   uint64_t* fullX = reinterpret_cast<uint64_t*>(smem + L.bars);  // [nbs] points + B landed
   uint64_t* emptyX = fullX + kTcBStages;                          // [nbs] MMA done with stage
   uint64_t* fullA = emptyX + kTcBStages;                          // [2] A written (256 arrivals)
@@ -108,6 +111,11 @@ __global__ void GP_TC_BOUNDS
   const int jt1 = min(jt0 + jt_per_split, jtiles);
   const int T = jt1 - jt0;
   const int acc_cols = NMAT * n_cols;    // accumulator columns = running-sum columns
+  // Tensor-memory column of A matrix (stage, K or D, hi or lo) when ATM.
+  auto a_col = [&](int st, int mat, int part) -> uint32_t {
+    return static_cast<uint32_t>(2 * acc_cols) +
+           static_cast<uint32_t>((st * NMAT + mat) * NSA + part) * ACOLS;
+  };
 
   if (tid == 0) {
     for (int i = 0; i < kTcBStages; ++i) {
@@ -163,10 +171,13 @@ __global__ void GP_TC_BOUNDS
       if (ok && t >= kTcAStages)
         ok = tc::wait_or_abort(&emptyA[as], ((t - kTcAStages) / kTcAStages) & 1, abort_s);
       if (!ok) break;
+      if constexpr (ATM) tc::fence_after();   // the MMAs that read this A stage are complete
       const float* xs = sX + bs * (L.xbytes / 4);
       const int jo = ((jt0 + t) * G::BK) & (kTcBK - 1);   // the tile's offset in its point tile
       unsigned char* aK = sA + (as * NMAT * NSA) * L.abytes;
       unsigned char* aD = aK + NSA * L.abytes;
+      // ATM: this thread's 16 entries of its row as 8 packed words per matrix.
+      uint32_t wK[ATM ? 2 : 1][8], wD[ATM ? 2 : 1][8];
 #pragma unroll
       for (int kh = 0; kh < HALF_CK; ++kh) {
         const int kg = half * HALF_CK + kh;
@@ -179,11 +190,28 @@ __global__ void GP_TC_BOUNDS
           eval_pair<KIND, GRAD>(q01, kv[2 * u], dv[2 * u]);
           eval_pair<KIND, GRAD>(q23, kv[2 * u + 1], dv[2 * u + 1]);
         }
-        const uint32_t off = rowoff + static_cast<uint32_t>(kg) * G::LBO;
-        tc::store_group<MODE, (NSA == 2)>(aK, aK + L.abytes, off, kv);
-        if constexpr (GRAD) tc::store_group<MODE, (NSA == 2)>(aD, aD + L.abytes, off, dv);
+        if constexpr (ATM) {
+          tc::pack_bf16<true>(kv, &wK[0][4 * kh], &wK[1][4 * kh]);
+          if constexpr (GRAD) tc::pack_bf16<true>(dv, &wD[0][4 * kh], &wD[1][4 * kh]);
+        } else {
+          const uint32_t off = rowoff + static_cast<uint32_t>(kg) * G::LBO;
+          tc::store_group<MODE, (NSA == 2)>(aK, aK + L.abytes, off, kv);
+          if constexpr (GRAD) tc::store_group<MODE, (NSA == 2)>(aD, aD + L.abytes, off, dv);
+        }
       }
-      tc::fence_proxy_async();
+      if constexpr (ATM) {
+        static_assert(HALF_CK == 2 && NSA == 2, "A in tensor memory: 16 entries, hi and lo");
+        const uint32_t lcol = lane_base + static_cast<uint32_t>(half * 8);
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          tc::st8(tmem + lcol + a_col(as, 0, part), wK[part]);
+          if constexpr (GRAD) tc::st8(tmem + lcol + a_col(as, 1, part), wD[part]);
+        }
+        tc::wait_st();
+        tc::fence_before();
+      } else {
+        tc::fence_proxy_async();
+      }
       tc::arrive(&fullA[as]);
       if (t > 0 && t % G::FLUSH == 0) {
         // Fold the block that ended at tile t-1 once its MMAs are complete.
@@ -287,10 +315,19 @@ __global__ void GP_TC_BOUNDS
           const uint64_t am = (pr == 2) ? 1u : 0u;
           const uint64_t bm = (pr == 1) ? 1u : 0u;
           const uint64_t bdesc = db + ((bm * L.bbytes) >> 4) + ko;
-          tc::mma<MODE>(tmem, da + ((am * L.abytes) >> 4) + ko, bdesc, idesc, acc);
-          if constexpr (GRAD)
-            tc::mma<MODE>(tmem + static_cast<uint32_t>(n_cols),
-                          da + (((NSA + am) * L.abytes) >> 4) + ko, bdesc, idesc, acc);
+          if constexpr (ATM) {
+            // One MMA takes 16 K values = 8 columns of the A matrix.
+            const uint32_t kc = static_cast<uint32_t>(ks * 8);
+            tc::mma_ts<MODE>(tmem, tmem + a_col(as, 0, static_cast<int>(am)) + kc, bdesc, idesc, acc);
+            if constexpr (GRAD)
+              tc::mma_ts<MODE>(tmem + static_cast<uint32_t>(n_cols),
+                               tmem + a_col(as, 1, static_cast<int>(am)) + kc, bdesc, idesc, acc);
+          } else {
+            tc::mma<MODE>(tmem, da + ((am * L.abytes) >> 4) + ko, bdesc, idesc, acc);
+            if constexpr (GRAD)
+              tc::mma<MODE>(tmem + static_cast<uint32_t>(n_cols),
+                            da + (((NSA + am) * L.abytes) >> 4) + ko, bdesc, idesc, acc);
+          }
           acc = 1u;
         }
       }
