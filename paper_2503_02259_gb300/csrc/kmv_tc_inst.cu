@@ -111,19 +111,23 @@ cudaError_t launch_one(const SimtPlan& p, const TcArgs& a, cudaStream_t st) {
   const int max_ctas = static_cast<int>(512 / cols);
   const auto fn = atm ? kernel_ptr<KIND, GRAD, DT, true>() : kernel_ptr<KIND, GRAD, DT, false>();
   const TcSmem L = tc_smem<MODE, DT>(n, GRAD, nbs, atm);
-  // Reserve extra shared memory when the occupancy would otherwise exceed the
-  // tensor-memory bound.
+  // Reserve shared memory so that no more CTAs reside on an SM than its 512
+  // tensor-memory columns hold: a CTA beyond them would only wait in
+  // tcgen05.alloc.  The bound is set from the SM's 228 KB (1 KB of it reserved
+  // per CTA) rather than from the occupancy query, which counted two CTAs
+  // where three were placed when the A operand left shared memory.
   size_t smem = L.total;
+  {
+    const size_t per_sm = 228u * 1024u;
+    // (smem + 1 KB) x (max_ctas + 1) > 228 KB.
+    const size_t floor_smem = per_sm / static_cast<size_t>(max_ctas + 1) + 1;
+    smem = std::max(smem, floor_smem);
+    if (smem > 227u * 1024u) smem = 227u * 1024u;
+  }
   int occ = 0;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTcThreads, smem);
   if (e != cudaSuccess) return e;
-  while (occ > max_ctas && smem < 227u * 1024u) {
-    smem += 8 * 1024;
-    if (smem > 227u * 1024u) smem = 227u * 1024u;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kTcThreads, smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (occ < 1 || occ > max_ctas) return cudaErrorNotSupported;
+  if (occ < 1) return cudaErrorNotSupported;
   // Stage V as the B operand.
   {
     const int64_t total = static_cast<int64_t>(p.jtiles) * n * G::CK;
