@@ -9,9 +9,12 @@
 //  - kResPair: FP32-pair ("double-float") arithmetic of pair_arith.cuh: the
 //    squared distance from the exact differences of the FP32 points, the
 //    kernel entry by the table-driven pair exponential, the products K X[j] as
-//    pairs, and compensated sums (a two-sum accumulator per 64-point tile,
+//    pairs, and compensated sums (two-sum accumulators per 64-point tile,
 //    renormalised every four entries, added into a running pair sum), about
-//    1e-14 relative per entry on the FP32 pipe.
+//    1e-14 relative per entry on the FP32 pipe.  Two column points are taken
+//    per step in packed FP32x2 arithmetic (pair_arith2.cuh: each lane rounds
+//    exactly as the scalar form), with one accumulator per lane, the two
+//    lanes added at the end of each tile.
 // Every block takes 128 rows k (one thread each), CW columns and one j range
 // (split s); partial sums go to part[s][k][c] as FP64 values (a pair converts
 // exactly) and a combine kernel sums the splits in a fixed order.
@@ -19,6 +22,7 @@
 
 #include "gp_internal.cuh"
 #include "pair_arith.cuh"
+#include "pair_arith2.cuh"
 
 namespace gp {
 
@@ -138,27 +142,30 @@ __global__ void __launch_bounds__(kResRows) residual_kernel(ResArgs a, pa::ExpCo
       }
     } else {
       const float2* sv = reinterpret_cast<const float2*>(sv_raw);
+      pa2::fp2 tacc2[CW];
+#pragma unroll
+      for (int cc = 0; cc < CW; ++cc) tacc2[cc] = {pa2::bc(0.0f), pa2::bc(0.0f)};
       for (int jj = 0; jj < kResTile; jj += 4) {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const pa::fpair r2 = pa::sqdist<DMAX>(xi, sx + (jj + u) * DMAX, d);
-          const pa::fpair kv = pa::kernel_entry(r2, a.kernel, a.kc, sC);
+        for (int u = 0; u < 4; u += 2) {
+          // Entries jj + u (lane 0) and jj + u + 1 (lane 1).
+          const pa2::fp2 r2 =
+              pa2::sqdist<DMAX>(xi, sx + (jj + u) * DMAX, sx + (jj + u + 1) * DMAX, d);
+          const pa2::fp2 kv = pa2::kernel_entry(r2, a.kernel, a.kc, sC);
 #pragma unroll
           for (int cc = 0; cc < CW; ++cc) {
-            const float2 xv = sv[(jj + u) * CW + cc];
-            const pa::fpair p = pa::mul(kv, pa::fpair{xv.x, xv.y});
-            const pa::fpair t2 = pa::two_sum(tacc[cc].hi, p.hi);
-            tacc[cc] = {t2.hi, pa::add(tacc[cc].lo, pa::add(t2.lo, p.lo))};
+            const float2 xa = sv[(jj + u) * CW + cc], xb = sv[(jj + u + 1) * CW + cc];
+            const pa2::fp2 p = pa2::mul(kv, pa2::fp2{make_float2(xa.x, xb.x), make_float2(xa.y, xb.y)});
+            const pa2::fp2 t2 = pa2::two_sum(tacc2[cc].hi, p.hi);
+            tacc2[cc] = {t2.hi, pa2::add(tacc2[cc].lo, pa2::add(t2.lo, p.lo))};
           }
         }
 #pragma unroll
-        for (int cc = 0; cc < CW; ++cc) tacc[cc] = pa::two_sum(tacc[cc].hi, tacc[cc].lo);
+        for (int cc = 0; cc < CW; ++cc) tacc2[cc] = pa2::two_sum(tacc2[cc].hi, tacc2[cc].lo);
       }
 #pragma unroll
-      for (int cc = 0; cc < CW; ++cc) {
-        run[cc] = pa::add(run[cc], tacc[cc]);
-        tacc[cc] = {0.0f, 0.0f};
-      }
+      for (int cc = 0; cc < CW; ++cc)
+        run[cc] = pa::add(run[cc], pa::add(pa2::lane(tacc2[cc], 0), pa2::lane(tacc2[cc], 1)));
     }
   }
   if (k < a.m_pad) {
