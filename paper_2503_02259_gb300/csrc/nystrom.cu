@@ -25,7 +25,9 @@ constexpr int kStepRowsPerBlock = kStepThreads * kStepRows;
 constexpr int kStepBatch = 8;                     // columns of L loaded ahead per thread
 constexpr int kGT = 64;                           // Gram tile (columns of L)
 constexpr int kGK = 32;                           // Gram rows per shared-memory slab
-constexpr int kLtvChunk = 4096;                   // rows per block of L^T V
+constexpr int kLtvChunk = 4096;                   // rows per block of L^T V (chunk bound of upart)
+constexpr int kLtM = 128;                         // columns of L per block of the tiled L^T V
+constexpr int kLtC = 8;                           // columns of V per block of the tiled L^T V
 constexpr int kZTile = 512;                       // rows of T staged per pass of the Z kernel
 constexpr int kInvWarps = 2;                      // columns of C^-1 per block
 constexpr int kRedCap = 152 * 16;                 // blocks of a grid_for reduction
@@ -630,41 +632,62 @@ __global__ void nys_inverse_kernel(const double* C, int r, double* Winv) {
 
 // ------------------------------------------------------------------ apply --
 
-// Partial sums of U = L^T V over a chunk of rows: warp w of block (x, y, z)
-// covers columns m0 .. m0 + 7 of L (m0 = 64 y + 8 w) and the four V columns
-// 4 z .. 4 z + 3; lanes stride the rows.
+// Partial sums of U = L^T V over a chunk of rows, tiled through shared memory
+// like the Gram kernel: block (x, y, z) covers columns kLtM y .. of L (rows of
+// Lt) and the kLtC columns kLtC z .. of V over its chunk of rows, in slabs of
+// kGK rows; thread t accumulates column m = t / 2 of L against four columns of
+// V (Dot2, renormalised per slab).
 __global__ void __launch_bounds__(256)
-    nys_ltv_kernel(const float* __restrict__ Lt, int64_t n_pad, int r, const float* __restrict__ V,
-                   int w_pad, double* upart, const int* active) {
+    nys_ltv_tiled_kernel(const float* __restrict__ Lt, int64_t n_pad, int r,
+                         const float* __restrict__ V, int w_pad, int64_t rows_per_chunk,
+                         double* upart, const int* active) {
   if (active != nullptr && *active == 0) return;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * 64 + warp * 8;
-  if (m0 >= r) return;
-  const int c0 = blockIdx.z * 4;
-  const int64_t i_begin = static_cast<int64_t>(blockIdx.x) * kLtvChunk;
-  const int64_t i_end = i_begin + kLtvChunk < n_pad ? i_begin + kLtvChunk : n_pad;
-  pa::fpair acc[8][4] = {};
-  for (int64_t i = i_begin + lane; i < i_end; i += 32) {
-    const float4 v = *reinterpret_cast<const float4*>(V + i * w_pad + c0);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      if (m0 + q < r) {
-        const float l = Lt[static_cast<int64_t>(m0 + q) * n_pad + i];
-        acc_prod(acc[q][0], l, v.x);
-        acc_prod(acc[q][1], l, v.y);
-        acc_prod(acc[q][2], l, v.z);
-        acc_prod(acc[q][3], l, v.w);
-      }
+  __shared__ __align__(16) float As[kGK][kLtM + 4];
+  __shared__ __align__(16) float Bs[kGK][kLtC];
+  const int m0 = blockIdx.y * kLtM, c0 = blockIdx.z * kLtC;
+  const int64_t i_begin = static_cast<int64_t>(blockIdx.x) * rows_per_chunk;
+  const int64_t i_end = i_begin + rows_per_chunk < n_pad ? i_begin + rows_per_chunk : n_pad;
+  const int tm = threadIdx.x >> 1, tc = (threadIdx.x & 1) * 4;
+  pa::fpair acc[4] = {};
+  for (int64_t i0 = i_begin; i0 < i_end; i0 += kGK) {
+    for (int q = threadIdx.x; q < kLtM * (kGK / 4); q += blockDim.x) {
+      const int mm = q / (kGK / 4), part = q % (kGK / 4);
+      const int m = m0 + mm;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (m < r) v = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(m) * n_pad + i0 + part * 4);
+      As[part * 4 + 0][mm] = v.x;
+      As[part * 4 + 1][mm] = v.y;
+      As[part * 4 + 2][mm] = v.z;
+      As[part * 4 + 3][mm] = v.w;
     }
+    if (threadIdx.x < kGK * (kLtC / 4)) {
+      const int ii = threadIdx.x / (kLtC / 4), h = threadIdx.x % (kLtC / 4);
+      const int c = c0 + h * 4;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c < w_pad) v = *reinterpret_cast<const float4*>(V + (i0 + ii) * w_pad + c);
+      *reinterpret_cast<float4*>(&Bs[ii][h * 4]) = v;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int ii = 0; ii < kGK; ++ii) {
+      const float a = As[ii][tm];
+      const float4 b = *reinterpret_cast<const float4*>(&Bs[ii][tc]);
+      acc_prod(acc[0], a, b.x);
+      acc_prod(acc[1], a, b.y);
+      acc_prod(acc[2], a, b.z);
+      acc_prod(acc[3], a, b.w);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) renorm(acc[q]);
+    __syncthreads();
   }
+  const int m = m0 + tm;
+  const int c = c0 + tc;
+  if (m < r && c < w_pad) {
+    double* out = upart + (static_cast<int64_t>(blockIdx.x) * r + m) * w_pad + c;
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-#pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      const pa::fpair s = warp_sum_pair(acc[q][cc]);
-      if (lane == 0 && m0 + q < r)
-        upart[(static_cast<int64_t>(blockIdx.x) * r + m0 + q) * w_pad + c0 + cc] = pa::to_double(s);
-    }
+    for (int q = 0; q < 4; ++q) out[q] = pa::to_double(acc[q]);
+  }
 }
 
 __global__ void nys_u_reduce_kernel(const double* upart, int chunks, int r, int w_pad, double* U,
@@ -977,6 +1000,27 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
   return cudaSuccess;
 }
 
+// U = Lm^T V for Lm = L or dL/dl: the tiled partial sums over row chunks (as
+// many chunks as keep about four blocks per SM busy, within upart's
+// allocation), then their fixed-order sum.
+static cudaError_t ltv_into(const NysWs& W, const float* Lm, int rank, const float* V, double* U,
+                           const int* active, cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  const int mt = (rank + kLtM - 1) / kLtM, ct = (w_pad + kLtC - 1) / kLtC;
+  const int64_t max_chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(max_chunks, (608 + mt * ct - 1) / (mt * ct)));
+  const int64_t rpc = round_up64((n_pad + G - 1) / G, kGK);
+  const int chunks = static_cast<int>((n_pad + rpc - 1) / rpc);
+  nys_ltv_tiled_kernel<<<dim3(chunks, mt, ct), 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, rpc, W.upart,
+                                                             active);
+  count_launch();
+  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
+      W.upart, chunks, rank, w_pad, U, active);
+  count_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t nys_closed_terms(const NysWs& W, int rank, int64_t n, double s, double f,
                              double* logdet_m, double* trm, cudaStream_t st) {
   nys_terms_kernel<<<1, 32, 0, st>>>(W.S, n, rank, s, f, logdet_m, trm);
@@ -1001,18 +1045,9 @@ cudaError_t nys_probes(const NysWs& W, int rank, int64_t n, double s, const floa
 
 cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const float* V, double* U,
                          cudaStream_t st) {
-  const int64_t n_pad = W.n_pad;
-  const int w_pad = W.w_pad;
-  if (rank < 1 || rank > W.kmax || w_pad % 4 != 0 || (deriv_matrix && !W.deriv))
+  if (rank < 1 || rank > W.kmax || W.w_pad % 4 != 0 || (deriv_matrix && !W.deriv))
     return cudaErrorInvalidValue;
-  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
-  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, w_pad / 4), 256, 0, st>>>(
-      deriv_matrix ? W.Ldt : W.Lt, n_pad, rank, V, w_pad, W.upart, nullptr);
-  count_launch();
-  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
-      W.upart, chunks, rank, w_pad, U, nullptr);
-  count_launch();
-  return cudaGetLastError();
+  return ltv_into(W, deriv_matrix ? W.Ldt : W.Lt, rank, V, U, nullptr, st);
 }
 
 cudaError_t nys_apply_m(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
@@ -1021,13 +1056,8 @@ cudaError_t nys_apply_m(const NysWs& W, int rank, int64_t n, double s, const flo
   const int w_pad = W.w_pad;
   if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
   const int cg = w_pad / 4;
-  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
-  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, cg), 256, 0, st>>>(W.Lt, n_pad, rank, V, w_pad,
-                                                                      W.upart, active);
-  count_launch();
-  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
-      W.upart, chunks, rank, w_pad, W.U, active);
-  count_launch();
+  cudaError_t e = ltv_into(W, W.Lt, rank, V, W.U, active, st);
+  if (e != cudaSuccess) return e;
   nys_mneg_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
       W.U, rank, w_pad, 1.0 / s, W.Tp, active);
   count_launch();
@@ -1043,13 +1073,8 @@ cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float
   const int w_pad = W.w_pad;
   if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
   const int cg = w_pad / 4;
-  const int chunks = static_cast<int>((n_pad + kLtvChunk - 1) / kLtvChunk);
-  nys_ltv_kernel<<<dim3(chunks, (rank + 63) / 64, cg), 256, 0, st>>>(W.Lt, n_pad, rank, V, w_pad,
-                                                                      W.upart, active);
-  count_launch();
-  nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
-      W.upart, chunks, rank, w_pad, W.U, active);
-  count_launch();
+  cudaError_t e = ltv_into(W, W.Lt, rank, V, W.U, active, st);
+  if (e != cudaSuccess) return e;
   nys_wu_kernel<<<dim3((rank + 3) / 4, cg), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp, active);
   count_launch();
   nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(

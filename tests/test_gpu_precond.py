@@ -271,3 +271,19 @@ def test_preconditioned_estimator_has_a_smaller_spread(api):
     for t in range(3):
         assert ip["trace_stderr"][t] < i0["trace_stderr"][t] / 3, (t, ip["trace_stderr"], i0["trace_stderr"])
     assert ip["cg_iters"] < i0["cg_iters"]
+
+
+def test_autograd_wrapper_takes_the_preconditioner(api):
+    import torch
+    from paper_2503_02259_gb300 import autograd
+    prob = inputs.uniform_problem(400, 2, 0, (0.05, 1.0, 0.4), seed=55)
+    theta = torch.tensor(prob.theta, dtype=torch.float64, requires_grad=True)
+    X, y = _dev(prob.X), _dev(prob.y)
+    L = autograd.neg_log_likelihood(theta, X, y, prob.kind, nprobe=8, nlanczos=20, cg_rtol=1e-8,
+                                    seed=9, precond_rank=60, precond_tol=1e-6)
+    (g,) = torch.autograd.grad(2.0 * L, theta)
+    opts = api.solve_opts(nprobe=8, nlanczos=20, cg_rtol=1e-8, seed=9, precond_rank=60,
+                          precond_tol=1e-6)
+    loss, grad, _ = api.gp_loss_and_grad(X, y, prob.kind, prob.theta, opts)
+    assert float(L) == loss
+    np.testing.assert_array_equal(g.numpy(), 2.0 * np.asarray(grad))
