@@ -20,8 +20,15 @@ namespace gp {
 namespace {
 
 constexpr int kStepThreads = 256;
-constexpr int kStepRows = 4;                      // rows per thread (one float4 per column of L)
-constexpr int kStepRowsPerBlock = kStepThreads * kStepRows;
+// Rows per thread of a factor step: 4 (one float4 per column of L), except
+// for the derivative factor when four rows would leave fewer than about four
+// blocks per SM: then 1 (more blocks and loads in flight for its two streams).
+// Measured at n = 2e5, rank 1500: the derivative build is faster with 1 row
+// (a preconditioned loss 2.88 -> 2.72 s), the plain factor slower (0.42 ->
+// 0.52 s, four times the shared-memory reads of the pivot row), so the plain
+// factor always takes 4.
+constexpr int kStepRowsWide = 4;
+constexpr int kStepWideMinBlocks = 152 * 4;
 constexpr int kStepBatch = 8;                     // columns of L loaded ahead per thread
 constexpr int kGT = 64;                           // Gram tile (columns of L)
 constexpr int kGK = 32;                           // Gram rows per shared-memory slab
@@ -171,7 +178,28 @@ __device__ __forceinline__ void kernel_and_dl(pa::fpair r2, int kernel, pa::fpai
 //   dL[i][j] = (dS_i - L[i][j] dd_p / 2 / sqrt(d_p)) / sqrt(d_p),
 // with dd_p = -2 sum_m L[p][m] dL[p][m] (dk/dl = 0 at r = 0), formed by the
 // previous step's last block.
-template <int DMAX, bool DERIV>
+template <int ROWS>
+__device__ __forceinline__ void load_rows(const float* p, float (&out)[ROWS]) {
+  if constexpr (ROWS == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    out[0] = t.x;
+    out[1] = t.y;
+    out[2] = t.z;
+    out[3] = t.w;
+  } else {
+    out[0] = *p;
+  }
+}
+
+template <int ROWS>
+__device__ __forceinline__ void store_rows(float* p, const float (&v)[ROWS]) {
+  if constexpr (ROWS == 4)
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else
+    *p = v[0];
+}
+
+template <int DMAX, bool DERIV, int ROWS>
 __global__ void __launch_bounds__(kStepThreads)
     nys_step_kernel(const __grid_constant__ StepArgs a, const __grid_constant__ pa::ExpConsts C, int j) {
   extern __shared__ float sp[];   // row p of L, then (DERIV) row p of dL/dl; columns < j
@@ -189,71 +217,61 @@ __global__ void __launch_bounds__(kStepThreads)
 #pragma unroll
   for (int t = 0; t < DMAX; ++t) xp[t] = t < a.d ? a.xs[p * a.d + t] : 0.0f;
   __syncthreads();
-  const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x) * kStepRows;
+  const int64_t i0 = (static_cast<int64_t>(blockIdx.x) * kStepThreads + threadIdx.x) * ROWS;
   double best = -INFINITY;
   long long besti = LLONG_MAX;
   if (i0 < a.n_pad) {
-    pa::fpair acc[kStepRows] = {};
-    pa::fpair dacc[kStepRows] = {};
+    pa::fpair acc[ROWS] = {};
+    pa::fpair dacc[ROWS] = {};
     const float* col = a.Lt + i0;
     const float* dcol = DERIV ? a.Ldt + i0 : nullptr;
     // Batches of columns: all loads of a batch are issued before the first
     // is used, so that enough bytes are in flight to stream L at the memory's
-    // rate when few blocks share an SM.
-    constexpr int kB = DERIV ? kStepBatch / 2 : kStepBatch;
+    // rate.
+    constexpr int kB = (ROWS == 1 ? 2 * kStepBatch : kStepBatch) / (DERIV ? 2 : 1);
     int m = 0;
     for (; m + kB <= j; m += kB) {
-      float4 l[kB], dl[kB];
+      float l[kB][ROWS], dl[kB][ROWS];
 #pragma unroll
       for (int u = 0; u < kB; ++u) {
-        l[u] = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m + u) * a.n_pad);
-        if constexpr (DERIV)
-          dl[u] = *reinterpret_cast<const float4*>(dcol + static_cast<int64_t>(m + u) * a.n_pad);
+        load_rows<ROWS>(col + static_cast<int64_t>(m + u) * a.n_pad, l[u]);
+        if constexpr (DERIV) load_rows<ROWS>(dcol + static_cast<int64_t>(m + u) * a.n_pad, dl[u]);
       }
 #pragma unroll
       for (int u = 0; u < kB; ++u) {
         const float b = sp[m + u];
-        acc_prod(acc[0], l[u].x, b);
-        acc_prod(acc[1], l[u].y, b);
-        acc_prod(acc[2], l[u].z, b);
-        acc_prod(acc[3], l[u].w, b);
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) acc_prod(acc[q], l[u][q], b);
         if constexpr (DERIV) {
           const float db = sdp[m + u];
-          acc_prod(dacc[0], dl[u].x, b);
-          acc_prod(dacc[1], dl[u].y, b);
-          acc_prod(dacc[2], dl[u].z, b);
-          acc_prod(dacc[3], dl[u].w, b);
-          acc_prod(dacc[0], l[u].x, db);
-          acc_prod(dacc[1], l[u].y, db);
-          acc_prod(dacc[2], l[u].z, db);
-          acc_prod(dacc[3], l[u].w, db);
+#pragma unroll
+          for (int q = 0; q < ROWS; ++q) {
+            acc_prod(dacc[q], dl[u][q], b);
+            acc_prod(dacc[q], l[u][q], db);
+          }
         }
       }
     }
     for (; m < j; ++m) {
-      const float4 l = *reinterpret_cast<const float4*>(col + static_cast<int64_t>(m) * a.n_pad);
+      float l[ROWS], dl[ROWS];
+      load_rows<ROWS>(col + static_cast<int64_t>(m) * a.n_pad, l);
       const float b = sp[m];
-      acc_prod(acc[0], l.x, b);
-      acc_prod(acc[1], l.y, b);
-      acc_prod(acc[2], l.z, b);
-      acc_prod(acc[3], l.w, b);
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) acc_prod(acc[q], l[q], b);
       if constexpr (DERIV) {
-        const float4 dl = *reinterpret_cast<const float4*>(dcol + static_cast<int64_t>(m) * a.n_pad);
+        load_rows<ROWS>(dcol + static_cast<int64_t>(m) * a.n_pad, dl);
         const float db = sdp[m];
-        acc_prod(dacc[0], dl.x, b);
-        acc_prod(dacc[1], dl.y, b);
-        acc_prod(dacc[2], dl.z, b);
-        acc_prod(dacc[3], dl.w, b);
-        acc_prod(dacc[0], l.x, db);
-        acc_prod(dacc[1], l.y, db);
-        acc_prod(dacc[2], l.z, db);
-        acc_prod(dacc[3], l.w, db);
+#pragma unroll
+        for (int q = 0; q < ROWS; ++q) {
+          acc_prod(dacc[q], dl[q], b);
+          acc_prod(dacc[q], l[q], db);
+        }
       }
     }
     const double inv = 1.0 / sqrt(dp);
-    float out[kStepRows], dout[kStepRows];
+    float out[ROWS], dout[ROWS];
 #pragma unroll
-    for (int q = 0; q < kStepRows; ++q) {
+    for (int q = 0; q < ROWS; ++q) {
       const int64_t i = i0 + q;
       float c = 0.0f, dc = 0.0f;
       if (i < a.n) {
@@ -278,11 +296,8 @@ __global__ void __launch_bounds__(kStepThreads)
       out[q] = c;
       dout[q] = dc;
     }
-    *reinterpret_cast<float4*>(a.Lt + static_cast<int64_t>(j) * a.n_pad + i0) =
-        make_float4(out[0], out[1], out[2], out[3]);
-    if constexpr (DERIV)
-      *reinterpret_cast<float4*>(a.Ldt + static_cast<int64_t>(j) * a.n_pad + i0) =
-          make_float4(dout[0], dout[1], dout[2], dout[3]);
+    store_rows<ROWS>(a.Lt + static_cast<int64_t>(j) * a.n_pad + i0, out);
+    if constexpr (DERIV) store_rows<ROWS>(a.Ldt + static_cast<int64_t>(j) * a.n_pad + i0, dout);
   }
   // Block argmax, then the last block picks the next pivot.
   __shared__ double wv[kStepThreads / 32];
@@ -848,7 +863,7 @@ struct NysCarve {
 NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad, bool deriv) {
   NysCarve c(base);
   NysWs w{};
-  const int step_blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
+  const int step_blocks = static_cast<int>((n_pad + kStepThreads - 1) / kStepThreads);   // most: 1 row per thread
   const int64_t chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
   w.xs = c.take<float>(static_cast<size_t>(n_pad) * d);
   w.Lt = c.take<float>(static_cast<size_t>(kmax) * n_pad);
@@ -930,13 +945,18 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
   a.dlc = pa::from_double(P.kernel == 0 ? 1.0 / (kl * kl * kl) : 1.0 / kl);
   const bool deriv = W.deriv;
   if (deriv && P.ls != nullptr) return cudaErrorInvalidValue;
-  const int blocks = static_cast<int>((n_pad + kStepRowsPerBlock - 1) / kStepRowsPerBlock);
+  const int wide_blocks =
+      static_cast<int>((n_pad + kStepThreads * kStepRowsWide - 1) / (kStepThreads * kStepRowsWide));
+  const bool wide = !deriv || wide_blocks >= kStepWideMinBlocks;
+  const int blocks = wide ? wide_blocks : static_cast<int>((n_pad + kStepThreads - 1) / kStepThreads);
   const size_t smem = static_cast<size_t>(kmax) * sizeof(float) * (deriv ? 2 : 1);
   for (int j = 0; j < kmax; ++j) {
-    if (deriv)
-      nys_step_kernel<GP_MAX_DIM, true><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+    if (deriv && wide)
+      nys_step_kernel<GP_MAX_DIM, true, kStepRowsWide><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+    else if (deriv)
+      nys_step_kernel<GP_MAX_DIM, true, 1><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
     else
-      nys_step_kernel<GP_MAX_DIM, false><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
+      nys_step_kernel<GP_MAX_DIM, false, kStepRowsWide><<<blocks, kStepThreads, smem, st>>>(a, consts, j);
     count_launch();
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
