@@ -512,6 +512,69 @@ def loss_grad_mixed_vs_fp32(api, torch, rates: dict, full_n: int = 200_000) -> d
     return out
 
 
+def loss_grad_diff_precond(api, torch, rates: dict, m_identity_ms: float | None = None,
+                           full_n: int = 200_000, rank_sub: int = 800, rank_full: int = 2000) -> dict:
+    """The differentiation problem's L(Theta) and dL/dTheta (32 probes x 40 Lanczos steps,
+    CG to 1e-6) with the Nystrom preconditioner (Eq. 1 / Eq. 2 with M = sI + LL^T,
+    probes z ~ N(0, M)).  On the n = 4000 subsample: the error against the exact L and
+    dL/dTheta (Cholesky, stored FP64 values) for M = I and for the rank-rank_sub M, and
+    the split arithmetic's difference from FP32 on the same probes.  At n = full_n: the
+    time per Theta with the rank-rank_full M in FP32 and in the split arithmetic, against
+    the unpreconditioned FP32 time (m_identity_ms, from loss_grad_mixed_vs_fp32)."""
+    from paper_2503_02259_gb300 import inputs
+    refs = _refs()
+    lref, gref = float(refs["diffx_loss"]), np.asarray(refs["diffx_grad"])
+
+    def relgrad(grad, ref):
+        fl = 1e-3 * np.linalg.norm(ref)
+        return max(abs(g - r) / max(abs(r), fl) for g, r in zip(grad, ref))
+
+    out = {"workload": f"differentiation problem (n={full_n}, d=8), 32 probes x 40 Lanczos steps, "
+                       f"CG 1e-6; Nystrom rank {rank_full} (rank {rank_sub} on the n=4000 "
+                       "subsample, accuracy vs the exact loss); arm = CG arithmetic[_slq_<SLQ>]"}
+    arms = (("fp32", 0, 0), ("bf16x3_slq_tf32x3", 4, 3))
+    sub = inputs.diff_problem(seed=0, n=4000)
+    Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
+    res = {}
+    for name, pr, sp in (("m_identity_fp32", 0, 0),) + arms:
+        rank = 0 if name.startswith("m_identity") else rank_sub
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=pr, slq_prec=sp,
+                              precond_rank=rank)
+        loss, grad, info = api.gp_loss_and_grad(Xs, ys, sub.kind, sub.theta, opts)
+        res[name] = (loss, grad)
+        key = name if rank == 0 else f"nystrom{rank_sub}_{name}"
+        out[key] = {"relerr_loss_vs_exact_n4000": abs(loss - lref) / abs(lref),
+                    "relerr_grad_vs_exact_n4000": relgrad(grad, gref),
+                    "logdet_stderr": info["logdet_stderr"], "cg_iters": info["cg_iters"]}
+        if rank and name != "fp32":
+            out[key]["reldiff_loss_vs_fp32_same_probes"] = abs(loss - res["fp32"][0]) / abs(res["fp32"][0])
+            out[key]["reldiff_grad_vs_fp32_same_probes"] = relgrad(grad, np.asarray(res["fp32"][1]))
+    full = inputs.diff_problem(seed=0, n=full_n)
+    Xf, yf = torch.from_numpy(full.X).cuda(), torch.from_numpy(full.y).cuda()
+    base = None
+    for name, pr, sp in arms:
+        opts = api.solve_opts(nprobe=32, nlanczos=40, cg_rtol=1e-6, seed=77, prec=pr, slq_prec=sp,
+                              precond_rank=rank_full)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        loss, grad, info = api.gp_loss_and_grad(Xf, yf, full.kind, full.theta, opts)
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3
+        rec = {"ms_per_theta": ms, "loss": loss, "grad": grad, "cg_iters": info["cg_iters"],
+               "relres_max": info["relres_max"], "logdet_stderr": info["logdet_stderr"],
+               "trace_stderr": info["trace_stderr"]}
+        if m_identity_ms:
+            rec["speedup_vs_m_identity_fp32"] = m_identity_ms / ms
+        if base is None:
+            base = (loss, np.asarray(grad), ms)
+        else:
+            rec["reldiff_loss_vs_fp32_same_probes"] = abs(loss - base[0]) / abs(base[0])
+            rec["reldiff_grad_vs_fp32_same_probes"] = relgrad(grad, base[1])
+            rec["speedup_vs_nystrom_fp32"] = base[2] / ms
+        out[f"nystrom{rank_full}_{name}_n{full_n}"] = rec
+    return out
+
+
 def loss_grad_precond(api, B, torch, rates: dict, full_n: int = 200_000, rank_sub: int = 800,
                       rank_full: int = 1500, p: int = 16, k: int = 30, cap_plain: int = 300) -> dict:
     """Eq. 1 / Eq. 2 with the Nystrom preconditioner on the precision problem's kernel
@@ -532,14 +595,32 @@ def loss_grad_precond(api, B, torch, rates: dict, full_n: int = 200_000, rank_su
                        f"n=4000 subsample ({p} probes x {k} Lanczos steps, CG 1e-8); time at "
                        f"n={full_n} (CG 1e-6; M = I capped at {cap_plain} CG iterations)"}
     Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
-    for name, extra in (("m_identity", {}), (f"nystrom_rank{rank_sub}", {"precond_rank": rank_sub})):
+
+    def relgrad(grad, ref, fl):
+        return max(abs(g - r) / max(abs(r), fl) for g, r in zip(grad, ref))
+
+    # The split tensor-core arithmetics run on the same probes as FP32 (the
+    # generator does not depend on the arithmetic), so their difference from the
+    # FP32 arm is the arithmetic's own error.
+    arms = (("m_identity", {}), (f"nystrom_rank{rank_sub}", {"precond_rank": rank_sub}))
+    arms += tuple((f"nystrom_rank{rank_sub}_{tag}", {"precond_rank": rank_sub, "prec": pc, "slq_prec": sp})
+                  for tag, pc, sp in PRECOND_TC_ARMS)
+    for name, extra in arms:
         opts = api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-8, cg_maxit=20000, seed=0, **extra)
         loss, grad, info = api.gp_loss_and_grad(Xs, ys, sub.kind, sub.theta, opts)
         out[name] = {"relerr_loss_vs_exact_n4000": abs(loss - lref) / abs(lref),
-                     "relerr_grad_vs_exact_n4000": max(abs(g - r) / max(abs(r), floor)
-                                                       for g, r in zip(grad, gref)),
+                     "relerr_grad_vs_exact_n4000": relgrad(grad, gref, floor),
                      "logdet_stderr": info["logdet_stderr"], "trace_stderr": info["trace_stderr"],
                      "cg_iters": info["cg_iters"]}
+        if "prec" in extra:
+            base = out[f"nystrom_rank{rank_sub}"]
+            out[name]["reldiff_loss_vs_fp32_same_probes"] = abs(loss - base["_loss"]) / abs(base["_loss"])
+            out[name]["reldiff_grad_vs_fp32_same_probes"] = relgrad(
+                grad, base["_grad"], 1e-3 * np.linalg.norm(base["_grad"]))
+        elif "precond_rank" in extra:
+            out[name]["_loss"], out[name]["_grad"] = loss, np.asarray(grad)
+    base = out[f"nystrom_rank{rank_sub}"]
+    del base["_loss"], base["_grad"]
     full = inputs.precision_problem(seed=0, n=full_n)
     Xf, yf = torch.from_numpy(full.X).cuda(), torch.from_numpy(full.y).cuda()
 
@@ -564,10 +645,26 @@ def loss_grad_precond(api, B, torch, rates: dict, full_n: int = 200_000, rank_su
                     "products_roofline": lossgrad_roofline(full_n, 2, False, p, k, info["cg_iters"],
                                                            ms, rates)})
     out[f"nystrom_rank{rank_full}_n{full_n}"] = rec
+    for tag, pc, sp in PRECOND_TC_ARMS:
+        r2, st2, ms2 = timed(api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-6, cg_maxit=2000, seed=0,
+                                            precond_rank=rank_full, prec=pc, slq_prec=sp))
+        arm = {"ms_per_theta": ms2, "status": st2}
+        if r2 is not None and res is not None:
+            l2, g2, i2 = r2
+            arm.update({"cg_iters": i2["cg_iters"], "relres_max": i2["relres_max"],
+                        "reldiff_loss_vs_fp32_same_probes": abs(l2 - rec["loss"]) / abs(rec["loss"]),
+                        "reldiff_grad_vs_fp32_same_probes": relgrad(
+                            g2, rec["grad"], 1e-3 * np.linalg.norm(rec["grad"])),
+                        "speedup_vs_fp32": ms / ms2})
+        out[f"nystrom_rank{rank_full}_n{full_n}_{tag}"] = arm
     _, st0, ms0 = timed(api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-6, cg_maxit=cap_plain, seed=0))
     out[f"m_identity_n{full_n}_capped"] = {"ms_per_theta": ms0, "cg_iters": cap_plain,
                                            "status": st0, "converged_to_1e-6": st0 == 0}
     return out
+
+
+# (tag, CG arithmetic, Lanczos arithmetic) of the preconditioned loss's tensor-core arms.
+PRECOND_TC_ARMS = (("bf16x3_slq_tf32x3", 4, 3), ("tf32x3", 3, 3))
 
 
 # (name, CG arithmetic, SLQ arithmetic, max_batch): max_batch > 1 runs compatible
@@ -757,6 +854,8 @@ def run_leg(args) -> int:
         out = loss_grad_mixed_vs_fp32(api, torch, rates)
     elif args.leg == "loss_grad_precond":
         out = loss_grad_precond(api, B, torch, rates)
+    elif args.leg == "loss_grad_diff_precond":
+        out = loss_grad_diff_precond(api, torch, rates)
     elif args.leg == "serving_accuracy":
         out = serving_accuracy(torch)
     else:
@@ -784,7 +883,7 @@ def main() -> int:
                          "profiling; the full run always uses 1e6)")
     ap.add_argument("--leg", default=None,
                     choices=["loss_grad", "precision_modes", "precision_config", "refinement",
-                             "precision_refinement", "loss_grad_precond",
+                             "precision_refinement", "loss_grad_precond", "loss_grad_diff_precond",
                              "loss_grad_mixed_vs_fp32", "serving", "serving_accuracy"],
                     help="run one extra leg alone on cuda:0 and print its JSON (for profiling)")
     args = ap.parse_args()
@@ -899,6 +998,9 @@ def main() -> int:
                 ("refinement", lambda: refinement(api, torch)),
                 ("precision_refinement", lambda: precision_refinement(api, B, torch)),
                 ("loss_grad_mixed_vs_fp32", lambda: loss_grad_mixed_vs_fp32(api, torch, rates)),
+                ("loss_grad_diff_precond", lambda: loss_grad_diff_precond(
+                    api, torch, rates, (extras.get("loss_grad_mixed_vs_fp32", {}).get("fp32") or {})
+                    .get("ms_per_theta"))),
                 ("loss_grad_precond", lambda: loss_grad_precond(api, B, torch, rates)),
                 ("serving", lambda: serving(torch, count=args.serving_requests,
                                             precs=SERVING_ARMS_ALL if args.serving_all_arms

@@ -22,7 +22,9 @@ Contents
       serving_kappa: the condition number of each request's Kh (eigvalsh);
   preck_loss, preck_grad: the exact L and dL/d(s, f, l) (Cholesky) on the
       n = 4000 subsample of the precision problem (d = 2, Gaussian l = 0.05,
-      s = 0.01), for the preconditioned-loss leg.
+      s = 0.01), for the preconditioned-loss leg;
+  diffx_loss, diffx_grad: the exact L and dL/d(s, f, l) (Cholesky) on the
+      n = 4000 differentiation subsample, for its preconditioned arm.
 """
 import os
 import sys
@@ -67,6 +69,12 @@ def preck_refs():
     return float(ex["loss"]), np.asarray(ex["grad"], dtype=np.float64)
 
 
+def diffx_refs():
+    sub = inputs.diff_problem(seed=0, n=4000)
+    ex = O.exact_nll(sub.X, sub.y, sub.kind, sub.theta)
+    return float(ex["loss"]), np.asarray(ex["grad"], dtype=np.float64)
+
+
 SERVING_NMAX = 3000
 SERVING_COUNT = 24
 SERVING_MU_POINTS = 200
@@ -105,10 +113,12 @@ def main():
     dl, dg = diff_refs()
     si, sl, sg, smu, sk = serving_refs()
     pl, pg = preck_refs()
+    xl, xg = diffx_refs()
     np.savez_compressed(OUT, matvec_rows=mr, matvec_Y=mY, matvec_L=mL, precision_rows=pr,
                         precision_Y=pY, diff_loss=np.float64(dl), diff_grad=dg, serving_idx=si,
                         serving_loss=sl, serving_grad=sg, serving_mu=smu,
-                        serving_kappa=sk, preck_loss=np.float64(pl), preck_grad=pg)
+                        serving_kappa=sk, preck_loss=np.float64(pl), preck_grad=pg,
+                        diffx_loss=np.float64(xl), diffx_grad=xg)
     print("wrote", OUT)
 
 

@@ -77,3 +77,11 @@ def test_precision_subsample_exact_loss_is_the_oracles():
     ex = O.exact_nll(sub.X, sub.y, sub.kind, sub.theta)
     assert abs(ex["loss"] - float(refs["preck_loss"])) <= 1e-9 * abs(ex["loss"])
     np.testing.assert_allclose(ex["grad"], refs["preck_grad"], rtol=1e-9, atol=0)
+
+
+def test_differentiation_subsample_exact_loss_is_the_oracles():
+    refs = np.load(REFS)
+    sub = inputs.diff_problem(seed=0, n=4000)
+    ex = O.exact_nll(sub.X, sub.y, sub.kind, sub.theta)
+    assert abs(ex["loss"] - float(refs["diffx_loss"])) <= 1e-9 * abs(ex["loss"])
+    np.testing.assert_allclose(ex["grad"], refs["diffx_grad"], rtol=1e-9, atol=0)

@@ -239,6 +239,33 @@ def test_preconditioned_loss_matches_the_oracle(api, kind, n, d, theta, rank, to
     _check_loss(loss, grad, est["loss"], est["grad"])
 
 
+@pytest.mark.parametrize("prec,slq", [(4, 3), (3, 3)])
+def test_preconditioned_loss_in_split_tensor_core_arithmetic(api, prec, slq):
+    # Split BF16 CG with split TF32 Lanczos, and split TF32 throughout: the
+    # solves and Lanczos products run on the tensor cores, the preconditioner and
+    # the derivative product in FP32.  A product entry carries at most ~4.3e-6
+    # relative error in either arithmetic, so to first order the solves and the
+    # loss may move by kappa(Kh) times that: the bound below.
+    n, d, rank, p, k = 700, 2, 100, 8, 25
+    prob = inputs.uniform_problem(n, d, 0, (0.05, 1.0, 0.2), seed=51)
+    ev = np.linalg.eigvalsh(O.khat_dense(prob.X, prob.kind, prob.theta))
+    tol = max(1e-4, ev[-1] / ev[0] * 4.3e-6)
+    eps = np.random.default_rng(54).standard_normal((n + rank, p)).astype(np.float32)
+    eps_d = _dev(eps)
+    opts = api.solve_opts(nprobe=p, nlanczos=k, cg_rtol=1e-8, cg_maxit=5000, precond_rank=rank,
+                          probes=eps_d, prec=prec, slq_prec=slq)
+    loss, grad, info = api.gp_loss_and_grad(_dev(prob.X), _dev(prob.y), prob.kind, prob.theta, opts)
+    piv = _pivots(api, prob, rank, 0.0)
+    est = O.est_nll_precond(prob.X, prob.y, prob.kind, prob.theta, piv,
+                            eps[n:n + len(piv)].astype(np.float64), eps[:n].astype(np.float64), k)
+    # log|M| comes from the FP32 factor alone, whatever the product arithmetic.
+    assert abs(info["logdet_m"] - est["logdet_M"]) <= 1e-7 * abs(est["logdet_M"])
+    assert abs(loss - est["loss"]) <= tol * abs(est["loss"]), (loss, est["loss"], tol)
+    g, gr = np.asarray(grad), est["grad"]
+    scale = np.maximum(np.abs(gr), 1e-3 * np.linalg.norm(gr))
+    assert np.all(np.abs(g - gr) / scale <= tol), (g, gr, tol)
+
+
 def test_preconditioned_loss_with_every_point_a_pivot_is_exact(api):
     # M = Kh up to the factor's rounding: the stochastic terms vanish for any
     # probes (generated on the device here) and the estimate is the exact loss.
