@@ -532,7 +532,7 @@ def loss_grad_diff_precond(api, torch, rates: dict, m_identity_ms: float | None 
     out = {"workload": f"differentiation problem (n={full_n}, d=8), 32 probes x 40 Lanczos steps, "
                        f"CG 1e-6; Nystrom rank {rank_full} (rank {rank_sub} on the n=4000 "
                        "subsample, accuracy vs the exact loss); arm = CG arithmetic[_slq_<SLQ>]"}
-    arms = (("fp32", 0, 0), ("bf16x3_slq_tf32x3", 4, 3))
+    arms = (("fp32", 0, 0), ("bf16x3_slq_tf32x3", 4, 3), ("bf16x3", 4, 4))
     sub = inputs.diff_problem(seed=0, n=4000)
     Xs, ys = torch.from_numpy(sub.X).cuda(), torch.from_numpy(sub.y).cuda()
     res = {}
@@ -572,6 +572,18 @@ def loss_grad_diff_precond(api, torch, rates: dict, m_identity_ms: float | None 
             rec["reldiff_grad_vs_fp32_same_probes"] = relgrad(grad, base[1])
             rec["speedup_vs_nystrom_fp32"] = base[2] / ms
         out[f"nystrom{rank_full}_{name}_n{full_n}"] = rec
+    # The fastest split arithmetic whose loss and gradient stay within 1e-4 of
+    # FP32 on the same probes (at the full n and on the subsample).
+    ok = [nm for nm, _, _ in arms[1:]
+          if out[f"nystrom{rank_full}_{nm}_n{full_n}"].get("reldiff_loss_vs_fp32_same_probes", 1.0) <= 1e-4
+          and out[f"nystrom{rank_full}_{nm}_n{full_n}"].get("reldiff_grad_vs_fp32_same_probes", 1.0) <= 1e-4
+          and out[f"nystrom{rank_sub}_{nm}"]["reldiff_loss_vs_fp32_same_probes"] <= 1e-4
+          and out[f"nystrom{rank_sub}_{nm}"]["reldiff_grad_vs_fp32_same_probes"] <= 1e-4]
+    best = min(ok, key=lambda nm: out[f"nystrom{rank_full}_{nm}_n{full_n}"]["ms_per_theta"]) if ok else None
+    rec = out[f"nystrom{rank_full}_{best}_n{full_n}"] if best else {}
+    out["mixed_at_1e-4"] = {"arithmetic": best, "ms_per_theta": rec.get("ms_per_theta"),
+                            "speedup_vs_nystrom_fp32": rec.get("speedup_vs_nystrom_fp32"),
+                            "speedup_vs_m_identity_fp32": rec.get("speedup_vs_m_identity_fp32")}
     return out
 
 

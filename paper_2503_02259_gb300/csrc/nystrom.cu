@@ -14,6 +14,7 @@
 #include <climits>
 
 #include "nystrom.cuh"
+#include "pair_arith2.cuh"
 
 namespace gp {
 
@@ -33,9 +34,10 @@ constexpr int kStepBatch = 8;                     // columns of L loaded ahead p
 constexpr int kGT = 64;                           // Gram tile (columns of L)
 constexpr int kGK = 32;                           // Gram rows per shared-memory slab
 constexpr int kLtvChunk = 4096;                   // rows per block of L^T V (chunk bound of upart)
-constexpr int kLtM = 128;                         // columns of L per block of the tiled L^T V
-constexpr int kLtC = 8;                           // columns of V per block of the tiled L^T V
-constexpr int kZTile = 512;                       // rows of T staged per pass of the Z kernel
+constexpr int kLtM = 64;                          // columns of L per block of L^T V
+constexpr int kLtPairs = 20;                      // column pairs of V per block of L^T V (at most)
+constexpr int kZPairs = 10;                       // column pairs of Z per thread (at most)
+constexpr int kZTile = 128;                       // rows of T staged per pass of the Z kernel
 constexpr int kInvWarps = 2;                      // columns of C^-1 per block
 constexpr int kRedCap = 152 * 16;                 // blocks of a grid_for reduction
 
@@ -56,6 +58,26 @@ __device__ __forceinline__ void acc_prod_pair(pa::fpair& acc, float a, float thi
 }
 
 __device__ __forceinline__ void renorm(pa::fpair& a) { a = pa::fast_two_sum(a.hi, a.lo); }
+
+// acc_prod and acc_prod_pair on two columns at once in packed FP32x2
+// arithmetic (pair_arith2.cuh): each lane performs the scalar form's rounded
+// operations, so each column's sum is the scalar Dot2 sum bit for bit.
+__device__ __forceinline__ void acc_prod2(pa2::fp2& acc, float a, float2 b) {
+  const pa2::fp2 p = pa2::two_prod(pa2::bc(a), b);
+  const pa2::fp2 s = pa2::two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = pa2::add(acc.lo, pa2::add(s.lo, p.lo));
+}
+
+__device__ __forceinline__ void acc_prod_pair2(pa2::fp2& acc, float a, float2 thi, float2 tlo) {
+  const pa2::f2 a2 = pa2::bc(a);
+  const pa2::fp2 p = pa2::two_prod(a2, thi);
+  const pa2::fp2 s = pa2::two_sum(acc.hi, p.hi);
+  acc.hi = s.hi;
+  acc.lo = pa2::add(acc.lo, pa2::add(s.lo, pa2::fma_(a2, tlo, p.lo)));
+}
+
+__device__ __forceinline__ void renorm2(pa2::fp2& a) { a = pa2::fast_two_sum(a.hi, a.lo); }
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -647,26 +669,33 @@ __global__ void nys_inverse_kernel(const double* C, int r, double* Winv) {
 
 // ------------------------------------------------------------------ apply --
 
-// Partial sums of U = L^T V over a chunk of rows, tiled through shared memory
-// like the Gram kernel: block (x, y, z) covers columns kLtM y .. of L (rows of
-// Lt) and the kLtC columns kLtC z .. of V over its chunk of rows, in slabs of
-// kGK rows; thread t accumulates column m = t / 2 of L against four columns of
-// V (Dot2, renormalised per slab).
+// Partial sums of U = L^T V over a chunk of rows: block (x, y, z) covers the
+// kLtM columns kLtM y .. of L (rows of Lt) and column group z of V (gw columns
+// from c0 = z gw, as column pairs) over chunk x of the rows, in slabs of kGK
+// rows staged in shared memory.  Thread t takes column m = t / 4 of L and the
+// column pairs k = t % 4 + 4 j, j < NPT, of the group (Dot2 in packed FP32x2,
+// renormalised per slab), so every element of L is read once per group.
+template <int NPT>
 __global__ void __launch_bounds__(256)
-    nys_ltv_tiled_kernel(const float* __restrict__ Lt, int64_t n_pad, int r,
-                         const float* __restrict__ V, int w_pad, int64_t rows_per_chunk,
-                         double* upart, const int* active) {
+    nys_ltv_pk_kernel(const float* __restrict__ Lt, int64_t n_pad, int r,
+                      const float* __restrict__ V, int w_pad, int gw, int64_t rows_per_chunk,
+                      double* upart, const int* active) {
   if (active != nullptr && *active == 0) return;
-  __shared__ __align__(16) float As[kGK][kLtM + 4];
-  __shared__ __align__(16) float Bs[kGK][kLtC];
-  const int m0 = blockIdx.y * kLtM, c0 = blockIdx.z * kLtC;
+  constexpr int BC = 8 * NPT;                        // columns staged per slab row
+  __shared__ float As[kGK][kLtM + 1];                // L slab, transposed (stride 65: no conflicts)
+  __shared__ __align__(16) float Bs[kGK][BC];
+  const int m0 = blockIdx.y * kLtM, c0 = blockIdx.z * gw;
+  const int cend = min(c0 + gw, w_pad);
   const int64_t i_begin = static_cast<int64_t>(blockIdx.x) * rows_per_chunk;
   const int64_t i_end = i_begin + rows_per_chunk < n_pad ? i_begin + rows_per_chunk : n_pad;
-  const int tm = threadIdx.x >> 1, tc = (threadIdx.x & 1) * 4;
-  pa::fpair acc[4] = {};
+  const int tm = threadIdx.x >> 2, tq = threadIdx.x & 3;
+  pa2::fp2 acc[NPT];
+#pragma unroll
+  for (int j = 0; j < NPT; ++j) acc[j] = {pa2::bc(0.0f), pa2::bc(0.0f)};
   for (int64_t i0 = i_begin; i0 < i_end; i0 += kGK) {
+    // L slab: kLtM rows of Lt x kGK entries, eight threads per row (coalesced).
     for (int q = threadIdx.x; q < kLtM * (kGK / 4); q += blockDim.x) {
-      const int mm = q / (kGK / 4), part = q % (kGK / 4);
+      const int part = q % (kGK / 4), mm = q / (kGK / 4);
       const int m = m0 + mm;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
       if (m < r) v = *reinterpret_cast<const float4*>(Lt + static_cast<int64_t>(m) * n_pad + i0 + part * 4);
@@ -675,33 +704,36 @@ __global__ void __launch_bounds__(256)
       As[part * 4 + 2][mm] = v.z;
       As[part * 4 + 3][mm] = v.w;
     }
-    if (threadIdx.x < kGK * (kLtC / 4)) {
-      const int ii = threadIdx.x / (kLtC / 4), h = threadIdx.x % (kLtC / 4);
+    // V slab: kGK rows x BC columns of the group (zero past its end).
+    for (int q = threadIdx.x; q < kGK * (BC / 4); q += blockDim.x) {
+      const int ii = q / (BC / 4), h = q % (BC / 4);
       const int c = c0 + h * 4;
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (c < w_pad) v = *reinterpret_cast<const float4*>(V + (i0 + ii) * w_pad + c);
+      if (c < cend) v = *reinterpret_cast<const float4*>(V + (i0 + ii) * w_pad + c);
       *reinterpret_cast<float4*>(&Bs[ii][h * 4]) = v;
     }
     __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
     for (int ii = 0; ii < kGK; ++ii) {
       const float a = As[ii][tm];
-      const float4 b = *reinterpret_cast<const float4*>(&Bs[ii][tc]);
-      acc_prod(acc[0], a, b.x);
-      acc_prod(acc[1], a, b.y);
-      acc_prod(acc[2], a, b.z);
-      acc_prod(acc[3], a, b.w);
+#pragma unroll
+      for (int j = 0; j < NPT; ++j)
+        acc_prod2(acc[j], a, *reinterpret_cast<const float2*>(&Bs[ii][2 * (tq + 4 * j)]));
     }
 #pragma unroll
-    for (int q = 0; q < 4; ++q) renorm(acc[q]);
+    for (int j = 0; j < NPT; ++j) renorm2(acc[j]);
     __syncthreads();
   }
   const int m = m0 + tm;
-  const int c = c0 + tc;
-  if (m < r && c < w_pad) {
-    double* out = upart + (static_cast<int64_t>(blockIdx.x) * r + m) * w_pad + c;
+  if (m >= r) return;
+  double* out = upart + (static_cast<int64_t>(blockIdx.x) * r + m) * w_pad;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) out[q] = pa::to_double(acc[q]);
+  for (int j = 0; j < NPT; ++j) {
+    const int c = c0 + 2 * (tq + 4 * j);
+    if (c < cend) {
+      out[c] = pa::to_double(pa2::lane(acc[j], 0));
+      out[c + 1] = pa::to_double(pa2::lane(acc[j], 1));
+    }
   }
 }
 
@@ -757,30 +789,36 @@ __global__ void nys_mneg_kernel(const double* U, int r, int w_pad, double inv_s,
   }
 }
 
-// Z = (V - L T) * scale for the four columns 4 y .. 4 y + 3; one row per
-// thread (V and Z may be the same block: each element is read, then written,
-// by one thread).
+// Z = (V - L T) * scale over column group y (gw columns from c0 = y gw, as
+// column pairs); one row per thread, NPZ column pairs per thread (packed FP32x2
+// Dot2 with T = thi + tlo: the high part's product exact, the low part's folded
+// into the error term), T staged in shared memory kZTile rows at a time as
+// (thi, thi, tlo, tlo) per pair.  V and Z may be the same block: each element
+// is read, then written, by one thread.
+template <int NPZ>
 __global__ void __launch_bounds__(256)
-    nys_z_kernel(const float* __restrict__ Lt, int64_t n_pad, int64_t n, int r, const float* Tp,
-                 const float* V, float* Z, int w_pad, double scale, const int* active) {
+    nys_z_pk_kernel(const float* __restrict__ Lt, int64_t n_pad, int64_t n, int r, const float* Tp,
+                    const float* V, float* Z, int w_pad, int gw, double scale, const int* active) {
   if (active != nullptr && *active == 0) return;
-  __shared__ float sT[kZTile][8];
-  const int c0 = blockIdx.y * 4;
+  __shared__ float4 sT[kZTile][NPZ];
+  const int c0 = blockIdx.y * gw;
+  const int cend = min(c0 + gw, w_pad);
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  pa::fpair acc[4] = {};
+  pa2::fp2 acc[NPZ];
+#pragma unroll
+  for (int k = 0; k < NPZ; ++k) acc[k] = {pa2::bc(0.0f), pa2::bc(0.0f)};
   for (int mt = 0; mt < r; mt += kZTile) {
     const int mcount = r - mt < kZTile ? r - mt : kZTile;
     __syncthreads();
-    for (int q = threadIdx.x; q < kZTile * 4; q += blockDim.x) {
-      const int mm = q >> 2, cc = q & 3;
-      float hi = 0.0f, lo = 0.0f;
-      if (mm < mcount) {
-        const float* t = Tp + (static_cast<int64_t>(mt + mm) * w_pad + c0 + cc) * 2;
-        hi = t[0];
-        lo = t[1];
+    for (int q = threadIdx.x; q < kZTile * NPZ; q += blockDim.x) {
+      const int mm = q / NPZ, k = q % NPZ;
+      const int c = c0 + 2 * k;
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (mm < mcount && c < cend) {
+        const float4 pr = *reinterpret_cast<const float4*>(Tp + (static_cast<int64_t>(mt + mm) * w_pad + c) * 2);
+        t = make_float4(pr.x, pr.z, pr.y, pr.w);
       }
-      sT[mm][2 * cc] = hi;
-      sT[mm][2 * cc + 1] = lo;
+      sT[mm][k] = t;
     }
     __syncthreads();
     if (i < n) {
@@ -793,24 +831,36 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
         for (int u = 0; u < kStepBatch; ++u)
 #pragma unroll
-          for (int cc = 0; cc < 4; ++cc)
-            acc_prod_pair(acc[cc], l[u], sT[mm + u][2 * cc], sT[mm + u][2 * cc + 1]);
+          for (int k = 0; k < NPZ; ++k) {
+            const float4 t = sT[mm + u][k];
+            acc_prod_pair2(acc[k], l[u], make_float2(t.x, t.y), make_float2(t.z, t.w));
+          }
       }
       for (; mm < mcount; ++mm) {
         const float l = col[static_cast<int64_t>(mm) * n_pad];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) acc_prod_pair(acc[cc], l, sT[mm][2 * cc], sT[mm][2 * cc + 1]);
+        for (int k = 0; k < NPZ; ++k) {
+          const float4 t = sT[mm][k];
+          acc_prod_pair2(acc[k], l, make_float2(t.x, t.y), make_float2(t.z, t.w));
+        }
       }
 #pragma unroll
-      for (int cc = 0; cc < 4; ++cc) renorm(acc[cc]);
+      for (int k = 0; k < NPZ; ++k) renorm2(acc[k]);
     }
   }
   if (i >= n_pad) return;
 #pragma unroll
-  for (int cc = 0; cc < 4; ++cc) {
-    float z = 0.0f;
-    if (i < n) z = static_cast<float>((static_cast<double>(V[i * w_pad + c0 + cc]) - pa::to_double(acc[cc])) * scale);
-    Z[i * w_pad + c0 + cc] = z;
+  for (int k = 0; k < NPZ; ++k) {
+    const int c = c0 + 2 * k;
+    if (c >= cend) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float z = 0.0f;
+      if (i < n)
+        z = static_cast<float>((static_cast<double>(V[i * w_pad + c + h]) -
+                                pa::to_double(pa2::lane(acc[k], h))) * scale);
+      Z[i * w_pad + c + h] = z;
+    }
   }
 }
 
@@ -1027,16 +1077,50 @@ static cudaError_t ltv_into(const NysWs& W, const float* Lm, int rank, const flo
                            const int* active, cudaStream_t st) {
   const int64_t n_pad = W.n_pad;
   const int w_pad = W.w_pad;
-  const int mt = (rank + kLtM - 1) / kLtM, ct = (w_pad + kLtC - 1) / kLtC;
+  // Column groups of at most 2 kLtPairs columns, as even as multiples of 4 allow.
+  const int ng = (w_pad + 2 * kLtPairs - 1) / (2 * kLtPairs);
+  const int gw = static_cast<int>(round_up64((w_pad + ng - 1) / ng, 4));
+  const int npt = (gw / 2 + 3) / 4;
+  const int mt = (rank + kLtM - 1) / kLtM;
   const int64_t max_chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
-  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(max_chunks, (608 + mt * ct - 1) / (mt * ct)));
+  const int64_t G = std::max<int64_t>(1, std::min<int64_t>(max_chunks, (608 + mt * ng - 1) / (mt * ng)));
   const int64_t rpc = round_up64((n_pad + G - 1) / G, kGK);
   const int chunks = static_cast<int>((n_pad + rpc - 1) / rpc);
-  nys_ltv_tiled_kernel<<<dim3(chunks, mt, ct), 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, rpc, W.upart,
-                                                             active);
+  const dim3 grid(chunks, mt, ng);
+  switch (npt) {
+    case 1: nys_ltv_pk_kernel<1><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+    case 2: nys_ltv_pk_kernel<2><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+    case 3: nys_ltv_pk_kernel<3><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+    case 4: nys_ltv_pk_kernel<4><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+    default: nys_ltv_pk_kernel<5><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+  }
   count_launch();
   nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
       W.upart, chunks, rank, w_pad, U, active);
+  count_launch();
+  return cudaGetLastError();
+}
+
+// Z = (V - L T) * scale with T = W.Tp, in column groups of at most 2 kZPairs
+// columns (as even as pairs allow).
+static cudaError_t z_into(const NysWs& W, int rank, int64_t n, const float* V, float* Z, double scale,
+                          const int* active, cudaStream_t st) {
+  const int64_t n_pad = W.n_pad;
+  const int w_pad = W.w_pad;
+  const int ng = (w_pad + 2 * kZPairs - 1) / (2 * kZPairs);
+  const int gw = 2 * ((w_pad / 2 + ng - 1) / ng);
+  const dim3 grid(static_cast<unsigned>((n_pad + 255) / 256), static_cast<unsigned>(ng));
+#define GP_Z_CASE(P)                                                                          \
+  case P:                                                                                     \
+    nys_z_pk_kernel<P><<<grid, 256, 0, st>>>(W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, gw, scale, \
+                                             active);                                         \
+    break;
+  switch (gw / 2) {
+    GP_Z_CASE(1) GP_Z_CASE(2) GP_Z_CASE(3) GP_Z_CASE(4) GP_Z_CASE(5)
+    GP_Z_CASE(6) GP_Z_CASE(7) GP_Z_CASE(8) GP_Z_CASE(9)
+    default: GP_Z_CASE(10)
+  }
+#undef GP_Z_CASE
   count_launch();
   return cudaGetLastError();
 }
@@ -1057,10 +1141,7 @@ cudaError_t nys_probes(const NysWs& W, int rank, int64_t n, double s, const floa
   nys_eps_kernel<<<grid_for((n_pad + rank) * w_pad, 256), 256, 0, st>>>(
       eps, tag, n, n_pad, rank, p, col0, w_pad, sqrt(s), B, W.Tp);
   count_launch();
-  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), w_pad / 4), 256, 0, st>>>(
-      W.Lt, n_pad, n, rank, W.Tp, B, B, w_pad, 1.0, nullptr);
-  count_launch();
-  return cudaGetLastError();
+  return z_into(W, rank, n, B, B, 1.0, nullptr, st);
 }
 
 cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const float* V, double* U,
@@ -1072,24 +1153,18 @@ cudaError_t nys_lt_times(const NysWs& W, int rank, bool deriv_matrix, const floa
 
 cudaError_t nys_apply_m(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
                         const int* active, cudaStream_t st) {
-  const int64_t n_pad = W.n_pad;
   const int w_pad = W.w_pad;
   if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
-  const int cg = w_pad / 4;
   cudaError_t e = ltv_into(W, W.Lt, rank, V, W.U, active, st);
   if (e != cudaSuccess) return e;
   nys_mneg_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
       W.U, rank, w_pad, 1.0 / s, W.Tp, active);
   count_launch();
-  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(
-      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, s, active);
-  count_launch();
-  return cudaGetLastError();
+  return z_into(W, rank, n, V, Z, s, active, st);
 }
 
 cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float* V, float* Z,
                       const int* active, cudaStream_t st) {
-  const int64_t n_pad = W.n_pad;
   const int w_pad = W.w_pad;
   if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
   const int cg = w_pad / 4;
@@ -1097,10 +1172,7 @@ cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float
   if (e != cudaSuccess) return e;
   nys_wu_kernel<<<dim3((rank + 3) / 4, cg), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp, active);
   count_launch();
-  nys_z_kernel<<<dim3(static_cast<unsigned>((n_pad + 255) / 256), cg), 256, 0, st>>>(
-      W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, 1.0 / s, active);
-  count_launch();
-  return cudaGetLastError();
+  return z_into(W, rank, n, V, Z, 1.0 / s, active, st);
 }
 
 }  // namespace gp
