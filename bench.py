@@ -867,7 +867,7 @@ def run_leg(args) -> int:
     elif args.leg == "loss_grad_precond":
         out = loss_grad_precond(api, B, torch, rates)
     elif args.leg == "loss_grad_diff_precond":
-        out = loss_grad_diff_precond(api, torch, rates)
+        out = loss_grad_diff_precond(api, torch, rates, full_n=args.precond_n)
     elif args.leg == "serving_accuracy":
         out = serving_accuracy(torch)
     else:
@@ -893,6 +893,9 @@ def main() -> int:
     ap.add_argument("--precision-n", type=int, default=1_000_000,
                     help="points of the precision_refinement leg when run alone (smaller n for "
                          "profiling; the full run always uses 1e6)")
+    ap.add_argument("--precond-n", type=int, default=200_000,
+                    help="points of the loss_grad_diff_precond leg when run alone (smaller n for "
+                         "profiling; the full run always uses 2e5)")
     ap.add_argument("--leg", default=None,
                     choices=["loss_grad", "precision_modes", "precision_config", "refinement",
                              "precision_refinement", "loss_grad_precond", "loss_grad_diff_precond",

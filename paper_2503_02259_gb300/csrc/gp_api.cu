@@ -602,6 +602,12 @@ static Precond carve_precond(void* base, int64_t n_pad, int d, int kmax, int w_p
   return pc;
 }
 
+// The preconditioner computes only the solve's own w columns (rounded up to 4)
+// of planes padded wider for a tensor-core product.
+static void set_live_width(Precond& pc, int w) {
+  pc.ws.w_live = static_cast<int>(std::min<int64_t>(pc.ws.w_pad, round_up(w, 4)));
+}
+
 static int precond_kmax(const gp_problem* prob, int rank) {
   return static_cast<int>(std::min<int64_t>(rank, prob->n));
 }
@@ -965,6 +971,7 @@ static gp_status forward_impl(const gp_problem* prob, const float* y, const gp_s
     const int kmax = precond_kmax(prob, o->precond_rank);
     ss.pcd = carve_precond(static_cast<char*>(ws) + align256(W.bytes), ss.pc.nr_pad, prob->d, kmax,
                            ss.pc.w_pad, lz_k, with_grad);
+    set_live_width(ss.pcd, w);
     if ((s = build_precond(prob, kmax, o->precond_tol, ss.pcd, st)) != GP_OK) return s;
     GP_CUDA(nys_closed_terms(ss.pcd.ws, ss.pcd.rank, n, prob->theta.s, prob->theta.f,
                              &W.S->logdet_m, W.S->trm, st));
@@ -1203,6 +1210,7 @@ gp_status refine_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if (kmax > 0) {
     pcond = carve_precond(static_cast<char*>(ws) + align256(base), ss.pc.nr_pad, prob->d, kmax,
                           ss.pc.w_pad);
+    set_live_width(pcond, w);
     if ((s = build_precond(prob, kmax, opts->precond_tol, pcond, st)) != GP_OK) return s;
   }
   const size_t plane = static_cast<size_t>(ss.pc.nr_pad) * ss.pc.w_pad;
@@ -1670,6 +1678,7 @@ gp_status gp_pcg_solve(const gp_problem* prob, const float* B, int32_t w, float*
   if (kmax > 0) {
     pcond = carve_precond(static_cast<char*>(ws) + align256(base), ss.pc.nr_pad, prob->d, kmax,
                           ss.pc.w_pad);
+    set_live_width(pcond, w);
     if ((s = build_precond(prob, kmax, opts->precond_tol, pcond, st)) != GP_OK) return s;
   }
   GP_CUDA(launch_pad_block(B, prob->n, w, w, ss.W.B, ss.pc.nr_pad, ss.pc.w_pad, 0, st));

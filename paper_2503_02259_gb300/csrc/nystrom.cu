@@ -678,14 +678,14 @@ __global__ void nys_inverse_kernel(const double* C, int r, double* Winv) {
 template <int NPT>
 __global__ void __launch_bounds__(256)
     nys_ltv_pk_kernel(const float* __restrict__ Lt, int64_t n_pad, int r,
-                      const float* __restrict__ V, int w_pad, int gw, int64_t rows_per_chunk,
-                      double* upart, const int* active) {
+                      const float* __restrict__ V, int w_pad, int w_live, int gw,
+                      int64_t rows_per_chunk, double* upart, const int* active) {
   if (active != nullptr && *active == 0) return;
   constexpr int BC = 8 * NPT;                        // columns staged per slab row
   __shared__ float As[kGK][kLtM + 1];                // L slab, transposed (stride 65: no conflicts)
   __shared__ __align__(16) float Bs[kGK][BC];
   const int m0 = blockIdx.y * kLtM, c0 = blockIdx.z * gw;
-  const int cend = min(c0 + gw, w_pad);
+  const int cend = min(c0 + gw, w_live);
   const int64_t i_begin = static_cast<int64_t>(blockIdx.x) * rows_per_chunk;
   const int64_t i_end = i_begin + rows_per_chunk < n_pad ? i_begin + rows_per_chunk : n_pad;
   const int tm = threadIdx.x >> 2, tq = threadIdx.x & 3;
@@ -737,14 +737,17 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-__global__ void nys_u_reduce_kernel(const double* upart, int chunks, int r, int w_pad, double* U,
-                                    const int* active) {
+// U = the fixed-order sum of the chunks' partial sums; zero in the columns from
+// w_live to w_pad (which the partial sums do not cover).
+__global__ void nys_u_reduce_kernel(const double* upart, int chunks, int r, int w_pad, int w_live,
+                                    double* U, const int* active) {
   if (active != nullptr && *active == 0) return;
   const int64_t total = static_cast<int64_t>(r) * w_pad;
   for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
     double v = 0.0;
-    for (int ch = 0; ch < chunks; ++ch) v += upart[static_cast<int64_t>(ch) * total + e];
+    if (static_cast<int>(e % w_pad) < w_live)
+      for (int ch = 0; ch < chunks; ++ch) v += upart[static_cast<int64_t>(ch) * total + e];
     U[e] = v;
   }
 }
@@ -793,16 +796,18 @@ __global__ void nys_mneg_kernel(const double* U, int r, int w_pad, double inv_s,
 // column pairs); one row per thread, NPZ column pairs per thread (packed FP32x2
 // Dot2 with T = thi + tlo: the high part's product exact, the low part's folded
 // into the error term), T staged in shared memory kZTile rows at a time as
-// (thi, thi, tlo, tlo) per pair.  V and Z may be the same block: each element
-// is read, then written, by one thread.
+// (thi, thi, tlo, tlo) per pair; the columns from w_live to w_pad of Z are
+// written as zeros.  V and Z may be the same block: each element is read, then
+// written, by one thread.
 template <int NPZ>
 __global__ void __launch_bounds__(256)
     nys_z_pk_kernel(const float* __restrict__ Lt, int64_t n_pad, int64_t n, int r, const float* Tp,
-                    const float* V, float* Z, int w_pad, int gw, double scale, const int* active) {
+                    const float* V, float* Z, int w_pad, int w_live, int gw, double scale,
+                    const int* active) {
   if (active != nullptr && *active == 0) return;
   __shared__ float4 sT[kZTile][NPZ];
   const int c0 = blockIdx.y * gw;
-  const int cend = min(c0 + gw, w_pad);
+  const int cend = min(c0 + gw, w_live);
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   pa2::fp2 acc[NPZ];
 #pragma unroll
@@ -849,6 +854,8 @@ __global__ void __launch_bounds__(256)
     }
   }
   if (i >= n_pad) return;
+  if (blockIdx.y == 0)
+    for (int c = w_live; c < w_pad; ++c) Z[i * w_pad + c] = 0.0f;
 #pragma unroll
   for (int k = 0; k < NPZ; ++k) {
     const int c = c0 + 2 * k;
@@ -940,6 +947,7 @@ NysWs carve_nys(void* base, int64_t n_pad, int d, int kmax, int w_pad, bool deri
   w.n_pad = n_pad;
   w.kmax = kmax;
   w.w_pad = w_pad;
+  w.w_live = w_pad;
   w.d = d;
   w.deriv = deriv;
   w.bytes = c.off + 256;
@@ -1076,10 +1084,10 @@ cudaError_t nys_build(const NysWs& W, const NysProblem& P, int kmax, double tol_
 static cudaError_t ltv_into(const NysWs& W, const float* Lm, int rank, const float* V, double* U,
                            const int* active, cudaStream_t st) {
   const int64_t n_pad = W.n_pad;
-  const int w_pad = W.w_pad;
-  // Column groups of at most 2 kLtPairs columns, as even as multiples of 4 allow.
-  const int ng = (w_pad + 2 * kLtPairs - 1) / (2 * kLtPairs);
-  const int gw = static_cast<int>(round_up64((w_pad + ng - 1) / ng, 4));
+  const int w_pad = W.w_pad, live = W.w_live;
+  // Column groups of at most 2 kLtPairs live columns, as even as multiples of 4 allow.
+  const int ng = (live + 2 * kLtPairs - 1) / (2 * kLtPairs);
+  const int gw = static_cast<int>(round_up64((live + ng - 1) / ng, 4));
   const int npt = (gw / 2 + 3) / 4;
   const int mt = (rank + kLtM - 1) / kLtM;
   const int64_t max_chunks = (n_pad + kLtvChunk - 1) / kLtvChunk;
@@ -1087,33 +1095,36 @@ static cudaError_t ltv_into(const NysWs& W, const float* Lm, int rank, const flo
   const int64_t rpc = round_up64((n_pad + G - 1) / G, kGK);
   const int chunks = static_cast<int>((n_pad + rpc - 1) / rpc);
   const dim3 grid(chunks, mt, ng);
+#define GP_LTV_CASE(P)                                                                        \
+  case P:                                                                                     \
+    nys_ltv_pk_kernel<P><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, live, gw, rpc, W.upart, \
+                                               active);                                       \
+    break;
   switch (npt) {
-    case 1: nys_ltv_pk_kernel<1><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
-    case 2: nys_ltv_pk_kernel<2><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
-    case 3: nys_ltv_pk_kernel<3><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
-    case 4: nys_ltv_pk_kernel<4><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
-    default: nys_ltv_pk_kernel<5><<<grid, 256, 0, st>>>(Lm, n_pad, rank, V, w_pad, gw, rpc, W.upart, active); break;
+    GP_LTV_CASE(1) GP_LTV_CASE(2) GP_LTV_CASE(3) GP_LTV_CASE(4)
+    default: GP_LTV_CASE(5)
   }
+#undef GP_LTV_CASE
   count_launch();
   nys_u_reduce_kernel<<<grid_for(static_cast<int64_t>(rank) * w_pad, 256), 256, 0, st>>>(
-      W.upart, chunks, rank, w_pad, U, active);
+      W.upart, chunks, rank, w_pad, live, U, active);
   count_launch();
   return cudaGetLastError();
 }
 
 // Z = (V - L T) * scale with T = W.Tp, in column groups of at most 2 kZPairs
-// columns (as even as pairs allow).
+// live columns (as even as pairs allow).
 static cudaError_t z_into(const NysWs& W, int rank, int64_t n, const float* V, float* Z, double scale,
                           const int* active, cudaStream_t st) {
   const int64_t n_pad = W.n_pad;
-  const int w_pad = W.w_pad;
-  const int ng = (w_pad + 2 * kZPairs - 1) / (2 * kZPairs);
-  const int gw = 2 * ((w_pad / 2 + ng - 1) / ng);
+  const int w_pad = W.w_pad, live = W.w_live;
+  const int ng = (live + 2 * kZPairs - 1) / (2 * kZPairs);
+  const int gw = 2 * ((live / 2 + ng - 1) / ng);
   const dim3 grid(static_cast<unsigned>((n_pad + 255) / 256), static_cast<unsigned>(ng));
 #define GP_Z_CASE(P)                                                                          \
   case P:                                                                                     \
-    nys_z_pk_kernel<P><<<grid, 256, 0, st>>>(W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, gw, scale, \
-                                             active);                                         \
+    nys_z_pk_kernel<P><<<grid, 256, 0, st>>>(W.Lt, n_pad, n, rank, W.Tp, V, Z, w_pad, live, gw,  \
+                                             scale, active);                                  \
     break;
   switch (gw / 2) {
     GP_Z_CASE(1) GP_Z_CASE(2) GP_Z_CASE(3) GP_Z_CASE(4) GP_Z_CASE(5)
@@ -1136,7 +1147,7 @@ cudaError_t nys_probes(const NysWs& W, int rank, int64_t n, double s, const floa
                        int p, float* B, int col0, cudaStream_t st) {
   const int64_t n_pad = W.n_pad;
   const int w_pad = W.w_pad;
-  if (rank < 1 || rank > W.kmax || col0 + p > w_pad || w_pad % 4 != 0) return cudaErrorInvalidValue;
+  if (rank < 1 || rank > W.kmax || col0 + p > W.w_live || w_pad % 4 != 0) return cudaErrorInvalidValue;
   const uint64_t tag = seed ^ (1ull << 39);
   nys_eps_kernel<<<grid_for((n_pad + rank) * w_pad, 256), 256, 0, st>>>(
       eps, tag, n, n_pad, rank, p, col0, w_pad, sqrt(s), B, W.Tp);
@@ -1167,10 +1178,10 @@ cudaError_t nys_apply(const NysWs& W, int rank, int64_t n, double s, const float
                       const int* active, cudaStream_t st) {
   const int w_pad = W.w_pad;
   if (rank < 1 || rank > W.kmax || w_pad % 4 != 0) return cudaErrorInvalidValue;
-  const int cg = w_pad / 4;
   cudaError_t e = ltv_into(W, W.Lt, rank, V, W.U, active, st);
   if (e != cudaSuccess) return e;
-  nys_wu_kernel<<<dim3((rank + 3) / 4, cg), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp, active);
+  nys_wu_kernel<<<dim3((rank + 3) / 4, W.w_live / 4), 128, 0, st>>>(W.Winv, W.U, rank, w_pad, W.Tp,
+                                                                     active);
   count_launch();
   return z_into(W, rank, n, V, Z, 1.0 / s, active, st);
 }

@@ -76,6 +76,11 @@ struct NysWs {
   double* U2;         // [kmax][w_pad] (dL/dl)^T V
   int64_t n_pad;
   int kmax, w_pad, d;
+  // Columns of the V / Z planes that the apply computes (a multiple of 4,
+  // <= w_pad): a solve sets it to its own width, rounded up to 4, when the
+  // planes are padded wider for a tensor-core product; the apply writes zeros
+  // to the columns from w_live to w_pad.  carve_nys sets it to w_pad.
+  int w_live;
   bool deriv;
   size_t bytes;
 };
