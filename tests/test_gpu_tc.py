@@ -119,3 +119,55 @@ def test_tc_split_matches_oracle_at_fused_matvec_size(api, prec):
     rows = np.sort(np.random.default_rng(5).choice(prob.n, 500, replace=False))
     rY, _, _ = O.kmv_rows(prob.X, V, prob.kind, prob.theta, rows=rows, block=100)
     assert colwise_relerr(Y[rows], rY) <= TOL[prec]
+
+
+# Split BF16 on point clouds unlike the uniform cubes above, at d in 5..16
+# without the derivative: compact Gaussian clouds, a spread cube at a short
+# length-scale, and clouds with far outliers.  On the clustered clouds K-hat is
+# close to a constant matrix and K-hat V cancels (|K-hat V| at most 0.09 of
+# K-hat |V| here), so the rounding of the entries, relative to the entries, is
+# bounded against K-hat |V|: measured up to 5.2e-5 of |K-hat V|, at most 3.6e-6
+# of K-hat |V|.  The product without the derivative and the K-hat V of the
+# derivative product share the evaluation and the split arithmetic: they agree
+# to 1e-5.
+def _cloud(kind, n, d, seed):
+    rng = np.random.default_rng(seed)
+    if kind == "compact":
+        return (0.5 * rng.standard_normal((n, d))).astype(np.float32)
+    if kind == "spread":
+        return rng.random((n, d)).astype(np.float32)
+    X = 0.3 * rng.standard_normal((n, d))
+    far = rng.random(n) < 0.03
+    X[far] += 2.5
+    return X.astype(np.float32)
+
+
+@pytest.mark.parametrize("n,d,w,kind,cloud,l", [
+    (1000, 8, 33, O.GAUSSIAN, "compact", 1.2),
+    (1537, 16, 48, O.MATERN32, "compact", 3.0),
+    (129, 8, 16, O.GAUSSIAN, "compact", 1.2),
+    (300, 8, 16, O.GAUSSIAN, "spread", 0.3),
+    (2000, 8, 128, O.MATERN32, "outliers", 1.5),
+    (777, 5, 20, O.GAUSSIAN, "outliers", 1.0),
+])
+def test_tc_split_bf16_on_clustered_clouds(api, n, d, w, kind, cloud, l):
+    X = _cloud(cloud, n, d, seed=n + d)
+    V = inputs.gaussian_block(n, w, seed=w + 1)
+    theta = (0.1, 1.0, l)
+    Y = api.gp_kernel_matmul(_dev(X), _dev(V), kind, theta, prec=4).cpu().numpy()
+    rY, _, _ = O.kmv_rows(X.astype(np.float64), V, kind, theta)
+    rA, _, _ = O.kmv_rows(X.astype(np.float64), np.abs(V), kind, theta)   # K-hat |V|
+    err = np.linalg.norm(Y - rY, axis=0) / np.linalg.norm(rA, axis=0)
+    assert float(err.max()) <= TOL[4]
+    # The derivative product's K-hat V.
+    import torch
+    Xd, Vd = _dev(X), _dev(V)
+    prob, _ = api.problem(Xd, kind, theta)
+    Y2 = torch.empty_like(Vd)
+    dYf = torch.empty_like(Vd)
+    from paper_2503_02259_gb300 import _binding as B
+    ws = api.workspace(B.OP_GRAD_MATMUL, prob, w, api.solve_opts(prec=4), Xd.device)
+    B.check(B.lib().gp_kernel_grad_matmul(B.ctypes.byref(prob), api._ptr(Vd), w, api._ptr(Y2),
+                                          api._ptr(dYf), None, 4, api._ptr(ws), ws.numel(),
+                                          api._stream(Xd.device)), "grad_matmul")
+    assert colwise_relerr(Y, Y2.cpu().numpy()) <= 1e-5
