@@ -247,6 +247,31 @@ def lossgrad_roofline(n: int, d: int, matern: bool, p: int, k: int, iters: int, 
                        "product runs all columns until the last converges)"}
 
 
+def precond_lossgrad_roofline(n: int, d: int, matern: bool, p: int, k: int, iters: int, r: int,
+                              ms: float, rates: dict) -> dict:
+    """Algorithmic work of one preconditioned loss + gradient evaluation: the
+    products of lossgrad_roofline, plus the Nystrom work in exact (Dot2) products
+    of 10 FP32 flops (11 for Z, whose T carries a low part): the rank-r factor
+    with dL/dl (three products per row and earlier column: 1.5 n r^2), the Gram
+    matrices L^T L and L^T dL/dl (1.5 n r^2), and n r w per L^T V or Z pass over
+    w = 1 + p rounded up to 4 columns: one apply (L^T V and Z) per CG iteration
+    and two per Lanczos step (M^-1 and M), one for the probes' M^-1 z, the probes'
+    Z, and L^T V and dL/dl^T V for the gradient."""
+    base = lossgrad_roofline(n, d, matern, p, k, iters, ms, rates)
+    wl = 4 * ((1 + p + 3) // 4)
+    factor = 10.0 * 1.5 * n * r * r
+    gram = 10.0 * 1.5 * n * r * r
+    applies = iters + 2 * k + 1
+    apply = float(n) * r * wl * (applies * (10 + 11) + 11 + 2 * 10)
+    flops = base["algorithmic_flops"] + factor + gram + apply
+    achieved = flops / (ms * 1e-3) / 1e12
+    return {"algorithmic_flops": flops, "products_flops": base["algorithmic_flops"],
+            "nystrom_flops": factor + gram + apply, "achieved_tflops": achieved,
+            "fp32_peak_tflops": rates["fp32_ffma2_tflops"],
+            "frac_of_fp32_pipe": achieved / rates["fp32_ffma2_tflops"],
+            "counted": base["counted"] + "; Nystrom work in 10-flop exact products"}
+
+
 def precision_modes(api, B, torch, prob, X, V, dev, rates: dict, steps: int = 5) -> dict:
     """Each tensor-core mode on the bench workload: product-kernel throughput and the
     norm-wise error of K.V and dK/dl.V against FP64 oracle values on 100 sampled rows
@@ -562,7 +587,9 @@ def loss_grad_diff_precond(api, torch, rates: dict, m_identity_ms: float | None 
         ms = (time.perf_counter() - t0) * 1e3
         rec = {"ms_per_theta": ms, "loss": loss, "grad": grad, "cg_iters": info["cg_iters"],
                "relres_max": info["relres_max"], "logdet_stderr": info["logdet_stderr"],
-               "trace_stderr": info["trace_stderr"]}
+               "trace_stderr": info["trace_stderr"],
+               "roofline": precond_lossgrad_roofline(full_n, 8, False, 32, 40, info["cg_iters"],
+                                                     rank_full, ms, rates)}
         if m_identity_ms:
             rec["speedup_vs_m_identity_fp32"] = m_identity_ms / ms
         if base is None:

@@ -52,3 +52,16 @@ def test_single_rank_needs_no_process_group():
     import bench
     assert bench.max_over_ranks(12.5) == 12.5
     assert bench.replica_rate(1, 3.2e11, 28.0) == pytest.approx(3.2e11 / 28e-3)
+
+
+def test_preconditioned_loss_roofline_count():
+    # n = 1000, d = 2 Gaussian (e = 3d + 1 = 7), p = 3 (w = 4), k = 5 Lanczos
+    # steps, 10 CG iterations, rank 20, one second.
+    import bench
+    rates = {"fp32_ffma2_tflops": 80.0, "mufu_ex2_gops": 10000.0}
+    r = bench.precond_lossgrad_roofline(1000, 2, False, 3, 5, 10, 20, 1000.0, rates)
+    n, w, e = 1000, 4, 7
+    products = n * n * (10 * (2 * w + e) + 5 * (2 * 3 + e) + (4 * w + e + 1))
+    nystrom = 2 * 15 * n * 20 ** 2 + n * 20 * 4 * ((10 + 2 * 5 + 1) * 21 + 11 + 20)
+    assert r["products_flops"] == products and r["nystrom_flops"] == nystrom
+    assert abs(r["achieved_tflops"] - (products + nystrom) / 1e12) < 1e-12
